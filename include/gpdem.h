@@ -1,0 +1,214 @@
+/*
+ * gpdem.h -- C ABI of the GB300 detector-error-model compiler.
+ *
+ * The library turns realised, fully unrolled, noisy Clifford circuits into
+ * decoding hypergraphs (detector error models, Sec. 2.1.4 of the GreenPeas
+ * paper) entirely on one GPU:
+ *
+ *   lowering          the flat circuit rows are scanned into TICK layers,
+ *                     measurement records and mechanism numbering
+ *                     (Sec. 2.3.1, "lowering the realised circuit");
+ *   stage 1           detector sensitivities are propagated backward through
+ *                     the layers as 64-bit bit-planes, one detector word per
+ *                     thread block, and every error mechanism receives the
+ *                     words of its flip mask (Sec. 3.1, Eqs. slp/init-slp,
+ *                     Sec. 2.3.4 for Y and two-qubit components);
+ *   stage 2           mechanisms are grouped by exact mask equality and the
+ *                     probabilities of each class are combined as
+ *                     P = (1 - prod(1 - 2 q_i)) / 2 (Eq. pmerge, Sec. 3.2),
+ *                     and the hyperedges are compacted.
+ * An adjoint kernel returns d(loss)/d(noise) for losses linear in the
+ * hyperedge probabilities and log-odds weights.
+ *
+ * Conventions
+ *  - Every entry point returns gp_status; GP_OK is 0.  On failure
+ *    gp_last_error() returns a message for the calling thread.  No entry
+ *    point throws, aborts or traps.
+ *  - Pointers marked "host" are read before the call returns and stay owned
+ *    by the caller.  Pointers marked "device" are CUDA device addresses on
+ *    the driver's device; they must stay valid until the work that reads
+ *    them has finished (gp_compile reads them before returning; the noise
+ *    vector of a compile is read again by gp_backward).
+ *  - Result arrays are device memory owned by the driver and valid until the
+ *    next gp_compile / gp_compile_batch on the same driver.
+ *  - A driver is not thread-safe; use one driver per host thread.
+ *  - All work is issued on the caller's CUDA stream (cudaStream_t passed as
+ *    void*, NULL = legacy default stream).
+ */
+#ifndef GPDEM_H
+#define GPDEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GP_OK = 0,
+    GP_ERR_INVALID = 1,          /* malformed circuit or argument            */
+    GP_ERR_NONDETERMINISTIC = 2, /* a detector/observable is not determined  */
+    GP_ERR_CAPACITY = 3,         /* exceeds the driver's bounds              */
+    GP_ERR_CUDA = 4,             /* a CUDA runtime call failed               */
+    GP_ERR_TIMEOUT = 5,          /* a bounded device wait gave up            */
+    GP_ERR_HORIZON = 6           /* serving window exceeded                  */
+} gp_status;
+
+/* Correlation level (Table tab:correlation-level, Sec. 3.3).  Two-qubit
+ * depolarising channels keep 6 / 10 / 15 Pauli components; one-qubit
+ * depolarising channels keep X and Z at L0 and X, Y, Z at L1 and L2. */
+typedef enum { GP_L0 = 0, GP_L1 = 1, GP_L2 = 2 } gp_level;
+
+/* Flat circuit row kinds (rows are 4 x uint32 = {kind, a, b, c}).
+ *   TICK                      layer boundary
+ *   R, M, MR, RX, MX, MRX     a = qubit
+ *   H, S                      a = qubit
+ *   CX                        a = control, b = target
+ *   CZ                        a, b = qubits
+ *   DETECTOR                  a = offset into recs, b = number of records
+ *   OBSERVABLE_INCLUDE        a = offset, b = number of records, c = index (< 64)
+ *   X_ERROR, Z_ERROR,
+ *   DEPOLARIZE1               a = qubit, c = noise location
+ *   DEPOLARIZE2               a, b = qubits, c = noise location
+ * recs[] holds measurement-record lookbacks k >= 1 (k-th most recent
+ * measurement before the annotation).  Between two TICKs a qubit takes part
+ * in at most one gate; a noise row on a qubit that still has a gate later in
+ * the same layer acts before that gate, otherwise after it (a two-qubit noise
+ * row must be on the same side for both qubits).  Violations give
+ * GP_ERR_INVALID. */
+enum {
+    GP_TICK = 0, GP_R = 1, GP_M = 2, GP_MR = 3, GP_RX = 4, GP_MX = 5, GP_MRX = 6,
+    GP_H = 8, GP_S = 9, GP_CX = 10, GP_CZ = 11,
+    GP_DETECTOR = 16, GP_OBSERVABLE_INCLUDE = 17,
+    GP_X_ERROR = 32, GP_Z_ERROR = 33, GP_DEPOLARIZE1 = 34, GP_DEPOLARIZE2 = 35
+};
+
+/* Channel parameter p per noise location: X_ERROR / Z_ERROR flip with
+ * probability p (0 <= p <= 1/2); DEPOLARIZE1 applies each non-identity Pauli
+ * with p/3 (p <= 3/4); DEPOLARIZE2 each of the fifteen with p/15
+ * (p <= 15/16).  Locations with p = 0 contribute no mechanism. */
+
+typedef struct {
+    const uint32_t *ops;      /* n_ops x 4 rows (host or device)            */
+    uint64_t n_ops;
+    const uint32_t *recs;     /* n_recs lookbacks (host or device)          */
+    uint64_t n_recs;
+    uint32_t n_qubits;        /* qubits are 0 .. n_qubits-1                 */
+    uint32_t n_detectors;     /* must equal the number of DETECTOR rows     */
+    uint32_t n_observables;   /* 1 + largest observable index, <= 64        */
+    uint32_t n_locations;     /* length of this circuit's noise vector      */
+} gp_circuit;
+
+/* Capacity of a driver (Sec. 3.4, buffer reuse: a driver built for a maximal
+ * circuit serves every circuit within these bounds without allocating).
+ * Totals are summed over the circuits of one batch. */
+typedef struct {
+    uint32_t max_circuits;        /* circuits per batch                       */
+    uint32_t max_qubits;          /* qubits of the widest circuit (<= 8192)  */
+    uint64_t max_ops;             /* total rows                               */
+    uint64_t max_recs;            /* total record lookbacks                   */
+    uint32_t max_layers;          /* total TICK layers                        */
+    uint32_t max_measurements;    /* total measurements                       */
+    uint32_t max_detectors;       /* total detectors                          */
+    uint32_t max_locations;       /* total noise locations                    */
+    uint32_t max_mechanisms;      /* total error mechanisms                   */
+    uint32_t max_mask_words;      /* non-zero 64-bit words per mechanism mask
+                                     (0 = default 8, at most 16)             */
+    uint64_t max_det_entries;     /* total detector ids over all hyperedges
+                                     (0 = 16 x max_mechanisms)                */
+} gp_bounds;
+
+/* Device-resident view of the last compile's result (all device pointers,
+ * driver-owned, valid until the next compile on the driver). */
+typedef struct {
+    uint32_t n_circuits;
+    uint32_t n_edges;             /* hyperedges over all circuits             */
+    uint64_t n_det_entries;
+    uint32_t n_mechanisms;        /* mechanisms over all circuits (incl. those
+                                     that flip nothing)                      */
+    uint32_t pad;
+    const uint32_t *det_offsets;  /* n_edges + 1; edge e's detectors are
+                                     det_idx[det_offsets[e] .. det_offsets[e+1]) */
+    const uint32_t *det_idx;      /* ascending detector indices (per circuit) */
+    const uint64_t *obs_mask;     /* bit k = observable k                     */
+    const float *prob;            /* P of the class (Eq. pmerge), FP32        */
+    const float *logodds;         /* w = log((1 - P) / P), FP32               */
+    const uint32_t *edge_circuit; /* circuit of each edge                     */
+    const int32_t *mech_class;    /* n_mechanisms: edge of each mechanism or -1 */
+    const uint32_t *edge_offsets; /* HOST array, n_circuits + 1: circuit b owns
+                                     edges [edge_offsets[b], edge_offsets[b+1]) */
+} gp_dem_view;
+
+typedef struct gp_driver gp_driver;
+
+/* Device bytes a driver with these bounds needs (the workspace that
+ * gp_driver_create carves its buffers from). */
+gp_status gp_workspace_size(const gp_bounds *bounds, uint64_t *bytes);
+
+/* Create a driver on the current CUDA device.  d_workspace: device memory of
+ * at least gp_workspace_size bytes, 256-byte aligned, owned by the caller and
+ * kept alive until gp_driver_destroy; NULL lets the driver allocate (and
+ * free) its own.  Pinned host staging buffers are allocated here, never
+ * during a compile.  Returns GP_ERR_INVALID for unusable bounds. */
+gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace,
+                           uint64_t workspace_bytes, gp_driver **out);
+void gp_driver_destroy(gp_driver *drv);
+
+/* Compile a batch of circuits into one set of hyperedges (Secs. 3.1-3.2).
+ * circuits: host array of n_circuits descriptors; their ops/recs pointers are
+ * device addresses if inputs_on_device, else host addresses.  noise: the
+ * concatenation of every circuit's noise vector (sum of n_locations floats),
+ * device or host likewise.  On GP_OK *out describes the result.  The call
+ * returns after the work has finished on `stream` (it reads back a small
+ * status block).  Errors: GP_ERR_INVALID (malformed rows, noise outside a
+ * channel's range), GP_ERR_NONDETERMINISTIC, GP_ERR_CAPACITY, GP_ERR_CUDA. */
+gp_status gp_compile_batch(gp_driver *drv, const gp_circuit *circuits,
+                           uint32_t n_circuits, const float *noise,
+                           int inputs_on_device, gp_level level, void *stream,
+                           gp_dem_view *out);
+
+/* gp_compile_batch with one circuit. */
+gp_status gp_compile(gp_driver *drv, const gp_circuit *circuit,
+                     const float *noise, int inputs_on_device, gp_level level,
+                     void *stream, gp_dem_view *out);
+
+/* Vector-Jacobian product of the last compile (not in the paper; used to fit
+ * noise parameters): given device arrays g_prob[n_edges] and
+ * g_logodds[n_edges] (either may be NULL = zeros), writes
+ *   g_noise[l] = sum_e g_prob[e] dP_e/dp_l + g_logodds[e] dw_e/dp_l
+ * for every location l of the batch (device array, length = total
+ * n_locations).  Uses dP/dq_i = prod_{j != i} (1 - 2 q_j) over the class of
+ * mechanism i and dw/dP = -1 / (P (1 - P)).  Accumulation is exact
+ * fixed-point, so the result does not depend on scheduling. */
+gp_status gp_backward(gp_driver *drv, const float *g_prob,
+                      const float *g_logodds, float *g_noise, void *stream);
+
+/* View of the last successful compile. */
+gp_status gp_result_view(const gp_driver *drv, gp_dem_view *out);
+
+/* Tunable launch parameters (picked by the package's autotuner). */
+typedef struct {
+    uint32_t stage1_threads;      /* 128, 256 or 512                          */
+    uint32_t stage1_blocks_per_sm;/* resident blocks per SM for stage 1 (0 = max) */
+    uint32_t stage2_threads;      /* 128, 256 or 512                          */
+    uint32_t stage2_blocks_per_sm;/* grid = SMs x this for grid-stride kernels */
+} gp_tuning;
+gp_status gp_set_tuning(gp_driver *drv, const gp_tuning *t);
+gp_status gp_get_tuning(const gp_driver *drv, gp_tuning *t);
+
+/* Per-stage device times of the last compile in microseconds, measured with
+ * CUDA events on the compile's stream when timing is enabled (enable != 0).
+ * times[0] lowering, [1] stage 1, [2] grouping + reduction, [3] compaction. */
+gp_status gp_enable_timing(gp_driver *drv, int enable);
+gp_status gp_last_timing(const gp_driver *drv, float times_us[4]);
+
+/* Number of kernel launches issued by the last compile / backward call. */
+uint32_t gp_last_launch_count(const gp_driver *drv);
+
+/* Thread-local message describing the last failure on this thread. */
+const char *gp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPDEM_H */

@@ -1,0 +1,296 @@
+// common.cuh -- device-side structures and helpers shared by the kernels of
+// the detector-error-model compiler (lowering, stage 1, stage 2, adjoint).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gpdem.h"
+
+namespace gpdem {
+
+// ---------------------------------------------------------------------------
+// limits and constants
+// ---------------------------------------------------------------------------
+constexpr int kRowTile = 4096;          // circuit rows per lowering tile
+constexpr int kLowerThreads = 256;      // 16 rows per thread
+constexpr int kMaxEntries = 1024;       // (measurement, word) pairs per column
+constexpr int kMaxMaskWords = 16;       // hard cap of mask words per mechanism
+constexpr int kMechPerBlockScan = 1024; // mechanisms per compaction block
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint32_t kObsColFlag = 0x80000000u;   // set on the column id of an
+                                                // observable word in a mask
+
+// ---------------------------------------------------------------------------
+// per-circuit descriptor (one per circuit of a batch)
+// ---------------------------------------------------------------------------
+struct CircuitDev {
+    const uint4 *ops;          // rows {kind, a, b, c}
+    const uint32_t *recs;      // record lookbacks
+    uint32_t n_ops, n_recs;
+    uint32_t n_qubits, n_det, n_obs, n_loc;
+    uint32_t col_base, n_cols; // global word columns: detector words, then
+                               // the observable word when n_obs > 0
+    uint32_t det_base, loc_base, op_base, tile_first;
+    uint32_t n_tiles;
+    // filled by the lowering kernels
+    uint32_t n_layers, layer_base;
+    uint32_t n_meas, meas_base;
+    uint32_t n_mech, mech_base;
+    uint32_t pad[1];
+};
+static_assert(sizeof(CircuitDev) % 16 == 0, "CircuitDev alignment");
+
+// compile-wide parameters (uploaded once per compile)
+struct Params {
+    uint32_t n_circuits;
+    uint32_t n_tiles;
+    uint32_t n_items;           // stage-1 work items (= total columns)
+    uint32_t level;
+    uint32_t n_cols_total;
+    uint32_t n_loc_total;
+    uint32_t table_log2;        // hash table capacity = 1 << table_log2
+    uint32_t mask_words;        // S: slots per mechanism
+    uint64_t max_det_entries;
+    uint32_t max_mech;
+    uint32_t max_layer_slots;
+    uint32_t max_meas;
+    uint32_t max_ops;
+    const float *noise;         // concatenated noise vectors
+    uint32_t pad[2];
+};
+
+// device status block (read back by the host after every compile)
+struct Status {
+    uint32_t code;              // first gp_status error reported
+    uint32_t info[3];
+    uint32_t n_mech;            // total mechanisms (lowering)
+    uint32_t n_edges;           // hyperedges
+    uint32_t n_det_entries;
+    uint32_t n_scan_blocks;
+    uint32_t queue_head;        // stage-1 work queue
+    uint32_t queue_done;        // stage-1 finished blocks
+    uint32_t pad[6];
+};
+
+// all device buffers of a driver (pointers into the workspace)
+struct Buffers {
+    Params *params;
+    CircuitDev *circ;
+    uint2 *tiles;               // {circuit, first row}
+    uint32_t *items;            // stage-1 work order: global column ids
+    uint32_t *col_circ;         // circuit of each global column
+    uint4 *ops_arena;
+    uint32_t *recs_arena;
+    float *noise_arena;
+    uint32_t *aux;              // per row (indexed by op_base + row)
+    uint4 *tile_sums, *tile_off;
+    uint32_t *layer_start;      // per circuit: n_layers + 1 row offsets
+    uint32_t *meas_layer;       // per measurement: its layer
+    uint32_t *det_row;          // per detector: its row
+    uint32_t *obs_rows;         // per circuit (at op_base): OBSERVABLE rows
+    uint32_t *obs_count;        // per circuit
+    uint32_t *mech_cnt;         // per mechanism: mask words received
+    unsigned long long *mech_info;   // loc | kind << 32 | comp << 40 | circuit << 48
+    uint32_t *slot_col;         // [mech][S] column ids (kObsColFlag on obs)
+    unsigned long long *slot_word;   // [mech][S] mask words
+    uint32_t *slot_of;          // per mechanism: hash-table slot or kNone
+    int32_t *mech_class;        // per mechanism: edge or -1
+    unsigned long long *table;  // hash table entries (key_hi << 32 | rep)
+    uint32_t *tab_min;          // smallest member per slot
+    unsigned long long *tab_acc;// 128-bit fixed-point sums (lo, hi) per slot
+    uint32_t *tab_class;        // edge per slot
+    uint2 *blk_sums, *blk_off;  // compaction scan
+    uint32_t *det_off;          // n_edges + 1
+    uint32_t *det_idx;
+    unsigned long long *obs_mask;
+    float *prob, *logodds;
+    uint32_t *class_slot, *edge_circ;
+    uint32_t *circ_edges;       // per circuit edge counts
+    unsigned long long *gacc;   // adjoint accumulators (lo, hi) per location
+    Status *status;
+};
+
+// ---------------------------------------------------------------------------
+// row kinds (flat format)
+// ---------------------------------------------------------------------------
+enum Kind : uint32_t {
+    K_TICK = 0, K_R = 1, K_M = 2, K_MR = 3, K_RX = 4, K_MX = 5, K_MRX = 6,
+    K_H = 8, K_S = 9, K_CX = 10, K_CZ = 11, K_DET = 16, K_OBS = 17,
+    K_XERR = 32, K_ZERR = 33, K_DEP1 = 34, K_DEP2 = 35
+};
+
+__host__ __device__ inline bool is_measure(uint32_t k) {
+    return k == K_M || k == K_MR || k == K_MX || k == K_MRX;
+}
+__host__ __device__ inline bool is_noise(uint32_t k) { return k >= K_XERR && k <= K_DEP2; }
+__host__ __device__ inline bool is_gate1(uint32_t k) { return (k >= K_R && k <= K_MRX) || k == K_H || k == K_S; }
+__host__ __device__ inline bool is_gate2(uint32_t k) { return k == K_CX || k == K_CZ; }
+__host__ __device__ inline bool is_gate(uint32_t k) { return is_gate1(k) || is_gate2(k); }
+
+// number of Pauli components a noise row contributes at a level
+__host__ __device__ inline uint32_t n_comp(uint32_t kind, uint32_t level) {
+    switch (kind) {
+    case K_XERR: case K_ZERR: return 1;
+    case K_DEP1: return level == 0 ? 2u : 3u;
+    case K_DEP2: return level == 0 ? 6u : (level == 1 ? 10u : 15u);
+    default: return 0;
+    }
+}
+
+// Which plane words make up component c: bit0 = X plane of the first qubit,
+// bit1 = Z plane of the first qubit, bit2 / bit3 the same for the second.
+// One-qubit depolarising: X, Z, Y.  Two-qubit: the level-0 terms
+// IX IZ XI XX ZI ZZ, then the level-1 terms IY XZ YI ZX, then the level-2
+// terms XY YX YY YZ ZY (Table tab:correlation-level).
+__device__ __forceinline__ uint32_t comp_planes(uint32_t kind, uint32_t c) {
+    // packed 4-bit codes, component 0 in the lowest nibble
+    const unsigned long long dep2 = 0x0EBF7D639CA25184ull;  // IX..ZY as listed above
+    switch (kind) {
+    case K_XERR: return 1u;
+    case K_ZERR: return 2u;
+    case K_DEP1: return (0x321u >> (4 * c)) & 0xFu;
+    default: return (uint32_t)((dep2 >> (4 * c)) & 0xFull);
+    }
+}
+
+// t = -log(1 - 2 q) of one component of a channel with parameter p.  With
+// the independent-component decomposition 1 - 2q = (1 - c p)^(1/k):
+// X/Z errors c = 2, k = 1; DEPOLARIZE1 c = 4/3, k = 2; DEPOLARIZE2 c = 16/15,
+// k = 8.
+__device__ __forceinline__ void channel_ck(uint32_t kind, float &c, float &k) {
+    switch (kind) {
+    case K_DEP1: c = 4.0f / 3.0f; k = 2.0f; break;
+    case K_DEP2: c = 16.0f / 15.0f; k = 8.0f; break;
+    default: c = 2.0f; k = 1.0f; break;
+    }
+}
+__device__ __forceinline__ float channel_pmax(uint32_t kind) {
+    return kind == K_DEP1 ? 0.75f : (kind == K_DEP2 ? 0.9375f : 0.5f);
+}
+
+// ---------------------------------------------------------------------------
+// status reporting: the first error wins
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void report(Status *st, uint32_t code, uint32_t a, uint32_t b, uint32_t c) {
+    if (atomicCAS(&st->code, 0u, code) == 0u) {
+        st->info[0] = a;
+        st->info[1] = b;
+        st->info[2] = c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exact 128-bit fixed-point accumulation (scheduling-independent sums)
+// ---------------------------------------------------------------------------
+// value v >= 0 as an unsigned integer v * 2^shift, split (lo, hi)
+__device__ __forceinline__ void to_fixed(float v, int shift, unsigned long long &lo, unsigned long long &hi) {
+    lo = 0; hi = 0;
+    if (!(v > 0.0f)) return;
+    int e;
+    float f = frexpf(v, &e);                        // v = f * 2^e, f in [0.5, 1)
+    unsigned long long mant = (unsigned long long)ldexpf(f, 24);  // 24-bit integer
+    int s = e - 24 + shift;                         // v * 2^shift = mant * 2^s
+    if (s <= -64) return;
+    if (s < 0) { lo = mant >> (-s); return; }
+    if (s < 64) {
+        lo = mant << s;
+        hi = (s == 0) ? 0ull : (mant >> (64 - s));
+        if (s + 24 <= 64) hi = 0ull;
+    } else if (s < 128) {
+        hi = mant << (s - 64);
+    } else {
+        hi = 0x7FFFFFFFFFFFFFFFull;                 // saturate (not reached for clamped inputs)
+    }
+}
+
+__device__ __forceinline__ void acc128_add(unsigned long long *acc, unsigned long long lo, unsigned long long hi) {
+    if (lo) {
+        unsigned long long old = atomicAdd(&acc[0], lo);
+        if (old + lo < old) hi += 1ull;             // carry out of the low word
+    }
+    if (hi) atomicAdd(&acc[1], hi);
+}
+
+// signed: two's complement modulo 2^128
+__device__ __forceinline__ void acc128_add_signed(unsigned long long *acc, float v, int shift) {
+    unsigned long long lo, hi;
+    to_fixed(fabsf(v), shift, lo, hi);
+    if (v < 0.0f) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    acc128_add(acc, lo, hi);
+}
+
+__device__ __forceinline__ float fixed_to_float(unsigned long long lo, unsigned long long hi, int shift) {
+    return ldexpf((float)hi, 64 - shift) + ldexpf((float)lo, -shift);
+}
+
+__device__ __forceinline__ float fixed_to_float_signed(unsigned long long lo, unsigned long long hi, int shift) {
+    bool neg = (hi >> 63) != 0ull;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    float v = fixed_to_float(lo, hi, shift);
+    return neg ? -v : v;
+}
+
+constexpr int kProbShift = 96;   // class sums of t = -log(1-2q): 2^-96 resolution
+constexpr int kGradShift = 64;   // adjoint sums: 2^-64 resolution
+
+// ---------------------------------------------------------------------------
+// hashing of masks (any well-mixed 64-bit function works: grouping verifies
+// whole masks).  Finaliser of splitmix64 (Steele, Lea and Flood 2014).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan of uint32 (blockDim.x a multiple of 32, <= 1024)
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *smem_warp, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < NT / 32) ? smem_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) smem_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t warp_prefix = warp ? smem_warp[warp - 1] : 0u;
+    total = smem_warp[NT / 32 - 1];
+    __syncthreads();
+    return warp_prefix + x - v;
+}
+
+}  // namespace gpdem
+
+// kernel entry points (implemented in lower.cu, stage1.cu, stage2.cu)
+namespace gpdem {
+void launch_lowering(const Buffers &b, uint32_t max_tiles, uint32_t n_tiles, cudaStream_t s, uint32_t *launches);
+void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_qubits, cudaStream_t s, uint32_t *launches);
+size_t stage1_smem_bytes(uint32_t max_qubits);
+const void *stage1_kernel_ptr(uint32_t threads);
+void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
+void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_scan_blocks, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
+void launch_backward(const Buffers &b, const float *g_prob, const float *g_logodds, float *g_noise,
+                     uint32_t n_mech, uint32_t n_loc, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches);
+}  // namespace gpdem

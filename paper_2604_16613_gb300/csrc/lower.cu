@@ -1,0 +1,216 @@
+// lower.cu -- device-side lowering of flat circuit rows (Sec. 2.3.1: the
+// realised circuit is lowered to a layered space-time structure before the
+// backward wave runs).
+//
+// Three launches, no device-wide waits:
+//   tile_count   per tile of 4096 rows: counts of TICKs, measurements,
+//                detectors and mechanisms (components at the chosen level)
+//   tile_scan    one block: per-circuit scan of the tile counts, circuit
+//                totals and batch offsets, capacity checks
+//   tile_lower   per tile: exclusive row scan, validation of every row and
+//                the scatters stage 1 reads (layer starts, record layers,
+//                detector rows, observable rows, per-row auxiliary index)
+#include "common.cuh"
+
+namespace gpdem {
+
+namespace {
+
+constexpr int kRowsPerThread = kRowTile / kLowerThreads;
+
+__device__ __forceinline__ uint4 row_counts(uint4 op, uint32_t level) {
+    uint4 c = make_uint4(0, 0, 0, 0);
+    const uint32_t k = op.x;
+    c.x = (k == K_TICK);
+    c.y = is_measure(k);
+    c.z = (k == K_DET);
+    c.w = is_noise(k) ? n_comp(k, level) : 0u;
+    return c;
+}
+
+__device__ __forceinline__ uint4 add4(uint4 a, uint4 b) {
+    return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__global__ void __launch_bounds__(kLowerThreads) tile_count_kernel(Buffers B) {
+    const Params &P = *B.params;
+    const uint32_t t = blockIdx.x;
+    if (t >= P.n_tiles) return;
+    const uint2 tile = B.tiles[t];
+    const CircuitDev &C = B.circ[tile.x];
+    const uint32_t r0 = tile.y + threadIdx.x * kRowsPerThread;
+    const uint32_t r1 = min(r0 + kRowsPerThread, C.n_ops);
+    uint4 acc = make_uint4(0, 0, 0, 0);
+    for (uint32_t r = r0; r < r1; r++) acc = add4(acc, row_counts(C.ops[r], P.level));
+    // block reduction of four counters
+    __shared__ uint4 red[kLowerThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_down_sync(0xFFFFFFFFu, acc.x, o);
+        acc.y += __shfl_down_sync(0xFFFFFFFFu, acc.y, o);
+        acc.z += __shfl_down_sync(0xFFFFFFFFu, acc.z, o);
+        acc.w += __shfl_down_sync(0xFFFFFFFFu, acc.w, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint4 s = make_uint4(0, 0, 0, 0);
+        for (int w = 0; w < kLowerThreads / 32; w++) s = add4(s, red[w]);
+        B.tile_sums[t] = s;
+    }
+}
+
+// One block.  Thread b scans the tiles of circuit b (tiles of a circuit are
+// contiguous); then block scans give the batch offsets.
+__global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
+    const Params &P = *B.params;
+    __shared__ uint32_t warp_tmp[kLowerThreads / 32];
+    __shared__ uint32_t carry_layer, carry_meas, carry_mech;
+    if (threadIdx.x == 0) { carry_layer = 0; carry_meas = 0; carry_mech = 0; }
+    __syncthreads();
+    for (uint32_t base = 0; base < P.n_circuits; base += kLowerThreads) {
+        const uint32_t b = base + threadIdx.x;
+        uint32_t layers = 0, meas = 0, mech = 0;
+        if (b < P.n_circuits) {
+            CircuitDev &C = B.circ[b];
+            uint4 run = make_uint4(0, 0, 0, 0);
+            for (uint32_t t = C.tile_first; t < C.tile_first + C.n_tiles; t++) {
+                B.tile_off[t] = run;
+                run = add4(run, B.tile_sums[t]);
+            }
+            if (run.z != C.n_det) report(B.status, GP_ERR_INVALID, 1u, b, run.z);
+            C.n_layers = run.x + 1;
+            C.n_meas = run.y;
+            C.n_mech = run.w;
+            layers = C.n_layers + 1;       // row offsets incl. the end sentinel
+            meas = run.y;
+            mech = run.w;
+            B.obs_count[b] = 0;
+            B.circ_edges[b] = 0;
+        }
+        uint32_t tot_l, tot_m, tot_x;
+        const uint32_t off_l = block_exclusive_scan<kLowerThreads>(layers, warp_tmp, tot_l);
+        const uint32_t off_m = block_exclusive_scan<kLowerThreads>(meas, warp_tmp, tot_m);
+        const uint32_t off_x = block_exclusive_scan<kLowerThreads>(mech, warp_tmp, tot_x);
+        if (b < P.n_circuits) {
+            CircuitDev &C = B.circ[b];
+            C.layer_base = carry_layer + off_l;
+            C.meas_base = carry_meas + off_m;
+            C.mech_base = carry_mech + off_x;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // 64-bit guards against wrap before comparing with the bounds
+            const unsigned long long L = (unsigned long long)carry_layer + tot_l;
+            const unsigned long long Mm = (unsigned long long)carry_meas + tot_m;
+            const unsigned long long X = (unsigned long long)carry_mech + tot_x;
+            carry_layer = (uint32_t)min(L, 0xFFFFFFFFull);
+            carry_meas = (uint32_t)min(Mm, 0xFFFFFFFFull);
+            carry_mech = (uint32_t)min(X, 0xFFFFFFFFull);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (carry_layer > P.max_layer_slots) report(B.status, GP_ERR_CAPACITY, 1u, carry_layer, P.max_layer_slots);
+        if (carry_meas > P.max_meas) report(B.status, GP_ERR_CAPACITY, 2u, carry_meas, P.max_meas);
+        if (carry_mech > P.max_mech) report(B.status, GP_ERR_CAPACITY, 3u, carry_mech, P.max_mech);
+        B.status->n_mech = carry_mech;
+    }
+    // layer 0 starts at row 0; the sentinel after the last layer is n_ops
+    __syncthreads();
+    if (B.status->code == 0) {
+        for (uint32_t b = threadIdx.x; b < P.n_circuits; b += kLowerThreads) {
+            const CircuitDev &C = B.circ[b];
+            B.layer_start[C.layer_base] = 0;
+            B.layer_start[C.layer_base + C.n_layers] = C.n_ops;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
+    const Params &P = *B.params;
+    const uint32_t t = blockIdx.x;
+    if (t >= P.n_tiles) return;
+    if (B.status->code != 0) return;
+    const uint2 tile = B.tiles[t];
+    const uint32_t b = tile.x;
+    const CircuitDev &C = B.circ[b];
+    const uint32_t r0 = tile.y + threadIdx.x * kRowsPerThread;
+    const uint32_t r1 = min(r0 + kRowsPerThread, C.n_ops);
+    uint4 mine = make_uint4(0, 0, 0, 0);
+    for (uint32_t r = r0; r < r1; r++) mine = add4(mine, row_counts(C.ops[r], P.level));
+    __shared__ uint32_t warp_tmp[kLowerThreads / 32];
+    uint32_t tot;
+    const uint4 toff = B.tile_off[t];
+    uint4 run;
+    run.x = block_exclusive_scan<kLowerThreads>(mine.x, warp_tmp, tot) + toff.x;
+    run.y = block_exclusive_scan<kLowerThreads>(mine.y, warp_tmp, tot) + toff.y;
+    run.z = block_exclusive_scan<kLowerThreads>(mine.z, warp_tmp, tot) + toff.z;
+    run.w = block_exclusive_scan<kLowerThreads>(mine.w, warp_tmp, tot) + toff.w;
+    for (uint32_t r = r0; r < r1; r++) {
+        const uint4 op = C.ops[r];
+        const uint32_t k = op.x;
+        const uint32_t ticks = run.x, meas = run.y, dets = run.z, mech = run.w;
+        uint32_t aux = 0;
+        bool bad = false;
+        switch (k) {
+        case K_TICK:
+            B.layer_start[C.layer_base + ticks + 1] = r + 1;
+            break;
+        case K_R: case K_RX: case K_H: case K_S:
+            bad = op.y >= C.n_qubits;
+            break;
+        case K_M: case K_MR: case K_MX: case K_MRX:
+            bad = op.y >= C.n_qubits;
+            aux = meas;
+            if (!bad) B.meas_layer[C.meas_base + meas] = ticks;
+            break;
+        case K_CX: case K_CZ:
+            bad = op.y >= C.n_qubits || op.z >= C.n_qubits || op.y == op.z;
+            break;
+        case K_DET: case K_OBS: {
+            bad = (unsigned long long)op.y + op.z > C.n_recs;
+            if (!bad) {
+                for (uint32_t i = 0; i < op.z; i++) {
+                    const uint32_t lb = C.recs[op.y + i];
+                    if (lb == 0 || lb > meas) { bad = true; break; }
+                }
+            }
+            if (k == K_OBS && op.w >= C.n_obs) bad = true;
+            aux = meas;
+            if (!bad) {
+                if (k == K_DET) B.det_row[C.det_base + dets] = r;
+                else B.obs_rows[C.op_base + atomicAdd(&B.obs_count[b], 1u)] = r;
+            }
+            break;
+        }
+        case K_XERR: case K_ZERR: case K_DEP1:
+            bad = op.y >= C.n_qubits || op.w >= C.n_loc;
+            aux = mech;
+            break;
+        case K_DEP2:
+            bad = op.y >= C.n_qubits || op.z >= C.n_qubits || op.y == op.z || op.w >= C.n_loc;
+            aux = mech;
+            break;
+        default:
+            bad = true;
+            break;
+        }
+        if (bad) report(B.status, GP_ERR_INVALID, 2u, b, r);
+        B.aux[C.op_base + r] = aux;
+        run = add4(run, row_counts(op, P.level));
+    }
+}
+
+}  // namespace
+
+void launch_lowering(const Buffers &b, uint32_t max_tiles, uint32_t n_tiles, cudaStream_t s, uint32_t *launches) {
+    const uint32_t grid = n_tiles ? n_tiles : 1u;
+    (void)max_tiles;
+    tile_count_kernel<<<grid, kLowerThreads, 0, s>>>(b);
+    tile_scan_kernel<<<1, kLowerThreads, 0, s>>>(b);
+    tile_lower_kernel<<<grid, kLowerThreads, 0, s>>>(b);
+    *launches += 3;
+}
+
+}  // namespace gpdem

@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA library against the FP64 oracle, through the C ABI.
+
+Masks (hyperedge keys) must match bit-exactly; probabilities within 1e-5
+relative; gradients within 1e-4 relative (or 1e-6 of the largest entry).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle
+from paper_2604_16613_gb300 import circuits as C
+from paper_2604_16613_gb300 import native
+from paper_2604_16613_gb300.dem import Bounds, DeviceCircuit, Driver
+
+from parity import compare_edges, oracle_edges
+
+pytestmark = pytest.mark.gpu
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32)
+
+
+def run(circ, noise, level="L2", device=True, drv=None):
+    drv = drv or Driver.for_circuits([circ])
+    if device:
+        dem = drv.compile(DeviceCircuit(circ), torch.tensor(f32(noise), device="cuda"), level)
+    else:
+        dem = drv.compile(circ, f32(noise), level)
+    return drv, dem
+
+
+CODES = [
+    ("fig1", lambda: C.repetition_code_memory(3, 2, C.NoiseModel.uniform(1e-3), final_data=False)),
+    ("rep5", lambda: C.repetition_code_memory(5, 5, C.NoiseModel.hardware_inspired(1e-2))),
+    ("surf3", lambda: C.rotated_surface_code_memory(3, 3, C.NoiseModel.uniform(1e-3))),
+    ("surf4", lambda: C.rotated_surface_code_memory(4, 4, C.NoiseModel.uniform(2e-3))),
+    ("surf5", lambda: C.rotated_surface_code_memory(5, 5, C.NoiseModel.hardware_inspired(1e-3))),
+    ("surf7", lambda: C.rotated_surface_code_memory(7, 7, C.NoiseModel.uniform(1e-3))),
+]
+
+
+@pytest.mark.parametrize("name,make", CODES, ids=[c[0] for c in CODES])
+@pytest.mark.parametrize("level", ["L0", "L1", "L2"])
+def test_codes_parity(name, make, level):
+    circ = make()
+    noise = C.log_uniform_noise(circ.n_locations, seed=3)
+    _, dem = run(circ, noise, level)
+    ref = oracle_edges(circ, noise, level)
+    compare_edges(dem.edges(), ref.edges(), f"{name}/{level}")
+    assert dem.n_edges == ref.n_classes
+
+
+def test_host_and_device_inputs_agree():
+    circ = C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))
+    noise = C.log_uniform_noise(circ.n_locations, seed=4)
+    drv, d1 = run(circ, noise, device=True)
+    h1 = d1.to_host()
+    _, d2 = run(circ, noise, device=False, drv=drv)
+    h2 = d2.to_host()
+    for k in ("det_offsets", "det_idx", "obs_mask", "prob", "logodds"):
+        assert np.array_equal(h1[k], h2[k]), k
+
+
+def test_repeated_compiles_bit_identical():
+    circ = C.rotated_surface_code_memory(7, 7, C.NoiseModel.uniform(1e-3))
+    noise = C.log_uniform_noise(circ.n_locations, seed=5)
+    drv = Driver.for_circuits([circ])
+    dc = DeviceCircuit(circ)
+    nz = torch.tensor(f32(noise), device="cuda")
+    outs = [drv.compile(dc, nz).to_host() for _ in range(3)]
+    for o in outs[1:]:
+        for k in o:
+            assert np.array_equal(o[k], outs[0][k]), k
+
+
+def test_random_circuits_parity():
+    for seed in range(240):
+        circ = C.random_circuit(seed)
+        noise = circ.default_noise
+        level = ["L0", "L1", "L2"][seed % 3]
+        _, dem = run(circ, noise, level)
+        compare_edges(dem.edges(), oracle_edges(circ, noise, level).edges(), f"seed {seed}")
+
+
+def test_batch_matches_individual_and_oracle():
+    circs = [C.random_circuit(1000 + s) for s in range(40)]
+    circs += [C.rotated_surface_code_memory(3, 3, C.NoiseModel.uniform(1e-3)),
+              C.repetition_code_memory(5, 3, C.NoiseModel.uniform(1e-3))]
+    noises = [c.default_noise for c in circs]
+    drv = Driver.for_circuits(circs)
+    dem = drv.compile(circs, f32(np.concatenate(noises)))
+    host = dem.to_host()
+    assert dem.n_circuits == len(circs)
+    for b, (c, nz) in enumerate(zip(circs, noises)):
+        got = dem.edges(b, host)
+        compare_edges(got, oracle_edges(c, nz).edges(), f"batch circuit {b}")
+        solo = Driver.for_circuits([c]).compile(c, f32(nz)).edges()
+        assert got == solo, f"circuit {b}: result differs alone and in the batch"
+
+
+@pytest.mark.parametrize("d", [11, 15])
+def test_surface_parity_large(d):
+    circ = C.rotated_surface_code_memory(d, d, C.NoiseModel.uniform(1e-3))
+    noise = C.log_uniform_noise(circ.n_locations, seed=2)
+    _, dem = run(circ, noise)
+    ref = oracle_edges(circ, noise)
+    compare_edges(dem.edges(), ref.edges(), f"d={d}")
+
+
+def test_surface_d25_full_size():
+    """The benchmark's workload (d = 25, 25 rounds, log-uniform noise, L2) in
+    the benchmark's launch configuration, compared with the oracle on every
+    hyperedge."""
+    circ = C.rotated_surface_code_memory(25, 25, C.NoiseModel.uniform(1e-3))
+    noise = C.log_uniform_noise(circ.n_locations, seed=2)
+    _, dem = run(circ, noise)
+    ref = oracle_edges(circ, noise)
+    assert dem.n_edges == ref.n_classes
+    wp, _ = compare_edges(dem.edges(), ref.edges(), "d=25")
+    assert wp <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_noiseless_and_detectorless_circuits():
+    c = C.rotated_surface_code_memory(3, 2, None)          # no noise rows
+    _, dem = run(c, np.zeros(0))
+    assert dem.n_edges == 0
+    c2 = C.Circuit(2)                                        # noise, nothing to flip
+    c2.gate1(C.R, [0, 1]); c2.tick()
+    c2.noise(C.DEPOLARIZE1, [0, 1], 0.01)
+    c2.measure(C.M, [0])
+    _, dem2 = run(c2, c2.default_noise)
+    assert dem2.n_edges == 0
+
+
+def test_zero_probability_locations_are_dropped():
+    circ = C.rotated_surface_code_memory(3, 3, C.NoiseModel.uniform(1e-3))
+    noise = C.log_uniform_noise(circ.n_locations, seed=6)
+    noise[::3] = 0.0
+    _, dem = run(circ, noise)
+    compare_edges(dem.edges(), oracle_edges(circ, noise).edges(), "p=0")
+
+
+def test_saturated_x_error():
+    c = C.Circuit(1)
+    c.gate1(C.R, [0]); c.tick()
+    c.noise(C.X_ERROR, [0], 0.5)
+    c.noise(C.X_ERROR, [0], 0.01)
+    rec = c.measure(C.M, [0])
+    c.detector([rec[0]])
+    _, dem = run(c, c.default_noise)
+    (e, (P, w)), = dem.edges().items()
+    assert e == ((0,), 0)
+    assert P == pytest.approx(0.5, abs=1e-7) and abs(w) < 1e-6
+
+
+def expect_error(code, fn):
+    with pytest.raises(native.GpError) as ex:
+        fn()
+    assert ex.value.code == code, str(ex.value)
+    return str(ex.value)
+
+
+def test_error_paths_and_recovery():
+    good = C.rotated_surface_code_memory(3, 3, C.NoiseModel.uniform(1e-3))
+    noise = good.default_noise
+    drv = Driver(Bounds.for_circuits([good], slack=2.0))
+    # non-deterministic detector: X-basis reset measured in Z
+    nd = C.Circuit(good.n_qubits)
+    nd.gate1(C.RX, [0]); nd.tick()
+    r = nd.measure(C.M, [0])
+    nd.detector([r[0]])
+    msg = expect_error(native.GP_ERR_NONDETERMINISTIC, lambda: drv.compile(nd, np.zeros(0)))
+    assert "anticommutes" in msg
+    # qubit out of range
+    bad = C.Circuit.from_text(good.to_text())
+    ops = bad.ops.copy()
+    ops[0, 1] = good.n_qubits + 5
+    bad._frozen = (ops, bad.recs, bad.default_noise)
+    expect_error(native.GP_ERR_INVALID, lambda: drv.compile(bad, noise))
+    # two gates on one qubit in one layer
+    two = C.Circuit(2)
+    two.gate1(C.R, [0, 1]); two.tick()
+    two.gate1(C.H, [0]); two.gate1(C.H, [0]); two.tick()
+    rr = two.measure(C.M, [1])
+    two.detector([rr[0]])
+    two.noise(C.X_ERROR, [1], 0.01)
+    expect_error(native.GP_ERR_INVALID, lambda: drv.compile(two, two.default_noise))
+    # noise outside the channel's range
+    nz = noise.copy()
+    nz[5] = 0.9
+    expect_error(native.GP_ERR_INVALID, lambda: drv.compile(good, nz))
+    # detector count in the header disagrees with the rows
+    wrong = C.Circuit.from_text(good.to_text())
+    wrong.n_detectors += 1
+    expect_error(native.GP_ERR_INVALID, lambda: drv.compile(wrong, noise))
+    # mask wider than the slot bound
+    wide = C.rotated_surface_code_memory(11, 2, C.NoiseModel.uniform(1e-3))
+    small2 = Driver(Bounds(**{**Bounds.for_circuits([wide]).__dict__, "max_mask_words": 1}))
+    expect_error(native.GP_ERR_CAPACITY, lambda: small2.compile(wide, wide.default_noise))
+    # too many circuits for the bounds
+    expect_error(native.GP_ERR_CAPACITY, lambda: drv.compile([good, good], np.concatenate([noise, noise])))
+    # the drivers still work after every failure
+    for dv in (drv, small2):
+        ok = dv.compile(good, f32(noise)).edges()
+        compare_edges(ok, oracle_edges(good, noise).edges(), "after errors")
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_gradient_matches_oracle(d):
+    circ = C.rotated_surface_code_memory(d, d, C.NoiseModel.uniform(1e-3))
+    noise = f32(C.log_uniform_noise(circ.n_locations, seed=9))
+    drv = Driver.for_circuits([circ])
+    dem = drv.compile(DeviceCircuit(circ), torch.tensor(noise, device="cuda"))
+    host = dem.to_host()
+    ref = oracle_edges(circ, noise)
+    keys_ref = [ref.split_ids(ref.class_ids(c)) for c in range(ref.n_classes)]
+    rng = np.random.default_rng(d)
+    gP_ref = rng.normal(size=ref.n_classes)
+    gW_ref = rng.normal(size=ref.n_classes) * 1e-3
+    index = {k: i for i, k in enumerate(keys_ref)}
+    keys_gpu = list(dem.edges(0, host).keys())
+    order = np.array([index[k] for k in keys_gpu])
+    g_gpu = drv.backward(torch.tensor(gP_ref[order], dtype=torch.float32, device="cuda"),
+                         torch.tensor(gW_ref[order], dtype=torch.float32, device="cuda")).cpu().numpy()
+    g_ref = ref.gradient(gP_ref.astype(np.float32).astype(np.float64),
+                         gW_ref.astype(np.float32).astype(np.float64), circ.n_locations)
+    floor = 1e-6 * np.abs(g_ref).max()
+    err = np.abs(g_gpu - g_ref)
+    bad = err > 1e-4 * np.abs(g_ref) + floor
+    assert not bad.any(), f"{bad.sum()} locations off; worst {err.max():.3g}"
