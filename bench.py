@@ -1,0 +1,356 @@
+"""Benchmark: error mechanisms per second of a plain d = 25 surface-code compile.
+
+Workload (one step): rotated surface code Z-memory, distance 25, 25 rounds,
+fully unrolled, circuit-level noise after every layer with per-location
+probabilities exp(U[ln 1e-4, ln 3e-3]) (seed 2), level L2; one full compile
+(lowering, stage 1, grouping and reduction, compaction) through the C ABI
+with the circuit and noise already in device memory.  L2 is flushed (a
+256 MiB write) between timed steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the same workload instead.  With WORLD_SIZE > 1 (torchrun) every rank
+compiles its own copy of the workload (independent replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "error mechanisms/s (plain GPU compile, rotated surface code d=25)"
+UNIT = "mechanisms/s"
+WORKLOAD = "rotated surface code Z-memory d=25, 25 rounds, log-uniform p in [1e-4, 3e-3], level L2"
+
+
+def make_workload(d: int = 25):
+    from paper_2604_16613_gb300 import circuits as C
+    circ = C.rotated_surface_code_memory(d, d, C.NoiseModel.uniform(1e-3))
+    noise = C.log_uniform_noise(circ.n_locations, seed=2).astype(np.float32)
+    return circ, noise
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def mask_word_count(host: dict, mech_class: np.ndarray) -> int:
+    """Sum over mechanisms of the 64-bit words in their masks (from the
+    compiled classes: members of a class share its mask)."""
+    off, idx, obs = host["det_offsets"], host["det_idx"], host["obs_mask"]
+    words = np.zeros(len(off) - 1, dtype=np.int64)
+    for e in range(len(off) - 1):
+        words[e] = len(set((idx[off[e]:off[e + 1]] // 64).tolist())) + (1 if obs[e] else 0)
+    sizes = np.bincount(mech_class[mech_class >= 0], minlength=len(words))
+    return int((words * sizes).sum())
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lower.cu", "stage1.cu", "stage2.cu", "api.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2604_16613_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return float(ent["dram_bytes_per_launch"])
+
+
+def peaks() -> tuple[float, str]:
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(mp["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(circ, noise, budget_s: float = 12.0, max_runs: int = 40) -> dict:
+    """The CPU oracle as it stands, one core, on the same workload."""
+    import oracle
+    oracle.build()
+    n64 = noise.astype(np.float64)
+    runs, t0, nm = 0, time.perf_counter(), 0
+    while True:
+        dem = oracle.analyze_circuit(circ, n64, "L2")
+        nm += dem.n_mechanisms
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or runs >= max_runs:
+            break
+    return {"value": nm / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{runs} full oracle compiles of the d=25 workload ({el:.1f} s, 1 thread, "
+                      f"{platform.machine()} host)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    circ, noise = make_workload()
+    import oracle
+    oracle.build()
+    n64 = noise.astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.analyze_circuit(circ, n64, "L2")
+    times, nm = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        dem = oracle.analyze_circuit(circ, n64, "L2")
+        times.append(time.perf_counter() - t0)
+        nm = dem.n_mechanisms
+    total = sum(times)
+    value = nm * args.steps / total
+    per_cycle = np.array(times) / 25 * 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "per_cycle_us": {"p50": float(np.percentile(per_cycle, 50)), "p99": float(np.percentile(per_cycle, 99))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full oracle compiles of the d=25 workload, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    from paper_2604_16613_gb300 import build as pbuild
+    from paper_2604_16613_gb300.dem import DeviceCircuit, Driver
+    pbuild.build()
+
+    circ, noise = make_workload()
+    drv = Driver.for_circuits([circ])
+    dc = DeviceCircuit(circ)
+    nz = torch.tensor(noise, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    drv.enable_timing(True)
+
+    for _ in range(max(args.warmup, 3)):
+        dem = drv.compile(dc, nz)
+    n_mech_total = dem.n_mechanisms
+    n_edges = dem.n_edges
+    host = dem.to_host()
+    mclass = dem.mech_class.cpu().numpy()
+    n_mech = int((mclass >= 0).sum())          # mechanisms that enter the DEM
+    launches_per_step = drv.last_launch_count()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    step_ms, stage_us = [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ev0.record(stream)
+        drv.compile(dc, nz)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        stage_us.append(drv.last_timing())
+    barrier()
+    clocks = sampler.stop()
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n_mech * args.steps / (total_ms / 1e3)
+    per_cycle = np.array(step_ms) * 1e3 / 25
+
+    # per-stage device times (CUDA events on the compile's stream)
+    st = np.array(stage_us)
+    stage_names = ["lowering", "stage1", "group", "compact"]
+    stage_mean = {n: float(st[:, i].mean()) for i, n in enumerate(stage_names)}
+    dom = max(stage_mean, key=stage_mean.get)
+
+    # algorithmic bytes (per launch of each stage; definitions in the design doc)
+    words = mask_word_count(host, mclass)
+    n_ops, n_recs = circ.n_ops, int(circ.recs.size)
+    b_in = 16 * n_ops + 4 * n_recs + 4 * circ.n_locations
+    alg = {
+        "lowering": 16 * n_ops * 2 + 4 * n_recs + 4 * n_ops,
+        "stage1": 16 * n_ops + 4 * n_recs + 12 * words + 12 * n_mech,
+        "group": 4 * n_mech_total + 12 * words + 8 * n_mech + 4 * n_mech,
+        "compact": 4 * n_mech_total * 2 + 12 * words + n_edges * 24 + 4 * host["det_idx"].size,
+    }
+    hbm_peak, peak_kind = peaks()
+    achieved = alg[dom] / (stage_mean[dom] * 1e-6) / 1e9
+    b_alg_pipeline = b_in + n_mech * 32 + 2 * 12 * words + n_edges * 16 + 4 * host["det_idx"].size
+    kernel_name = {"stage1": "stage1_kernel", "group": "group_kernel", "lowering": "tile_lower_kernel",
+                   "compact": "compact_write_kernel"}[dom]
+    traffic = measured_traffic(kernel_name)
+
+    # end to end through the C ABI with host buffers: H2D of the circuit and
+    # noise, compile, D2H of the hyperedges into pinned host memory
+    e2e_steps = max(10, min(args.steps, 200))
+    pinned = {
+        "det_offsets": torch.empty(n_edges + 1, dtype=torch.int32, pin_memory=True),
+        "det_idx": torch.empty(int(host["det_idx"].size), dtype=torch.int32, pin_memory=True),
+        "obs": torch.empty(n_edges, dtype=torch.int64, pin_memory=True),
+        "prob": torch.empty(n_edges, dtype=torch.float32, pin_memory=True),
+        "logodds": torch.empty(n_edges, dtype=torch.float32, pin_memory=True),
+    }
+    d2h = sum(t.numel() * t.element_size() for t in pinned.values())
+    h2d = 16 * n_ops + 4 * n_recs + 4 * circ.n_locations
+    barrier()
+    walls = []
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        dm = drv.compile(circ, noise)
+        pinned["det_offsets"].copy_(dm.det_offsets, non_blocking=True)
+        pinned["det_idx"].copy_(dm.det_idx, non_blocking=True)
+        pinned["obs"].copy_(dm.obs_mask, non_blocking=True)
+        pinned["prob"].copy_(dm.prob, non_blocking=True)
+        pinned["logodds"].copy_(dm.logodds, non_blocking=True)
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - t_a)
+    e2e_time = float(sum(walls))
+    if dist is not None:
+        t = torch.tensor([e2e_time], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_time = float(t.item())
+    e2e_value = world * n_mech * e2e_steps / e2e_time
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64 masks + f32 probabilities", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "qubits": circ.n_qubits, "rows": n_ops,
+                       "detectors": circ.n_detectors, "mechanisms": n_mech,
+                       "mechanisms_incl_empty": n_mech_total, "hyperedges": n_edges,
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "per_cycle_us": {"p50": float(np.percentile(per_cycle, 50)),
+                             "p99": float(np.percentile(per_cycle, 99))},
+            "stage_us": stage_mean,
+            "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm_peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": traffic, "alg_bytes": alg[dom],
+                         "pipeline_alg_bytes": b_alg_pipeline,
+                         "pipeline_frac": b_alg_pipeline / (total_ms / args.steps * 1e-3) / 1e9 / hbm_peak},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(circ, noise)
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -188,7 +188,7 @@ gp_status gp_result_view(const gp_driver *drv, gp_dem_view *out);
 
 /* Tunable launch parameters (picked by the package's autotuner). */
 typedef struct {
-    uint32_t stage1_threads;      /* 128, 256 or 512                          */
+    uint32_t stage1_threads;      /* 128, 256, 512 or 1024                    */
     uint32_t stage1_blocks_per_sm;/* resident blocks per SM for stage 1 (0 = max) */
     uint32_t stage2_threads;      /* 128, 256 or 512                          */
     uint32_t stage2_blocks_per_sm;/* grid = SMs x this for grid-stride kernels */

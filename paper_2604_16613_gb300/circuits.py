@@ -289,9 +289,9 @@ class Circuit:
                 out.append(f"OBSERVABLE_INCLUDE({cc}) " +
                            " ".join(f"rec[-{k}]" for k in recs[a:a + b]))
             elif kind == DEPOLARIZE2:
-                out.append(f"{name}({noise[cc]!r}) {a} {b}")
+                out.append(f"{name}({float(noise[cc])!r}) {a} {b}")
             elif kind in NOISE_KINDS:
-                out.append(f"{name}({noise[cc]!r}) {a}")
+                out.append(f"{name}({float(noise[cc])!r}) {a}")
             elif kind in TWO_QUBIT_GATES:
                 out.append(f"{name} {a} {b}")
             else:

@@ -38,6 +38,7 @@ struct Layout {
     // sizes derived from the bounds
     uint32_t max_tiles, max_cols, max_layer_slots, S, table_log2, max_scan_blocks;
     uint64_t max_det_entries;
+    uint64_t rec_cap;
     // byte offsets in the workspace
     uint64_t total = 0;
     uint64_t params_bytes = 0;   // Params + Status + circuits + tiles + items + col_circ
@@ -77,6 +78,9 @@ Layout make_layout(const gp_bounds &b) {
     L.table_log2 = lg;
     L.max_scan_blocks = (b.max_mechanisms + kMechPerBlockScan - 1) / kMechPerBlockScan;
     L.max_det_entries = b.max_det_entries ? b.max_det_entries : 16ull * b.max_mechanisms;
+    // every mechanism holds at most S words; each stage-1 block may leave
+    // the unused tail of one chunk (at most 1024 resident blocks counted)
+    L.rec_cap = std::min<uint64_t>((uint64_t)b.max_mechanisms * L.S + 1024ull * kChunkRecs, 0xFFFFFFF0ull);
     return L;
 }
 
@@ -97,6 +101,9 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     B.recs_arena = c.take<uint32_t>(std::max<uint64_t>(bd.max_recs, 1));
     B.noise_arena = c.take<float>(std::max<uint32_t>(bd.max_locations, 1));
     B.aux = c.take<uint32_t>(bd.max_ops);
+    B.packed = c.take<uint2>(bd.max_ops + 4);
+    B.layer_seg = c.take<uint4>(L.max_layer_slots + 1);
+    B.records = c.take<uint4>(L.rec_cap);
     B.tile_sums = c.take<uint4>(L.max_tiles);
     B.tile_off = c.take<uint4>(L.max_tiles);
     B.layer_start = c.take<uint32_t>(L.max_layer_slots + 1);
@@ -152,7 +159,7 @@ struct gp_driver {
     std::vector<uint32_t> edge_offsets;
     uint32_t n_loc_total = 0;
     // tuning / instrumentation
-    gp_tuning tuning{256, 0, 256, 4};
+    gp_tuning tuning{512, 0, 256, 8};
     bool timing = false;
     cudaEvent_t ev[5] = {};
     float times[4] = {0, 0, 0, 0};
@@ -168,6 +175,8 @@ gp_status full_reset(gp_driver *d, cudaStream_t s) {
     GP_CUDA(cudaMemsetAsync(d->B.tab_acc, 0, (2 * sizeof(unsigned long long)) << L.table_log2, s));
     GP_CUDA(cudaMemsetAsync(d->B.mech_cnt, 0, sizeof(uint32_t) * (size_t)d->bounds.max_mechanisms, s));
     GP_CUDA(cudaMemsetAsync(d->B.gacc, 0, 2 * sizeof(unsigned long long) * std::max<uint32_t>(d->bounds.max_locations, 1), s));
+    GP_CUDA(cudaMemsetAsync(d->B.records, 0xFF, sizeof(uint4) * L.rec_cap, s));
+    GP_CUDA(cudaMemsetAsync(d->B.packed, 0, sizeof(uint2) * (d->bounds.max_ops + 4), s));
     GP_CUDA(cudaStreamSynchronize(s));
     return GP_OK;
 }
@@ -196,7 +205,7 @@ std::string describe(const Status &st) {
         break;
     case GP_ERR_NONDETERMINISTIC:
         if (b == 0xFFFFFFFFu) snprintf(buf, sizeof buf, "circuit %u: a detector or observable of word column %u anticommutes with the initial |0> state", a, c);
-        else snprintf(buf, sizeof buf, "circuit %u row %u: a detector or observable of word column %u anticommutes with this reset or measurement", a, b, c);
+        else snprintf(buf, sizeof buf, "circuit %u layer %u: a detector or observable of word column %u anticommutes with a reset or measurement", a, b, c);
         break;
     case GP_ERR_CAPACITY:
         if (a == 1) snprintf(buf, sizeof buf, "%u layer slots needed, bound allows %u", b, c);
@@ -206,6 +215,7 @@ std::string describe(const Status &st) {
         else if (a == 5) snprintf(buf, sizeof buf, "word column %u references %u (measurement, detector) pairs; at most %d", b, c, kMaxEntries);
         else if (a == 6) snprintf(buf, sizeof buf, "hash table of %u slots is full", c);
         else if (a == 7) snprintf(buf, sizeof buf, "%u detector ids in the hyperedges, bound allows %u", b, c);
+        else if (a == 8) snprintf(buf, sizeof buf, "mask-word record pool of %u entries is full", c);
         else snprintf(buf, sizeof buf, "capacity exceeded (%u, %u, %u)", a, b, c);
         break;
     default:
@@ -274,7 +284,7 @@ gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace, uint64_t 
     if (st != GP_OK) return cleanup(st);
     // stage-1 shared memory above the default 48 KB
     const size_t smem = stage1_smem_bytes(bounds->max_qubits);
-    for (uint32_t t : {128u, 256u, 512u}) {
+    for (uint32_t t : {128u, 256u, 512u, 1024u}) {
         if (cudaFuncSetAttribute(stage1_kernel_ptr(t), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return cleanup(fail(GP_ERR_CUDA, "cudaFuncSetAttribute(stage1 shared memory) failed"));
     }
@@ -299,9 +309,10 @@ void gp_driver_destroy(gp_driver *d) {
 gp_status gp_set_tuning(gp_driver *d, const gp_tuning *t) {
     if (!d || !t) return fail(GP_ERR_INVALID, "null argument");
     auto ok_threads = [](uint32_t x) { return x == 128 || x == 256 || x == 512; };
-    if (!ok_threads(t->stage1_threads) || !ok_threads(t->stage2_threads) || t->stage2_blocks_per_sm == 0 ||
+    if (!(ok_threads(t->stage1_threads) || t->stage1_threads == 1024) || !ok_threads(t->stage2_threads) ||
+        t->stage2_blocks_per_sm == 0 ||
         t->stage2_blocks_per_sm > 64 || t->stage1_blocks_per_sm > 64)
-        return fail(GP_ERR_INVALID, "tuning: threads must be 128, 256 or 512; blocks per SM 1..64");
+        return fail(GP_ERR_INVALID, "tuning: stage-1 threads 128..1024, stage-2 threads 128..512 (powers of two); blocks per SM 1..64");
     d->tuning = *t;
     return GP_OK;
 }
@@ -455,6 +466,8 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     P->max_layer_slots = L.max_layer_slots;
     P->max_meas = bd.max_measurements;
     P->max_ops = (uint32_t)bd.max_ops;
+    P->rec_cap = (uint32_t)L.rec_cap;
+    P->max_qubits = bd.max_qubits;
     GP_CUDA(cudaMemcpyAsync(d->B.params, d->h_params, d->params_bytes, cudaMemcpyHostToDevice, s));
 
     // ---- pipeline ------------------------------------------------------------
@@ -468,11 +481,11 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     const uint32_t grid1 = std::max<uint32_t>(1u, std::min<uint32_t>(ni, (uint32_t)d->n_sms * bps));
 
     if (d->timing) GP_CUDA(cudaEventRecord(d->ev[0], s));
-    launch_lowering(d->B, L.max_tiles, tiles_total, s, &d->launches);
+    launch_lowering(d->B, tiles_total, L.max_layer_slots, bd.max_qubits, s, &d->launches);
     if (d->timing) GP_CUDA(cudaEventRecord(d->ev[1], s));
     launch_stage1(d->B, grid1, d->tuning.stage1_threads, bd.max_qubits, s, &d->launches);
     if (d->timing) GP_CUDA(cudaEventRecord(d->ev[2], s));
-    launch_group(d->B, grid2, d->tuning.stage2_threads, bd.max_mechanisms, s, &d->launches);
+    launch_group(d->B, grid2, d->tuning.stage2_threads, s, &d->launches);
     if (d->timing) GP_CUDA(cudaEventRecord(d->ev[3], s));
     launch_compact(d->B, grid2, d->tuning.stage2_threads, L.max_scan_blocks, bd.max_mechanisms, s, &d->launches);
     if (d->timing) GP_CUDA(cudaEventRecord(d->ev[4], s));

@@ -17,6 +17,10 @@ constexpr int kLowerThreads = 256;      // 16 rows per thread
 constexpr int kMaxEntries = 1024;       // (measurement, word) pairs per column
 constexpr int kMaxMaskWords = 16;       // hard cap of mask words per mechanism
 constexpr int kMechPerBlockScan = 1024; // mechanisms per compaction block
+constexpr int kRowBuf = 1920;           // packed rows per staged layer buffer
+constexpr int kStageRecs = 2048;        // staged mask records per block
+constexpr uint32_t kChunkRecs = 4096;   // records per global chunk of a block
+constexpr int kPackThreads = 256;       // layer packing block size
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint32_t kObsColFlag = 0x80000000u;   // set on the column id of an
@@ -58,7 +62,8 @@ struct Params {
     uint32_t max_meas;
     uint32_t max_ops;
     const float *noise;         // concatenated noise vectors
-    uint32_t pad[2];
+    uint32_t rec_cap;           // capacity of the record pool
+    uint32_t max_qubits;
 };
 
 // device status block (read back by the host after every compile)
@@ -70,7 +75,7 @@ struct Status {
     uint32_t n_det_entries;
     uint32_t n_scan_blocks;
     uint32_t queue_head;        // stage-1 work queue
-    uint32_t queue_done;        // stage-1 finished blocks
+    uint32_t rec_count;         // records handed out from the pool
     uint32_t pad[6];
 };
 
@@ -85,6 +90,11 @@ struct Buffers {
     uint32_t *recs_arena;
     float *noise_arena;
     uint32_t *aux;              // per row (indexed by op_base + row)
+    uint2 *packed;              // per row: packed gate / noise rows, per layer
+                                // ordered gates | after-noise | before-noise
+    uint4 *layer_seg;           // per layer slot: {start, end of gates,
+                                // end of after-noise, end of before-noise}
+    uint4 *records;             // mask-word records {mech, column, word lo, hi}
     uint4 *tile_sums, *tile_off;
     uint32_t *layer_start;      // per circuit: n_layers + 1 row offsets
     uint32_t *meas_layer;       // per measurement: its layer
@@ -168,6 +178,58 @@ __device__ __forceinline__ void channel_ck(uint32_t kind, float &c, float &k) {
 }
 __device__ __forceinline__ float channel_pmax(uint32_t kind) {
     return kind == K_DEP1 ? 0.75f : (kind == K_DEP2 ? 0.9375f : 0.5f);
+}
+
+// packed rows: kind (6 bits) | qubit a (13 bits) | qubit b (13 bits), aux
+__host__ __device__ inline uint2 pack_row(uint32_t kind, uint32_t a, uint32_t b, uint32_t aux) {
+    return make_uint2((kind << 26) | (a << 13) | b, aux);
+}
+__host__ __device__ inline uint32_t row_kind(uint2 r) { return r.x >> 26; }
+__host__ __device__ inline uint32_t row_a(uint2 r) { return (r.x >> 13) & 0x1FFFu; }
+__host__ __device__ inline uint32_t row_b(uint2 r) { return r.x & 0x1FFFu; }
+
+// ---------------------------------------------------------------------------
+// shared-memory barriers and 1-D bulk (TMA) copies
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// arrive on the barrier and announce `bytes` of transaction for this phase
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted on the barrier
+// (addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// bounded wait: false if the phase did not complete within the limit
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -285,11 +347,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 
 // kernel entry points (implemented in lower.cu, stage1.cu, stage2.cu)
 namespace gpdem {
-void launch_lowering(const Buffers &b, uint32_t max_tiles, uint32_t n_tiles, cudaStream_t s, uint32_t *launches);
+void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, cudaStream_t s,
+                     uint32_t *launches);
 void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_qubits, cudaStream_t s, uint32_t *launches);
 size_t stage1_smem_bytes(uint32_t max_qubits);
 const void *stage1_kernel_ptr(uint32_t threads);
-void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
+void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches);
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_scan_blocks, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
 void launch_backward(const Buffers &b, const float *g_prob, const float *g_logodds, float *g_noise,
                      uint32_t n_mech, uint32_t n_loc, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches);

@@ -2,14 +2,20 @@
 // realised circuit is lowered to a layered space-time structure before the
 // backward wave runs).
 //
-// Three launches, no device-wide waits:
+// Four launches, no device-wide waits:
 //   tile_count   per tile of 4096 rows: counts of TICKs, measurements,
 //                detectors and mechanisms (components at the chosen level)
 //   tile_scan    one block: per-circuit scan of the tile counts, circuit
 //                totals and batch offsets, capacity checks
 //   tile_lower   per tile: exclusive row scan, validation of every row and
 //                the scatters stage 1 reads (layer starts, record layers,
-//                detector rows, observable rows, per-row auxiliary index)
+//                detector rows, observable rows, per-row auxiliary index,
+//                per-mechanism location/kind/component)
+//   layer_pack   one block per TICK layer: checks that no qubit takes part
+//                in two gates, decides for every noise row whether it acts
+//                before or after the layer's gate on its qubit(s), and writes
+//                the layer as packed 8-byte rows ordered gates | noise after
+//                the gates | noise before the gates
 #include "common.cuh"
 
 namespace gpdem {
@@ -184,13 +190,18 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
             }
             break;
         }
-        case K_XERR: case K_ZERR: case K_DEP1:
-            bad = op.y >= C.n_qubits || op.w >= C.n_loc;
+        case K_XERR: case K_ZERR: case K_DEP1: case K_DEP2:
+            bad = op.y >= C.n_qubits || op.w >= C.n_loc ||
+                  (k == K_DEP2 && (op.z >= C.n_qubits || op.y == op.z));
             aux = mech;
-            break;
-        case K_DEP2:
-            bad = op.y >= C.n_qubits || op.z >= C.n_qubits || op.y == op.z || op.w >= C.n_loc;
-            aux = mech;
+            if (!bad) {
+                const uint32_t nc = n_comp(k, P.level);
+                for (uint32_t c = 0; c < nc; c++)
+                    B.mech_info[C.mech_base + mech + c] = (unsigned long long)(C.loc_base + op.w) |
+                                                          ((unsigned long long)k << 32) |
+                                                          ((unsigned long long)c << 40) |
+                                                          ((unsigned long long)b << 48);
+            }
             break;
         default:
             bad = true;
@@ -202,15 +213,99 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
     }
 }
 
+// One block per layer slot.  Slots are numbered across the batch; circuit b
+// owns slots [layer_base, layer_base + n_layers] (the last one is the end
+// sentinel, which has no rows).
+__global__ void __launch_bounds__(kPackThreads) layer_pack_kernel(Buffers B) {
+    extern __shared__ uint32_t gt[];          // qubit -> row of its gate in this layer
+    const Params &P = *B.params;
+    if (B.status->code != 0) return;
+    const uint32_t g = blockIdx.x;
+    // circuit owning slot g (circuits are laid out in slot order)
+    uint32_t lo = 0, hi = P.n_circuits;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (B.circ[mid].layer_base <= g) lo = mid; else hi = mid;
+    }
+    const uint32_t b = lo;
+    const CircuitDev &C = B.circ[b];
+    if (g < C.layer_base || g >= C.layer_base + C.n_layers) return;
+    const uint32_t rs = B.layer_start[g], re = B.layer_start[g + 1];
+    for (uint32_t q = threadIdx.x; q < C.n_qubits; q += kPackThreads) gt[q] = kNone;
+    __syncthreads();
+    for (uint32_t r = rs + threadIdx.x; r < re; r += kPackThreads) {
+        const uint4 op = C.ops[r];
+        if (!is_gate(op.x)) continue;
+        bool dup = atomicExch(&gt[op.y], r) != kNone;
+        if (is_gate2(op.x)) dup |= atomicExch(&gt[op.z], r) != kNone;
+        if (dup) report(B.status, GP_ERR_INVALID, 4u, b, r);
+    }
+    __syncthreads();
+    // category of a row: 0 none, 1 gate, 2 noise after the gates, 3 before
+    auto category = [&](uint32_t r, uint4 &op) -> uint32_t {
+        op = C.ops[r];
+        if (is_gate(op.x)) return 1u;
+        if (!is_noise(op.x)) return 0u;
+        const uint32_t ga = gt[op.y];
+        const bool bef = ga != kNone && ga > r;
+        if (op.x == K_DEP2) {
+            const uint32_t gb = gt[op.z];
+            if ((gb != kNone && gb > r) != bef) {
+                report(B.status, GP_ERR_INVALID, 3u, b, r);
+                return 0u;
+            }
+        }
+        return bef ? 3u : 2u;
+    };
+    __shared__ uint32_t warp_tmp[kPackThreads / 32];
+    // pass 1: totals per category
+    uint32_t cg = 0, ca = 0, cb = 0, tot;
+    for (uint32_t r = rs + threadIdx.x; r < re; r += kPackThreads) {
+        uint4 op;
+        const uint32_t c = category(r, op);
+        cg += c == 1u;
+        ca += c == 2u;
+        cb += c == 3u;
+    }
+    block_exclusive_scan<kPackThreads>(cg, warp_tmp, tot);
+    const uint32_t nG = tot;
+    block_exclusive_scan<kPackThreads>(ca, warp_tmp, tot);
+    const uint32_t nA = tot;
+    block_exclusive_scan<kPackThreads>(cb, warp_tmp, tot);
+    const uint32_t nB = tot;
+    // pass 2: chunks of kPackThreads consecutive rows keep row order; within
+    // a chunk the three counts fit 10-bit fields of one scanned word
+    uint32_t run[3] = {0, 0, 0};
+    const uint32_t seg0[3] = {rs, rs + nG, rs + nG + nA};
+    for (uint32_t base = rs; base < re; base += kPackThreads) {
+        const uint32_t r = base + threadIdx.x;
+        uint4 op = make_uint4(0, 0, 0, 0);
+        const uint32_t c = r < re ? category(r, op) : 0u;
+        const uint32_t v = c ? (1u << (10u * (c - 1u))) : 0u;
+        uint32_t ctot;
+        const uint32_t ex = block_exclusive_scan<kPackThreads>(v, warp_tmp, ctot);
+        if (c) {
+            const uint32_t rank = ((ex >> (10u * (c - 1u))) & 0x3FFu) + run[c - 1u];
+            const uint32_t aux = (is_measure(op.x) || is_noise(op.x)) ? B.aux[C.op_base + r] : 0u;
+            B.packed[C.op_base + seg0[c - 1u] + rank] = pack_row(op.x, op.y, op.z, aux);
+        }
+        run[0] += ctot & 0x3FFu;
+        run[1] += (ctot >> 10) & 0x3FFu;
+        run[2] += ctot >> 20;
+    }
+    if (threadIdx.x == 0) B.layer_seg[g] = make_uint4(rs, rs + nG, rs + nG + nA, rs + nG + nA + nB);
+}
+
 }  // namespace
 
-void launch_lowering(const Buffers &b, uint32_t max_tiles, uint32_t n_tiles, cudaStream_t s, uint32_t *launches) {
+void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, cudaStream_t s,
+                     uint32_t *launches) {
     const uint32_t grid = n_tiles ? n_tiles : 1u;
-    (void)max_tiles;
     tile_count_kernel<<<grid, kLowerThreads, 0, s>>>(b);
     tile_scan_kernel<<<1, kLowerThreads, 0, s>>>(b);
     tile_lower_kernel<<<grid, kLowerThreads, 0, s>>>(b);
-    *launches += 3;
+    layer_pack_kernel<<<layer_slots, kPackThreads, max_qubits * sizeof(uint32_t), s>>>(b);
+    *launches += 4;
 }
 
 }  // namespace gpdem

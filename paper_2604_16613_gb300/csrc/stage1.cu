@@ -2,37 +2,52 @@
 //
 // The straight-line program of Eq. slp is linear over GF(2), so every 64
 // detectors (one "word column") can be propagated on their own.  A thread
-// block takes one word column at a time from a work queue and keeps, in
-// shared memory, two 64-bit bit-planes per qubit of that column:
+// block takes word columns from a work queue and keeps, in shared memory, two
+// 64-bit bit-planes per qubit of the column:
 //   xs[q] bit j = detector j flips under an X error on q at the current time
 //   zs[q] bit j = the same for a Z error.
 // It walks the TICK layers backward from the latest measurement of the
 // column's detectors (Eq. init-slp seeds the bits there) and stops once every
-// plane is zero and no earlier measurement of the column remains, so each
-// column only pays for the layers its detecting regions cover.  Per layer:
-//   P1  mask words of noise rows that act before the layer's gates of the
-//       previous (later-in-time) layer, and the qubit -> gate-row table of
-//       this layer (double-buffered by layer parity)
-//   P2  mask words of noise rows that act after this layer's gates
-//   P3  the gates undone backward (H swaps the planes, S: x ^= z,
-//       CX(c,t): x_c ^= x_t and z_t ^= z_c, CZ(a,b): x_a ^= z_b and
-//       x_b ^= z_a; measurements XOR in the column's detector bits; resets
-//       clear the planes after checking determinism).
-// A noise component's mask word is the XOR of the planes named by its Pauli
-// (Y = X xor Z; two-qubit terms combine both qubits, Sec. 2.3.4); non-zero
-// words are appended to the mechanism's slots with one atomic counter per
-// mechanism.
+// plane is zero and no earlier measurement of the column remains, so a column
+// only pays for the layers its detecting regions cover.
+//
+// Layers arrive pre-packed by the lowering (gates | noise after the gates |
+// noise before the gates, 8 bytes a row).  Each layer is staged into shared
+// memory by a 1-D bulk copy (TMA) issued one layer ahead into a
+// double buffer and tracked by an mbarrier; layers larger than a buffer are
+// read from global memory directly.  Per layer L two barrier-separated
+// phases run:
+//   A  mask words of the noise rows acting after the gates of L and before
+//      the gates of L+1 (the planes hold the state between the two), and the
+//      termination test;
+//   B  the gates of L undone backward: H swaps the planes, S: x ^= z,
+//      CX(c,t): x_c ^= x_t and z_t ^= z_c, CZ(a,b): x_a ^= z_b and
+//      x_b ^= z_a; measurements XOR in the column's detector bits; resets
+//      clear the planes after checking that the detectors commute with them.
+// A component's mask word is the XOR of the planes its Pauli names (Y = X xor
+// Z, two-qubit terms combine both qubits: Sec. 2.3.4).  Non-zero words become
+// 16-byte records {mechanism, column, word}; they are staged in shared memory
+// during phase A and copied to the block's chunk of the global record pool
+// during phase B, so the walk never waits on a global atomic.
 #include "common.cuh"
 
 namespace gpdem {
 
 namespace {
 
+constexpr int kRowBufs = 3;         // layer buffers: L+1 (held), L, L-1 .. L-2 in flight
+constexpr int kSegCache = 256;      // layer segments cached in shared memory
+constexpr int kActive = 2 * kRowBuf; // noise rows examined per emission piece
+
 struct Smem {
     unsigned long long *xs, *zs;
-    uint32_t *gtab[2];
-    uint32_t *ent_m;
     unsigned long long *ent_w;
+    unsigned long long *st_word;    // staged records: word
+    uint4 *segc;
+    uint2 *rows[kRowBufs];
+    uint32_t *ent_m;
+    uint32_t *st_mech;              // staged records: mechanism
+    uint16_t *act;                  // active noise rows of the current piece
 };
 
 __device__ __forceinline__ Smem carve(unsigned char *base, uint32_t maxq) {
@@ -40,9 +55,13 @@ __device__ __forceinline__ Smem carve(unsigned char *base, uint32_t maxq) {
     s.xs = reinterpret_cast<unsigned long long *>(base);
     s.zs = s.xs + maxq;
     s.ent_w = s.zs + maxq;
-    s.gtab[0] = reinterpret_cast<uint32_t *>(s.ent_w + kMaxEntries);
-    s.gtab[1] = s.gtab[0] + maxq;
-    s.ent_m = s.gtab[1] + maxq;
+    s.st_word = s.ent_w + kMaxEntries;
+    s.segc = reinterpret_cast<uint4 *>(s.st_word + kStageRecs);
+    uint2 *rw = reinterpret_cast<uint2 *>(s.segc + kSegCache);
+    for (int i = 0; i < kRowBufs; i++) s.rows[i] = rw + i * (kRowBuf + 2);
+    s.ent_m = reinterpret_cast<uint32_t *>(rw + kRowBufs * (kRowBuf + 2));
+    s.st_mech = s.ent_m + kMaxEntries;
+    s.act = reinterpret_cast<uint16_t *>(s.st_mech + kStageRecs);
     return s;
 }
 
@@ -60,59 +79,100 @@ __device__ __forceinline__ unsigned long long meas_word(const Smem &s, uint32_t 
     return w;
 }
 
-// Emit the mask words of the noise rows of layer [rs, re) that act on the
-// requested side of the layer's gates (before == true: before the gates).
+// rows of one layer: a base pointer (shared or global) and segment bounds
+struct LayerView {
+    const uint2 *rows;      // rows[0] is the layer's first packed row
+    uint32_t g, a, b;       // ends of the gate, after-noise, before-noise segments
+};
+
+struct Shared {
+    unsigned long long mbar[kRowBufs];
+    uint32_t cnt[2];        // staged records per epoch parity (one data buffer:
+                            // an epoch's records are copied out before the
+                            // next epoch stages any)
+    uint32_t chunk_pos, chunk_end;
+    uint32_t item, bail, nent, lmax, lmin, tmo;
+    uint32_t n_act;         // active rows listed for the current piece
+    uint32_t next_chunk;    // record chunk requested ahead (kNone: none)
+};
+
+// The noise rows of one emission step are rows [g, a) of layer L (after its
+// gates) followed by rows [a', b') of layer L+1 (before its gates), indexed
+// 0 .. nA + nB - 1.
+__device__ __forceinline__ uint2 emission_row(const LayerView &cur, const LayerView &nxt, uint32_t nA, uint32_t i) {
+    return i < nA ? cur.rows[cur.g + i] : nxt.rows[nxt.a + (i - nA)];
+}
+
+// A1: list the rows of [p0, p1) whose planes are not all zero (warp-aggregated
+// appends to the shared list).
 template <int NT>
-__device__ __forceinline__ void emit_layer(const Buffers &B, const CircuitDev &C, const Smem &s,
-                                           uint32_t rs, uint32_t re, const uint32_t *gtab,
-                                           bool before, uint32_t gcol_tag, uint32_t b,
-                                           uint32_t level, uint32_t S) {
-    for (uint32_t r = rs + threadIdx.x; r < re; r += NT) {
-        const uint4 op = __ldg(&C.ops[r]);
-        const uint32_t k = op.x;
-        if (!is_noise(k)) continue;
-        const uint32_t a = op.y;
-        const uint32_t ga = gtab[a];
-        const bool bef_a = (ga >= rs && ga < re && ga > r);
-        bool side = bef_a;
-        unsigned long long xa = s.xs[a], za = s.zs[a], xb = 0ull, zb = 0ull;
-        if (k == K_DEP2) {
-            const uint32_t bq = op.z;
-            const uint32_t gb = gtab[bq];
-            const bool bef_b = (gb >= rs && gb < re && gb > r);
-            if (bef_b != bef_a) {
-                report(B.status, GP_ERR_INVALID, 3u, b, r);
-                continue;
+__device__ __forceinline__ void list_active(const Smem &s, Shared &sh, const LayerView &cur, const LayerView &nxt,
+                                            uint32_t nA, uint32_t p0, uint32_t p1) {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t base = p0; base < p1; base += NT) {
+        const uint32_t i = base + threadIdx.x;
+        bool active = false;
+        if (i < p1) {
+            const uint2 r = emission_row(cur, nxt, nA, i);
+            const uint32_t a = row_a(r);
+            unsigned long long v = s.xs[a] | s.zs[a];
+            if (row_kind(r) == K_DEP2) {
+                const uint32_t bq = row_b(r);
+                v |= s.xs[bq] | s.zs[bq];
             }
-            xb = s.xs[bq];
-            zb = s.zs[bq];
+            active = v != 0ull;
         }
-        if (side != before) continue;
-        if ((xa | za | xb | zb) == 0ull) continue;
-        const uint32_t nc = n_comp(k, level);
-        const uint32_t mbase = C.mech_base + B.aux[C.op_base + r];
-        for (uint32_t c = 0; c < nc; c++) {
-            const uint32_t code = comp_planes(k, c);
-            unsigned long long w = 0ull;
-            if (code & 1u) w ^= xa;
-            if (code & 2u) w ^= za;
-            if (code & 4u) w ^= xb;
-            if (code & 8u) w ^= zb;
-            if (w == 0ull) continue;
-            const uint32_t mech = mbase + c;
-            const uint32_t idx = atomicAdd(&B.mech_cnt[mech], 1u);
-            if (idx == 0u) {
-                B.mech_info[mech] = (unsigned long long)(C.loc_base + op.w) |
-                                    ((unsigned long long)k << 32) |
-                                    ((unsigned long long)c << 40) |
-                                    ((unsigned long long)b << 48);
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, active);
+        if (m == 0u) continue;
+        uint32_t wbase = 0;
+        if (lane == 0u) wbase = atomicAdd(&sh.n_act, (uint32_t)__popc(m));
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+        if (active) s.act[wbase + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(i - p0);
+    }
+}
+
+// A2: every half-warp takes one listed row and evaluates its Pauli
+// components one per lane; non-zero words are staged with one reservation per
+// warp (spilling straight to the pool if the stage is full).
+template <int NT>
+__device__ __forceinline__ void emit_active(const Buffers &B, const Smem &s, Shared &sh, const CircuitDev &C,
+                                            const LayerView &cur, const LayerView &nxt, uint32_t nA, uint32_t p0,
+                                            uint32_t n_act, uint32_t col_tag, uint32_t level, uint32_t sb,
+                                            uint32_t rec_cap) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t c = lane & 15u;
+    const uint32_t mech_base = C.mech_base;
+    for (uint32_t base = 2u * warp; base < n_act; base += 2u * (NT / 32)) {
+        const uint32_t idx = base + (lane >> 4);
+        unsigned long long w = 0ull;
+        uint32_t mech = 0;
+        if (idx < n_act) {
+            const uint2 r = emission_row(cur, nxt, nA, p0 + s.act[idx]);
+            const uint32_t kind = row_kind(r);
+            if (c < n_comp(kind, level)) {
+                const uint32_t code = comp_planes(kind, c);
+                const uint32_t a = row_a(r), bq = row_b(r);
+                if (code & 1u) w ^= s.xs[a];
+                if (code & 2u) w ^= s.zs[a];
+                if (code & 4u) w ^= s.xs[bq];
+                if (code & 8u) w ^= s.zs[bq];
+                mech = mech_base + r.y + c;
             }
-            if (idx < S) {
-                const size_t slot = (size_t)mech * S + idx;
-                B.slot_col[slot] = gcol_tag;
-                B.slot_word[slot] = w;
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, w != 0ull);
+        if (m == 0u) continue;
+        uint32_t wbase = 0;
+        if (lane == 0u) wbase = atomicAdd(&sh.cnt[sb], (uint32_t)__popc(m));
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+        if (w != 0ull) {
+            const uint32_t pos = wbase + __popc(m & ((1u << lane) - 1u));
+            if (pos < (uint32_t)kStageRecs) {
+                s.st_mech[pos] = mech;
+                s.st_word[pos] = w;
             } else {
-                report(B.status, GP_ERR_CAPACITY, 4u, mech, idx + 1);
+                const uint32_t g = atomicAdd(&B.status->rec_count, 1u);
+                if (g < rec_cap) B.records[g] = make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+                else report(B.status, GP_ERR_CAPACITY, 8u, g, rec_cap);
             }
         }
     }
@@ -120,36 +180,88 @@ __device__ __forceinline__ void emit_layer(const Buffers &B, const CircuitDev &C
 
 template <int NT>
 __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const Smem s = carve(smem_raw, maxq);
+    __shared__ Shared sh;
     const Params &P = *B.params;
-    const uint32_t level = P.level, S = P.mask_words;
-    __shared__ uint32_t s_item, s_bail, s_nent, s_lmax, s_lmin;
+    const uint32_t level = P.level, rec_cap = P.rec_cap;
+    const uint4 *layer_seg = B.layer_seg;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kRowBufs; i++) mbar_init(&sh.mbar[i], 1);
+        fence_mbar_init();
+        sh.cnt[0] = sh.cnt[1] = 0;
+        sh.chunk_pos = sh.chunk_end = 0;
+        sh.tmo = 0;
+        sh.next_chunk = kNone;
+        sh.n_act = 0;
+    }
+    __syncthreads();
+    uint32_t phase_bits = 0u;         // mbarrier parity per row buffer (bit i)
+    uint32_t pend_bits = 0u;          // copies issued and not yet waited for
+    uint32_t epoch = 0;               // emission epochs alternate staging buffers
+    bool timed_out = false;
+
+    // thread 0, at the start of every phase A: retire the previous epoch's
+    // staged records (copied during the last phase B) and make sure the
+    // block's chunk can take a full staging buffer
+    auto housekeeping = [&](uint32_t ep) {
+        if (threadIdx.x != 0) return;
+        if (ep > 0) {
+            const uint32_t pb = (ep - 1u) & 1u;
+            sh.chunk_pos += min(sh.cnt[pb], (uint32_t)kStageRecs);
+            sh.cnt[pb] = 0;
+        }
+        const uint32_t room = sh.chunk_end - sh.chunk_pos;
+        // ask for the next chunk while two stages still fit, so the atomic's
+        // latency is hidden behind later layers
+        if (room < 3u * (uint32_t)kStageRecs && sh.next_chunk == kNone)
+            sh.next_chunk = atomicAdd(&B.status->rec_count, kChunkRecs);
+        if (room < (uint32_t)kStageRecs) {
+            const uint32_t base = sh.next_chunk;
+            sh.next_chunk = kNone;
+            if (base == kNone || base + kChunkRecs > rec_cap || base + kChunkRecs < base) {
+                report(B.status, GP_ERR_CAPACITY, 8u, base, rec_cap);
+                sh.chunk_pos = sh.chunk_end = 0;   // nothing is flushed below
+            } else {
+                sh.chunk_pos = base;
+                sh.chunk_end = base + kChunkRecs;
+            }
+        }
+    };
+    // all threads, during phase B: copy epoch ep's staged records to the chunk
+    auto flush = [&](uint32_t ep, uint32_t col_tag) {
+        const uint32_t sb = ep & 1u;
+        const uint32_t n = min(sh.cnt[sb], (uint32_t)kStageRecs);
+        if (sh.chunk_end - sh.chunk_pos < n) return;    // capacity already reported
+        for (uint32_t i = threadIdx.x; i < n; i += NT) {
+            const unsigned long long w = s.st_word[i];
+            B.records[sh.chunk_pos + i] = make_uint4(s.st_mech[i], col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+        }
+    };
 
     for (;;) {
         if (threadIdx.x == 0) {
-            s_item = atomicAdd(&B.status->queue_head, 1u);
-            s_bail = (*(volatile uint32_t *)&B.status->code) != 0u;
-            s_nent = 0;
-            s_lmax = 0;
-            s_lmin = 0xFFFFFFFFu;
+            sh.item = atomicAdd(&B.status->queue_head, 1u);
+            sh.bail = (*(volatile uint32_t *)&B.status->code) != 0u;
+            sh.nent = 0;
+            sh.lmax = 0;
+            sh.lmin = 0xFFFFFFFFu;
         }
         __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= P.n_items || s_bail) break;
+        const uint32_t item = sh.item;
+        if (item >= P.n_items || sh.bail || timed_out) break;
         const uint32_t gcol = B.items[item];
         const uint32_t b = B.col_circ[gcol];
         const CircuitDev &C = B.circ[b];
         const uint32_t local = gcol - C.col_base;
         const bool is_obs = (C.n_obs > 0u) && (local == C.n_cols - 1u);
-        const uint32_t gcol_tag = gcol | (is_obs ? kObsColFlag : 0u);
+        const uint32_t col_tag = gcol | (is_obs ? kObsColFlag : 0u);
         const uint32_t nq = C.n_qubits;
 
         for (uint32_t q = threadIdx.x; q < nq; q += NT) {
             s.xs[q] = 0ull;
             s.zs[q] = 0ull;
-            s.gtab[0][q] = kNone;
-            s.gtab[1][q] = kNone;
         }
         // (measurement, word) entries of this column (Eq. init-slp)
         if (!is_obs) {
@@ -159,7 +271,7 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
                 const uint4 op = C.ops[row];
                 const uint32_t mb = B.aux[C.op_base + row];
                 for (uint32_t i = 0; i < op.z; i++) {
-                    const uint32_t e = atomicAdd(&s_nent, 1u);
+                    const uint32_t e = atomicAdd(&sh.nent, 1u);
                     if (e < (uint32_t)kMaxEntries) {
                         s.ent_m[e] = mb - C.recs[op.y + i];
                         s.ent_w[e] = 1ull << (j & 63u);
@@ -173,7 +285,7 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
                 const uint4 op = C.ops[row];
                 const uint32_t mb = B.aux[C.op_base + row];
                 for (uint32_t i = 0; i < op.z; i++) {
-                    const uint32_t e = atomicAdd(&s_nent, 1u);
+                    const uint32_t e = atomicAdd(&sh.nent, 1u);
                     if (e < (uint32_t)kMaxEntries) {
                         s.ent_m[e] = mb - C.recs[op.y + i];
                         s.ent_w[e] = 1ull << op.w;
@@ -182,13 +294,12 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
             }
         }
         __syncthreads();
-        const uint32_t n_ent_raw = s_nent;
-        if (n_ent_raw > (uint32_t)kMaxEntries) {
-            if (threadIdx.x == 0) report(B.status, GP_ERR_CAPACITY, 5u, gcol, n_ent_raw);
+        const uint32_t n_ent = sh.nent;
+        if (n_ent > (uint32_t)kMaxEntries) {
+            if (threadIdx.x == 0) report(B.status, GP_ERR_CAPACITY, 5u, gcol, n_ent);
             __syncthreads();
             continue;
         }
-        const uint32_t n_ent = n_ent_raw;
         if (n_ent == 0u) { __syncthreads(); continue; }
         // bitonic sort of the entries by measurement index
         uint32_t npow = 1;
@@ -214,92 +325,189 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
         }
         for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
             const uint32_t L = B.meas_layer[C.meas_base + s.ent_m[i]];
-            atomicMax(&s_lmax, L);
-            atomicMin(&s_lmin, L);
+            atomicMax(&sh.lmax, L);
+            atomicMin(&sh.lmin, L);
         }
         __syncthreads();
-        const uint32_t lmax = s_lmax, lmin = s_lmin;
+        const uint32_t lmax = sh.lmax, lmin = sh.lmin;
         const uint32_t m_lo = s.ent_m[0], m_hi = s.ent_m[n_ent - 1];
-        const uint32_t *ls = B.layer_start + C.layer_base;
+        const uint4 *seg_g = layer_seg + C.layer_base;
+        const uint2 *packed = B.packed + C.op_base;
+        // the column's layer segments, cached once
+        const uint32_t n_cache = min(lmax + 1u, (uint32_t)kSegCache);
+        for (uint32_t i = threadIdx.x; i < n_cache; i += NT) s.segc[i] = seg_g[i];
+        __syncthreads();
+        auto segL = [&](uint32_t L) -> uint4 { return L < (uint32_t)kSegCache ? s.segc[L] : seg_g[L]; };
+        auto staged = [&](const uint4 &sg) -> bool {
+            const uint32_t n = sg.w - sg.x;
+            return n != 0u && n <= (uint32_t)kRowBuf;
+        };
+        auto row_delta = [&](const uint4 &sg) -> uint32_t {
+            return (uint32_t)((reinterpret_cast<uintptr_t>(packed + sg.x) & 15u) >> 3);
+        };
+        // stage layer L into buffer L % 3 (thread 0 issues the bulk copy)
+        auto issue = [&](uint32_t L) {
+            const uint4 sg = segL(L);
+            if (!staged(sg)) return;
+            const uint32_t bi = L % (uint32_t)kRowBufs;
+            if (threadIdx.x == NT - 32) {
+                const uint32_t delta = row_delta(sg);
+                const uint32_t bytes = ((sg.w - sg.x + delta) * 8u + 15u) & ~15u;
+                fence_proxy_async_smem();
+                mbar_expect_tx(&sh.mbar[bi], bytes);
+                bulk_load(s.rows[bi], packed + sg.x - delta, bytes, &sh.mbar[bi]);
+            }
+            pend_bits |= 1u << bi;
+        };
+        // every thread waits for layer L's copy itself (no block barrier)
+        auto wait = [&](uint32_t L) {
+            const uint32_t bi = L % (uint32_t)kRowBufs;
+            if (!((pend_bits >> bi) & 1u)) return;
+            if (!mbar_wait_bounded(&sh.mbar[bi], (phase_bits >> bi) & 1u)) sh.tmo = 1u;
+            phase_bits ^= 1u << bi;
+            pend_bits &= ~(1u << bi);
+        };
+        auto view = [&](uint32_t L) -> LayerView {
+            const uint4 sg = segL(L);
+            LayerView v;
+            v.rows = staged(sg) ? s.rows[L % (uint32_t)kRowBufs] + row_delta(sg) : packed + sg.x;
+            v.g = sg.y - sg.x;
+            v.a = sg.z - sg.x;
+            v.b = sg.w - sg.x;
+            return v;
+        };
 
         // backward wave over the layers
         uint32_t L = lmax;
         bool stopped = false;
+        issue(L);
+        if (L > 0u) issue(L - 1u);
+        wait(L);
+        LayerView vnext{};            // layer L+1 (held for its before-noise)
         for (;;) {
-            const uint32_t rs = ls[L], re = ls[L + 1];
-            // P1: before-gate noise of layer L+1, and the gate table of layer L
-            if (L < lmax) emit_layer<NT>(B, C, s, re, ls[L + 2], s.gtab[(L + 1) & 1u], true, gcol_tag, b, level, S);
-            uint32_t *gt = s.gtab[L & 1u];
-            for (uint32_t r = rs + threadIdx.x; r < re; r += NT) {
-                const uint4 op = __ldg(&C.ops[r]);
-                if (!is_gate(op.x)) continue;
-                const uint32_t old = atomicExch(&gt[op.y], r);
-                bool dup = (old != kNone && old >= rs && old < re);
-                if (is_gate2(op.x)) {
-                    const uint32_t old2 = atomicExch(&gt[op.z], r);
-                    dup |= (old2 != kNone && old2 >= rs && old2 < re);
+            const LayerView vcur = view(L);
+            // phase A: noise after the gates of L and before the gates of L+1,
+            // in pieces of at most kActive rows (one piece for staged layers)
+            housekeeping(epoch);
+            const uint32_t sb = epoch & 1u;
+            const bool tmo_here = sh.tmo != 0u;
+            const uint32_t nA = (L < lmax) ? vcur.a - vcur.g : 0u;
+            const uint32_t total = (L < lmax && !tmo_here) ? nA + (vnext.b - vnext.a) : 0u;
+            const bool check = (L < lmax) && (L + 1u <= lmin);
+            int any = 1;
+            for (uint32_t p0 = 0;; p0 += (uint32_t)kActive) {
+                const uint32_t p1 = min(p0 + (uint32_t)kActive, total);
+                if (p0 < p1) list_active<NT>(s, sh, vcur, vnext, nA, p0, p1);
+                int nonzero = 0;
+                if (check && p0 == 0u) {
+                    for (uint32_t q = threadIdx.x; q < nq; q += NT)
+                        if ((s.xs[q] | s.zs[q]) != 0ull) { nonzero = 1; break; }
                 }
-                if (dup) report(B.status, GP_ERR_INVALID, 4u, b, r);
+                const int piece_any = __syncthreads_or(nonzero);
+                if (p0 == 0u) any = piece_any;
+                const uint32_t n_act = sh.n_act;
+                if (n_act) emit_active<NT>(B, s, sh, C, vcur, vnext, nA, p0, n_act, col_tag, level, sb, rec_cap);
+                __syncthreads();
+                if (threadIdx.x == 0) sh.n_act = 0;
+                if (p1 >= total) break;
+                __syncthreads();
             }
-            __syncthreads();
-            // P2: after-gate noise of layer L (planes are still zero at lmax)
-            if (L < lmax) emit_layer<NT>(B, C, s, rs, re, gt, false, gcol_tag, b, level, S);
-            __syncthreads();
-            // P3: undo the gates of layer L
-            for (uint32_t r = rs + threadIdx.x; r < re; r += NT) {
-                const uint4 op = __ldg(&C.ops[r]);
-                const uint32_t k = op.x, a = op.y;
+            if (sh.tmo) { timed_out = true; break; }
+            // phase B: records of phase A flushed, the gates of L undone
+            flush(epoch, col_tag);
+            epoch++;
+            if (check && !any) { stopped = true; break; }
+            if (L >= 2u) issue(L - 2u);     // into the buffer layer L+1 held
+            for (uint32_t i = threadIdx.x; i < vcur.g; i += NT) {
+                const uint2 r = vcur.rows[i];
+                const uint32_t k = row_kind(r), a = row_a(r);
                 switch (k) {
                 case K_H: { const unsigned long long t = s.xs[a]; s.xs[a] = s.zs[a]; s.zs[a] = t; break; }
                 case K_S: s.xs[a] ^= s.zs[a]; break;
-                case K_CX: s.xs[a] ^= s.xs[op.z]; s.zs[op.z] ^= s.zs[a]; break;
-                case K_CZ: { const unsigned long long za = s.zs[a], zb = s.zs[op.z]; s.xs[a] ^= zb; s.xs[op.z] ^= za; break; }
+                case K_CX: { const uint32_t t = row_b(r); s.xs[a] ^= s.xs[t]; s.zs[t] ^= s.zs[a]; break; }
+                case K_CZ: {
+                    const uint32_t t = row_b(r);
+                    const unsigned long long za = s.zs[a], zb = s.zs[t];
+                    s.xs[a] ^= zb;
+                    s.xs[t] ^= za;
+                    break;
+                }
                 case K_R: case K_M: case K_MR: {
-                    if (s.zs[a] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, r, gcol);
-                    if (k == K_R || k == K_MR) { s.xs[a] = 0ull; s.zs[a] = 0ull; }
-                    if (k != K_R) s.xs[a] ^= meas_word(s, n_ent, B.aux[C.op_base + r], m_lo, m_hi);
+                    if (s.zs[a] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, L, gcol);
+                    if (k != K_M) { s.xs[a] = 0ull; s.zs[a] = 0ull; }
+                    if (k != K_R) s.xs[a] ^= meas_word(s, n_ent, r.y, m_lo, m_hi);
                     break;
                 }
                 case K_RX: case K_MX: case K_MRX: {
-                    if (s.xs[a] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, r, gcol);
-                    if (k == K_RX || k == K_MRX) { s.xs[a] = 0ull; s.zs[a] = 0ull; }
-                    if (k != K_RX) s.zs[a] ^= meas_word(s, n_ent, B.aux[C.op_base + r], m_lo, m_hi);
+                    if (s.xs[a] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, L, gcol);
+                    if (k != K_MX) { s.xs[a] = 0ull; s.zs[a] = 0ull; }
+                    if (k != K_RX) s.zs[a] ^= meas_word(s, n_ent, r.y, m_lo, m_hi);
                     break;
                 }
                 default: break;
                 }
             }
-            int nonzero = 0;
-            if (L <= lmin) {
-                for (uint32_t q = threadIdx.x; q < nq; q += NT)
-                    if ((s.xs[q] | s.zs[q]) != 0ull) { nonzero = 1; break; }
-            }
-            const int any = __syncthreads_or(nonzero);
-            if (L <= lmin && !any) { stopped = true; break; }
+            __syncthreads();
             if (L == 0u) break;
+            vnext = vcur;
             L--;
+            wait(L);
         }
-        if (!stopped) {
+        if (!stopped && !timed_out) {
             // before-gate noise of layer 0, then the |0> initial state
-            emit_layer<NT>(B, C, s, ls[0], ls[1], s.gtab[0], true, gcol_tag, b, level, S);
+            const LayerView v0 = view(0u);
+            housekeeping(epoch);
+            const uint32_t sb = epoch & 1u;
+            const uint32_t total = v0.b - v0.a;
+            LayerView none = v0;
+            none.g = none.a;             // empty "after" part: rows [a, a)
+            for (uint32_t p0 = 0;; p0 += (uint32_t)kActive) {
+                const uint32_t p1 = min(p0 + (uint32_t)kActive, total);
+                if (p0 < p1) list_active<NT>(s, sh, none, v0, 0u, p0, p1);
+                __syncthreads();
+                const uint32_t n_act = sh.n_act;
+                if (n_act) emit_active<NT>(B, s, sh, C, none, v0, 0u, p0, n_act, col_tag, level, sb, rec_cap);
+                __syncthreads();
+                if (threadIdx.x == 0) sh.n_act = 0;
+                if (p1 >= total) break;
+                __syncthreads();
+            }
             for (uint32_t q = threadIdx.x; q < nq; q += NT)
                 if (s.zs[q] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, 0xFFFFFFFFu, gcol);
+            __syncthreads();
+            flush(epoch, col_tag);
+            epoch++;
+        }
+        // copies still in flight after an early stop land before the buffers
+        // are reused
+        for (uint32_t i = 0; i < (uint32_t)kRowBufs; i++) {
+            if ((pend_bits >> i) & 1u) {
+                if (!mbar_wait_bounded(&sh.mbar[i], (phase_bits >> i) & 1u)) sh.tmo = 1u;
+                phase_bits ^= 1u << i;
+                pend_bits &= ~(1u << i);
+            }
         }
         __syncthreads();
+        if (timed_out || sh.tmo) {
+            if (threadIdx.x == 0) report(B.status, GP_ERR_TIMEOUT, 1u, gcol, L);
+            break;
+        }
     }
 }
 
 }  // namespace
 
 size_t stage1_smem_bytes(uint32_t maxq) {
-    return (size_t)maxq * (8 + 8 + 4 + 4) + (size_t)kMaxEntries * (8 + 4);
+    return (size_t)maxq * 16 + (size_t)kMaxEntries * 12 + (size_t)kStageRecs * 12 + (size_t)kSegCache * 16 +
+           (size_t)(kRowBuf + 2) * kRowBufs * 8 + (size_t)kActive * 2;
 }
 
 const void *stage1_kernel_ptr(uint32_t threads) {
     switch (threads) {
     case 128: return (const void *)stage1_kernel<128>;
-    case 512: return (const void *)stage1_kernel<512>;
-    default: return (const void *)stage1_kernel<256>;
+    case 256: return (const void *)stage1_kernel<256>;
+    case 1024: return (const void *)stage1_kernel<1024>;
+    default: return (const void *)stage1_kernel<512>;
     }
 }
 
@@ -308,8 +516,9 @@ void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t m
     const size_t smem = stage1_smem_bytes(maxq);
     switch (threads) {
     case 128: stage1_kernel<128><<<grid, 128, smem, s>>>(b, maxq); break;
-    case 512: stage1_kernel<512><<<grid, 512, smem, s>>>(b, maxq); break;
-    default: stage1_kernel<256><<<grid, 256, smem, s>>>(b, maxq); break;
+    case 256: stage1_kernel<256><<<grid, 256, smem, s>>>(b, maxq); break;
+    case 1024: stage1_kernel<1024><<<grid, 1024, smem, s>>>(b, maxq); break;
+    default: stage1_kernel<512><<<grid, 512, smem, s>>>(b, maxq); break;
     }
     *launches += 1;
 }

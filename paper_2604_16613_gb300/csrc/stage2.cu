@@ -1,5 +1,7 @@
 // stage2.cu -- probability aggregation (Sec. 3.2) and the adjoint.
 //
+// scatter    records of stage 1 {mechanism, column, word} are appended to
+//            per-mechanism slots (the pool cleans itself as it is read)
 // group      one thread per mechanism: sort its mask words by column, hash
 //            them, insert into an open-addressing table whose claims are
 //            verified word by word (so grouping is exact whatever the hash
@@ -46,6 +48,24 @@ __device__ __forceinline__ bool same_mask(const Buffers &B, uint32_t rep, uint32
     for (uint32_t i = 0; i < cnt; i++)
         if (c2[i] != col[i] || w2[i] != w[i]) return false;
     return true;
+}
+
+__global__ void scatter_kernel(Buffers B) {
+    if (*(volatile uint32_t *)&B.status->code != 0u) return;
+    const Params &P = *B.params;
+    const uint32_t n = min(B.status->rec_count, P.rec_cap), S = P.mask_words;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint4 r = B.records[i];
+        if (r.x == kNone) continue;
+        B.records[i].x = kNone;
+        const uint32_t pos = atomicAdd(&B.mech_cnt[r.x], 1u);
+        if (pos < S) {
+            B.slot_col[(size_t)r.x * S + pos] = r.y;
+            B.slot_word[(size_t)r.x * S + pos] = ((unsigned long long)r.w << 32) | r.z;
+        } else {
+            report(B.status, GP_ERR_CAPACITY, 4u, r.x, pos + 1);
+        }
+    }
 }
 
 __global__ void group_kernel(Buffers B) {
@@ -226,9 +246,17 @@ __global__ void __launch_bounds__(kScanThreads) compact_write_kernel(Buffers B) 
         B.class_slot[e] = slot;
         B.edge_circ[e] = b;
         B.tab_class[slot] = e;
-        atomicAdd(&B.circ_edges[b], 1u);
         d = dd;
         e++;
+    }
+    // edges per circuit: one atomic per circuit present in the warp
+    for (int i = 0; i < kPerThread; i++) {
+        const uint32_t m = m0 + threadIdx.x * kPerThread + i;
+        const bool lead = v[i].x != 0u;
+        const uint32_t b = lead ? (uint32_t)(B.mech_info[m] >> 48) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
+        if (lead && (__ffs(peers) - 1) == (int)(threadIdx.x & 31u))
+            atomicAdd(&B.circ_edges[b], (uint32_t)__popc(peers));
     }
 }
 
@@ -288,11 +316,10 @@ __global__ void backward_loc_kernel(Buffers B, float *g_noise, uint32_t n_loc) {
 
 }  // namespace
 
-void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
-                  uint32_t *launches) {
-    (void)max_mech;
+void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches) {
+    scatter_kernel<<<grid, threads, 0, s>>>(b);
     group_kernel<<<grid, threads, 0, s>>>(b);
-    *launches += 1;
+    *launches += 2;
 }
 
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_scan_blocks,

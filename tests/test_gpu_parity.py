@@ -207,10 +207,13 @@ def test_error_paths_and_recovery():
     expect_error(native.GP_ERR_CAPACITY, lambda: small2.compile(wide, wide.default_noise))
     # too many circuits for the bounds
     expect_error(native.GP_ERR_CAPACITY, lambda: drv.compile([good, good], np.concatenate([noise, noise])))
-    # the drivers still work after every failure
-    for dv in (drv, small2):
-        ok = dv.compile(good, f32(noise)).edges()
-        compare_edges(ok, oracle_edges(good, noise).edges(), "after errors")
+    # the drivers still work after every failure (a one-word bound still
+    # serves circuits whose masks fit one word: no observable, 64 detectors)
+    ok = drv.compile(good, f32(noise)).edges()
+    compare_edges(ok, oracle_edges(good, noise).edges(), "after errors")
+    narrow = C.repetition_code_memory(5, 3, C.NoiseModel.uniform(1e-3), final_data=False)
+    ok2 = small2.compile(narrow, f32(narrow.default_noise)).edges()
+    compare_edges(ok2, oracle_edges(narrow, narrow.default_noise).edges(), "narrow after errors")
 
 
 # ---------------------------------------------------------------------------
