@@ -134,7 +134,14 @@ typedef struct {
     const float *prob;            /* P of the class (Eq. pmerge), FP32        */
     const float *logodds;         /* w = log((1 - P) / P), FP32               */
     const uint32_t *edge_circuit; /* circuit of each edge                     */
-    const int32_t *mech_class;    /* n_mechanisms: edge of each mechanism or -1 */
+    const int32_t *mech_class;    /* n_mechanisms: edge of each mechanism or -1.
+                                     Mechanisms are numbered circuit by circuit,
+                                     noise rows in row order, and within a row
+                                     the components in the order of
+                                     tab:correlation-level (one-qubit channels
+                                     X, Z, Y; two-qubit IX IZ XI XX ZI ZZ, then
+                                     IY XZ YI ZX, then XY YX YY YZ ZY), keeping
+                                     only those of the compile's level.       */
     const uint32_t *edge_offsets; /* HOST array, n_circuits + 1: circuit b owns
                                      edges [edge_offsets[b], edge_offsets[b+1]) */
 } gp_dem_view;
@@ -207,6 +214,33 @@ uint32_t gp_last_launch_count(const gp_driver *drv);
 
 /* Thread-local message describing the last failure on this thread. */
 const char *gp_last_error(void);
+
+/* Class probabilities for callers that may not allocate device memory.
+ *
+ * (The paper has no counterpart: this is a service entry point.)  A decoder
+ * host in a real-time feedback loop with a fixed memory budget, or a process
+ * whose device memory is owned by another framework, may be unable to call
+ * cudaMalloc: it cannot take the allocator's device-wide locks or accept the
+ * implicit synchronisation an allocation can bring.  This call needs no
+ * driver and allocates nothing.  Given, in device memory, the class of each
+ * of n_mech mechanisms (mech_class[i] in [0, n_classes), anything else is
+ * skipped) and each mechanism's component probability q[i] in [0, 1/2], it
+ * writes prob[c] = (1 - prod_{i in c} (1 - 2 q_i)) / 2 and, if logodds is not
+ * NULL, logodds[c] = log((1 - prob[c]) / prob[c]) for every class c, exactly
+ * as gp_compile combines the members of a class.  All pointers are device
+ * pointers owned by the caller; work is queued on `stream` and the call
+ * returns without waiting for it.
+ *
+ * Its scratch is a built-in device array of 2^19 classes (8 MiB), which every
+ * GPU that loads the library keeps until the process exits.  More than
+ * 524,288 classes gives GP_ERR_CAPACITY.  The first call on a device looks up
+ * that array's address on the current device and remembers it; make that
+ * first call before any stream capture.  Each call zeroes the part of the
+ * array it uses before using it, but all calls share the one array: calls
+ * whose work overlaps on the GPU (different streams or host threads) race and
+ * must be serialised by the caller. */
+gp_status gp_pmerge_noalloc(const int32_t *mech_class, const float *q, uint32_t n_mech,
+                            uint32_t n_classes, float *prob, float *logodds, void *stream);
 
 #ifdef __cplusplus
 }

@@ -138,6 +138,11 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
 
 }  // namespace
 
+namespace gpdem {
+// lets other translation units report through gp_last_error()
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace gpdem
+
 struct gp_driver {
     gp_bounds bounds{};
     Layout L{};

@@ -21,7 +21,7 @@ LEVELS = {"L0": 0, "L1": 1, "L2": 2, 0: 0, 1: 1, 2: 2}
 EXPORTED = [
     "gp_workspace_size", "gp_driver_create", "gp_driver_destroy", "gp_compile_batch", "gp_compile",
     "gp_backward", "gp_result_view", "gp_set_tuning", "gp_get_tuning", "gp_enable_timing",
-    "gp_last_timing", "gp_last_launch_count", "gp_last_error",
+    "gp_last_timing", "gp_last_launch_count", "gp_last_error", "gp_pmerge_noalloc",
 ]
 
 
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         lib.gp_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.gp_last_launch_count.argtypes = [vp]
         lib.gp_last_launch_count.restype = u32
+        lib.gp_pmerge_noalloc.argtypes = [vp, vp, u32, u32, vp, vp, vp]
+        lib.gp_pmerge_noalloc.restype = i32
         lib.gp_last_error.argtypes = []
         lib.gp_last_error.restype = ctypes.c_char_p
         for name in ("gp_workspace_size", "gp_driver_create", "gp_compile_batch", "gp_compile",
