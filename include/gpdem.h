@@ -112,8 +112,10 @@ typedef struct {
     uint32_t max_detectors;       /* total detectors                          */
     uint32_t max_locations;       /* total noise locations                    */
     uint32_t max_mechanisms;      /* total error mechanisms                   */
-    uint32_t max_mask_words;      /* non-zero 64-bit words per mechanism mask
-                                     (0 = default 8, at most 16)             */
+    uint32_t max_mask_words;      /* non-zero 64-bit words in one mechanism's
+                                     mask (0 = default 16, at most 16); the
+                                     pool for all words holds 4 per mechanism
+                                     of max_mechanisms on average            */
     uint64_t max_det_entries;     /* total detector ids over all hyperedges
                                      (0 = 16 x max_mechanisms)                */
 } gp_bounds;

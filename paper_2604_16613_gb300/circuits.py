@@ -728,3 +728,356 @@ def random_circuit(seed: int, n_qubits: int | None = None, n_blocks: int | None 
             sel = rng.choice(pool, size=min(len(pool), int(rng.integers(1, 4))), replace=False)
             c.observable(k, [int(x) for x in sel])
     return c
+
+
+# ---------------------------------------------------------------------------
+# GF(2) helpers for code construction (inputs only)
+# ---------------------------------------------------------------------------
+
+def _gf2_rank_basis(rows: np.ndarray):
+    """Row-echelon form over GF(2); returns (echelon rows, pivot columns)."""
+    m = rows.copy().astype(np.uint8) & 1
+    piv = []
+    r = 0
+    for c in range(m.shape[1]):
+        if r >= m.shape[0]:
+            break
+        nz = np.flatnonzero(m[r:, c])
+        if nz.size == 0:
+            continue
+        p = r + nz[0]
+        if p != r:
+            m[[r, p]] = m[[p, r]]
+        others = np.flatnonzero(m[:, c])
+        others = others[others != r]
+        m[others] ^= m[r]
+        piv.append(c)
+        r += 1
+    return m[:r], piv
+
+
+def _gf2_kernel(h: np.ndarray) -> np.ndarray:
+    """Basis of {v : h v = 0} over GF(2) (rows of the result)."""
+    ech, piv = _gf2_rank_basis(h)
+    n = h.shape[1]
+    free = [c for c in range(n) if c not in set(piv)]
+    basis = []
+    for f in free:
+        v = np.zeros(n, dtype=np.uint8)
+        v[f] = 1
+        for i, pc in enumerate(piv):
+            if ech[i, f]:
+                v[pc] = 1
+        basis.append(v)
+    return np.array(basis, dtype=np.uint8).reshape(-1, n)
+
+
+def _greedy_colouring(edges, rng) -> list:
+    """Greedy proper edge colouring of a bipartite multigraph given as (u, v)
+    pairs in a seeded random order; returns one list of edges per colour."""
+    order = rng.permutation(len(edges))
+    used_u: dict = {}
+    used_v: dict = {}
+    colours: list = []
+    for i in order:
+        u, v = edges[i]
+        cu, cv = used_u.setdefault(u, set()), used_v.setdefault(v, set())
+        c = 0
+        while c in cu or c in cv:
+            c += 1
+        cu.add(c)
+        cv.add(c)
+        while len(colours) <= c:
+            colours.append([])
+        colours[c].append((u, v))
+    return colours
+
+
+# ---------------------------------------------------------------------------
+# Bivariate bicycle code [[144, 12, 12]] (Sec. 4), Z-basis memory
+# ---------------------------------------------------------------------------
+
+def bb_check_matrices(l: int = 12, m: int = 6):
+    """H_X = [A | B], H_Z = [B^T | A^T] with A = x^3 + y + y^2 and
+    B = y^3 + x + x^2, x = S_l (x) I_m and y = I_l (x) S_m (cyclic shifts)."""
+    Sl = np.roll(np.eye(l, dtype=np.uint8), 1, axis=1)
+    Sm = np.roll(np.eye(m, dtype=np.uint8), 1, axis=1)
+    x = np.kron(Sl, np.eye(m, dtype=np.uint8))
+    y = np.kron(np.eye(l, dtype=np.uint8), Sm)
+    mp = np.linalg.matrix_power
+    A = (mp(x, 3) + y + mp(y, 2)) % 2
+    B = (mp(y, 3) + x + mp(x, 2)) % 2
+    hx = np.concatenate([A, B], axis=1).astype(np.uint8)
+    hz = np.concatenate([B.T, A.T], axis=1).astype(np.uint8)
+    return hx, hz
+
+
+def z_logicals(hx: np.ndarray, hz: np.ndarray) -> np.ndarray:
+    """A basis of Z-type logical operators: kernel of H_X modulo the row space
+    of H_Z (rows of the result)."""
+    ker = _gf2_kernel(hx)
+    ech, _ = _gf2_rank_basis(hz)
+    rank = ech.shape[0]
+    out = []
+    cur = ech
+    for v in ker:
+        trial, _ = _gf2_rank_basis(np.vstack([cur, v[None, :]]))
+        if trial.shape[0] > rank:
+            out.append(v)
+            cur, rank = trial, trial.shape[0]
+    return np.array(out, dtype=np.uint8)
+
+
+def css_memory_circuit(hx, hz, zlog, rounds: int, noise: NoiseModel | None, seed: int,
+                       data_qubits=None) -> Circuit:
+    """Z-basis memory of a CSS code with a seeded syndrome circuit.
+
+    Per round: reset ancillas (data too in round 1), H on X ancillas, all
+    Z-check CX layers (data -> ancilla), then all X-check CX layers
+    (ancilla -> data), each block scheduled by a greedy edge colouring of its
+    Tanner graph; H on X ancillas; measure ancillas.  Running the Z checks
+    and X checks as separate blocks keeps the two measurement circuits
+    commuting.  Detectors: Z checks in round 1, every check against its
+    previous outcome afterwards, Z checks closed by the final data
+    measurement; one observable per row of zlog.
+    """
+    n = hx.shape[1]
+    nx, nz = hx.shape[0], hz.shape[0]
+    data = np.arange(n)
+    xanc = np.arange(n, n + nx)
+    zanc = np.arange(n + nx, n + nx + nz)
+    c = Circuit(n + nx + nz)
+    allq = np.arange(c.n_qubits)
+    rng = rng_for(seed, 3)
+    z_edges = [(int(zanc[i]), int(j)) for i in range(nz) for j in np.flatnonzero(hz[i])]
+    x_edges = [(int(xanc[i]), int(j)) for i in range(nx) for j in np.flatnonzero(hx[i])]
+    z_layers = _greedy_colouring(z_edges, rng)
+    x_layers = _greedy_colouring(x_edges, rng)
+    anc = np.concatenate([xanc, zanc])
+    prev = None
+    for r in range(rounds):
+        L = _Layer(c, noise, allq)
+        L.reset(allq if r == 0 else anc)
+        L.close()
+        L = _Layer(c, noise, allq)
+        L.single(H, xanc)
+        L.close()
+        for layer in z_layers:
+            L = _Layer(c, noise, allq)
+            L.two(CX, [(d_, a) for a, d_ in layer])
+            L.close()
+        for layer in x_layers:
+            L = _Layer(c, noise, allq)
+            L.two(CX, [(a, d_) for a, d_ in layer])
+            L.close()
+        L = _Layer(c, noise, allq)
+        L.single(H, xanc)
+        L.close()
+        L = _Layer(c, noise, allq)
+        rec = L.measure(anc)
+        L.close(tick=False)
+        if prev is None:
+            c.detectors([[rec[nx + i]] for i in range(nz)])
+        else:
+            c.detectors([[m_, pm] for m_, pm in zip(rec, prev)])
+        prev = rec
+        c.tick()
+    L = _Layer(c, noise, allq)
+    drec = L.measure(data)
+    L.close(tick=False)
+    c.detectors([[drec[j] for j in np.flatnonzero(hz[i])] + [prev[nx + i]] for i in range(nz)])
+    for k, lg in enumerate(zlog):
+        c.observable(k, [drec[j] for j in np.flatnonzero(lg)])
+    return c
+
+
+def bb_memory(rounds: int = 12, noise: NoiseModel | None = None, seed: int = 3) -> Circuit:
+    """[[144,12,12]] bivariate bicycle Z-memory (workload of config 3)."""
+    hx, hz = bb_check_matrices(12, 6)
+    zl = z_logicals(hx, hz)
+    return css_memory_circuit(hx, hz, zl, rounds, noise, seed)
+
+
+# ---------------------------------------------------------------------------
+# Adaptive [[4,2,2]]-concatenated rotated surface code (Sec. 5)
+# ---------------------------------------------------------------------------
+
+def iceberg_pairs(d: int) -> list:
+    """Pairs of outer data qubits sharing one [[4,2,2]] block.
+
+    Eq. iceberg-mapping sends (r, c) to (d-1-r, (c+2) mod d).  That map is an
+    involution only when d is a multiple of 4, so the pairs are taken along
+    its orbits (each orbit has even length because the row flips at every
+    step): consecutive orbit elements are paired, starting from the smallest
+    row-major index.  Qubit index = r * d + c.
+    """
+    seen = set()
+    pairs = []
+    for start in range(d * d):
+        if start in seen:
+            continue
+        orbit = []
+        q = start
+        while q not in orbit:
+            orbit.append(q)
+            r, cc = divmod(q, d)
+            q = (d - 1 - r) * d + (cc + 2) % d
+        assert len(orbit) % 2 == 0
+        for i in range(0, len(orbit), 2):
+            pairs.append((orbit[i], orbit[i + 1]))
+        seen.update(orbit)
+    return pairs
+
+
+class ConcatenatedLayout:
+    """Physical layout of the [[4,2,2]]-concatenated rotated surface code.
+
+    Each block holds physical qubits p0..p3 with stabilisers XXXX and ZZZZ and
+    two logical qubits: logical 1 has X1 = X p0 p1, Z1 = Z p0 p2; logical 2
+    has X2 = X p0 p2, Z2 = Z p0 p1.  Outer data qubit q is logical j of block
+    b; an outer check is the product of the matching logical operators.
+    """
+
+    def __init__(self, d: int):
+        self.d = d
+        self.surface = rotated_surface_layout(d)
+        pairs = iceberg_pairs(d)
+        self.n_blocks = len(pairs)
+        self.block_of = {}
+        for b, (q1, q2) in enumerate(pairs):
+            self.block_of[q1] = (b, 1)
+            self.block_of[q2] = (b, 2)
+        # outer data index in the surface layout: coordinates -> r*d + c
+        coords = self.surface.data_xy
+        self.outer_id = {i: ((int(y) - 1) // 2) * d + (int(x) - 1) // 2 for i, (x, y) in enumerate(coords.tolist())}
+        nb = self.n_blocks
+        self.phys = np.arange(4 * nb).reshape(nb, 4)
+        self.inner_x = np.arange(4 * nb, 5 * nb)
+        self.inner_z = np.arange(5 * nb, 6 * nb)
+        base = 6 * nb
+        self.outer_checks = []            # (ancilla, is_x, physical support, outer qubits)
+        for is_x, checks in ((True, self.surface.x_checks), (False, self.surface.z_checks)):
+            for _, nb_list in checks:
+                outer = [self.outer_id[q] for q in nb_list if q >= 0]
+                blocks = [self.block_of[o][0] for o in outer]
+                assert len(set(blocks)) == len(blocks), "two qubits of one block in a check"
+                sup = set()
+                for o in outer:
+                    b, j = self.block_of[o]
+                    p = self.phys[b]
+                    if is_x:
+                        op = (p[0], p[1]) if j == 1 else (p[0], p[2])
+                    else:
+                        op = (p[0], p[2]) if j == 1 else (p[0], p[1])
+                    sup ^= set(int(v) for v in op)
+                self.outer_checks.append((base, is_x, sorted(sup), outer))
+                base += 1
+        self.n_qubits = base
+        # Z_L of the outer code on the data row y = 1 -> physical support
+        zl = set()
+        for i in self.surface.z_logical:
+            b, j = self.block_of[self.outer_id[int(i)]]
+            p = self.phys[b]
+            zl ^= set(int(v) for v in ((p[0], p[2]) if j == 1 else (p[0], p[1])))
+        self.z_logical = sorted(zl)
+
+
+def concatenated_adaptive_branch(d: int = 10, cycles: int = 20, seed: int = 0, fire_rate: float = 0.05,
+                                 noise: NoiseModel | None = None, layout: ConcatenatedLayout | None = None
+                                 ) -> Circuit:
+    """One realised branch of the adaptive [[4,2,2]]-concatenated surface-code
+    memory (Sec. 5.1-5.2; workload of config 4).
+
+    Every cycle measures all inner checks (ZZZZ block, then XXXX block).  The
+    outer checks run in the first and last cycle and every gamma = d/2 cycles
+    (Sec. 5.2.3); in other cycles only the outer checks touching a block whose
+    inner syndrome fired run, a block firing with seeded Bernoulli(fire_rate)
+    per cycle.  Detectors are instantiated dynamically (Sec. 5.2.4): a check
+    gets a detector when it runs and has a previous outcome; Z-type checks
+    also on their first run (deterministic from |0>).  The final cycle
+    measures the physical data: inner ZZZZ and outer Z checks are closed and
+    the outer Z_L is observable 0.
+    """
+    lay = layout or ConcatenatedLayout(d)
+    rng = rng_for(seed, 4)
+    gamma = max(1, d // 2)
+    c = Circuit(lay.n_qubits)
+    allq = np.arange(lay.n_qubits)
+    phys = lay.phys.reshape(-1)
+    last = {}                        # check id -> last measurement record
+
+    def run_checks(checks):
+        """checks: list of (id, ancilla, is_x, physical support)."""
+        if not checks:
+            return
+        anc = np.array([a for _, a, _, _ in checks])
+        xanc = np.array([a for _, a, ix, _ in checks if ix], dtype=np.int64)
+        L = _Layer(c, noise, allq)
+        L.reset(anc)
+        L.close()
+        L = _Layer(c, noise, allq)
+        L.single(H, xanc)
+        L.close()
+        for want_x in (False, True):
+            edges = [(a, q) for _, a, ix, sup in checks if ix == want_x for q in sup]
+            for layer in _greedy_colouring(edges, rng):
+                L = _Layer(c, noise, allq)
+                L.two(CX, [(a, q) if want_x else (q, a) for a, q in layer])
+                L.close()
+        L = _Layer(c, noise, allq)
+        L.single(H, xanc)
+        L.close()
+        L = _Layer(c, noise, allq)
+        rec = L.measure(anc)
+        L.close(tick=False)
+        groups = []
+        for (cid, a, ix, sup), m_ in zip(checks, rec):
+            if cid in last:
+                groups.append([m_, last[cid]])
+            elif not ix:
+                groups.append([m_])
+            last[cid] = m_
+        c.detectors(groups)
+        c.tick()
+
+    L = _Layer(c, noise, allq)
+    L.reset(phys)
+    L.close()
+    inner = []
+    for b in range(lay.n_blocks):
+        inner.append((("iz", b), int(lay.inner_z[b]), False, [int(v) for v in lay.phys[b]]))
+        inner.append((("ix", b), int(lay.inner_x[b]), True, [int(v) for v in lay.phys[b]]))
+    outer = [(("o", i), a, ix, sup) for i, (a, ix, sup, _) in enumerate(lay.outer_checks)]
+    touches = [set(lay.block_of[o][0] for o in og) for (_, _, _, og) in lay.outer_checks]
+    for t in range(cycles):
+        run_checks(inner)
+        if t == 0 or t == cycles - 1 or t % gamma == 0:
+            active = outer
+        else:
+            fired = set(np.flatnonzero(rng.random(lay.n_blocks) < fire_rate).tolist())
+            active = [oc for oc, tb in zip(outer, touches) if tb & fired]
+        run_checks(active)
+    L = _Layer(c, noise, allq)
+    drec = L.measure(phys)
+    L.close(tick=False)
+    pos = {int(q): i for i, q in enumerate(phys)}
+    groups = []
+    for b in range(lay.n_blocks):
+        groups.append([drec[pos[int(q)]] for q in lay.phys[b]] + [last[("iz", b)]])
+    for i, (a, ix, sup, _) in enumerate(lay.outer_checks):
+        if not ix:
+            groups.append([drec[pos[q]] for q in sup] + [last[("o", i)]])
+    c.detectors(groups)
+    c.observable(0, [drec[pos[q]] for q in lay.z_logical])
+    return c
+
+
+def adaptive_branches(n: int = 256, d: int = 10, lo: int = 10, hi: int = 30, seed: int = 4,
+                      noise: NoiseModel | None = None) -> list:
+    """n realised branches with cycle counts U{lo..hi} (config 4)."""
+    lay = ConcatenatedLayout(d)
+    r = rng_for(seed, 5)
+    lengths = r.integers(lo, hi + 1, size=n)
+    nm = noise or NoiseModel.uniform(1e-3)
+    return [concatenated_adaptive_branch(d, int(lengths[i]), seed=seed * 100003 + i, noise=nm, layout=lay)
+            for i in range(n)]

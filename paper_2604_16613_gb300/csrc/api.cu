@@ -72,15 +72,18 @@ Layout make_layout(const gp_bounds &b) {
     L.max_tiles = (uint32_t)((b.max_ops + kRowTile - 1) / kRowTile) + b.max_circuits;
     L.max_cols = b.max_detectors / 64u + 2u * b.max_circuits + 1u;
     L.max_layer_slots = b.max_layers + 2u * b.max_circuits;
-    L.S = b.max_mask_words ? b.max_mask_words : 8u;
+    L.S = b.max_mask_words ? b.max_mask_words : (uint32_t)kMaxMaskWords;
+    // classes never outnumber mechanisms: at least 1.5 slots per mechanism
+    // keeps the open-addressing load factor below 2/3
     uint32_t lg = 10;
-    while ((1ull << lg) < 2ull * b.max_mechanisms) lg++;
+    while ((double)(1ull << lg) < 1.5 * (double)b.max_mechanisms) lg++;
     L.table_log2 = lg;
     L.max_scan_blocks = (b.max_mechanisms + kMechPerBlockScan - 1) / kMechPerBlockScan;
     L.max_det_entries = b.max_det_entries ? b.max_det_entries : 16ull * b.max_mechanisms;
-    // every mechanism holds at most S words; each stage-1 block may leave
-    // the unused tail of one chunk (at most 1024 resident blocks counted)
-    L.rec_cap = std::min<uint64_t>((uint64_t)b.max_mechanisms * L.S + 1024ull * kChunkRecs, 0xFFFFFFF0ull);
+    // mask words over all mechanisms: four per mechanism on average (the
+    // workloads here average 2 to 2.5), plus the unused chunk tails that
+    // stage-1 blocks may leave (at most 1024 blocks counted)
+    L.rec_cap = std::min<uint64_t>(4ull * b.max_mechanisms + 1024ull * kChunkRecs, 0xFFFFFFF0ull);
     return L;
 }
 
@@ -112,17 +115,22 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     B.obs_rows = c.take<uint32_t>(bd.max_ops);
     B.obs_count = c.take<uint32_t>(bd.max_circuits);
     B.mech_cnt = c.take<uint32_t>(bd.max_mechanisms);
+    B.mech_fill = c.take<uint32_t>(bd.max_mechanisms);
+    B.mech_off = c.take<uint2>((uint64_t)bd.max_mechanisms + 1);
     B.mech_info = c.take<unsigned long long>(bd.max_mechanisms);
-    B.slot_col = c.take<uint32_t>((uint64_t)bd.max_mechanisms * L.S);
-    B.slot_word = c.take<unsigned long long>((uint64_t)bd.max_mechanisms * L.S);
+    B.slot_col = c.take<uint32_t>(L.rec_cap);
+    B.slot_word = c.take<unsigned long long>(L.rec_cap);
     B.slot_of = c.take<uint32_t>(bd.max_mechanisms);
     B.mech_class = c.take<int32_t>(bd.max_mechanisms);
-    B.table = c.take<unsigned long long>(1ull << L.table_log2);
-    B.tab_min = c.take<uint32_t>(1ull << L.table_log2);
-    B.tab_acc = c.take<unsigned long long>(2ull << L.table_log2);
-    B.tab_class = c.take<uint32_t>(1ull << L.table_log2);
-    B.blk_sums = c.take<uint2>(L.max_scan_blocks + 1);
-    B.blk_off = c.take<uint2>(L.max_scan_blocks + 1);
+    B.table = c.take<TabSlot>(1ull << L.table_log2);
+    B.scan_val = c.take<uint2>(bd.max_mechanisms);
+    B.comp_off = c.take<uint2>((uint64_t)bd.max_mechanisms + 1);
+    {
+        const uint64_t nb = ((uint64_t)bd.max_mechanisms + 2047) / 2048;
+        B.scan_bsum = c.take<uint2>(nb + 1);
+        B.scan_bsum2 = c.take<uint2>((nb + 2047) / 2048 + 1);
+        B.scan_total = c.take<uint2>(1);
+    }
     B.det_off = c.take<uint32_t>((uint64_t)bd.max_mechanisms + 1);
     B.det_idx = c.take<uint32_t>(L.max_det_entries);
     B.obs_mask = c.take<unsigned long long>(bd.max_mechanisms);
@@ -163,6 +171,13 @@ struct gp_driver {
     gp_dem_view view{};
     std::vector<uint32_t> edge_offsets;
     uint32_t n_loc_total = 0;
+    // the compile pipeline captured as one CUDA graph (re-captured when the
+    // tuning or the timing switch changes)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool exec_timing = false;
+    gp_tuning exec_tuning{0, 0, 0, 0};
+    uint32_t graph_kernels = 0;
     // tuning / instrumentation
     gp_tuning tuning{512, 0, 256, 8};
     bool timing = false;
@@ -175,10 +190,10 @@ namespace {
 
 gp_status full_reset(gp_driver *d, cudaStream_t s) {
     const Layout &L = d->L;
-    GP_CUDA(cudaMemsetAsync(d->B.table, 0xFF, sizeof(unsigned long long) << L.table_log2, s));
-    GP_CUDA(cudaMemsetAsync(d->B.tab_min, 0xFF, sizeof(uint32_t) << L.table_log2, s));
-    GP_CUDA(cudaMemsetAsync(d->B.tab_acc, 0, (2 * sizeof(unsigned long long)) << L.table_log2, s));
+    launch_init_table(d->B.table, (size_t)1 << L.table_log2, s);
+    GP_CUDA(cudaGetLastError());
     GP_CUDA(cudaMemsetAsync(d->B.mech_cnt, 0, sizeof(uint32_t) * (size_t)d->bounds.max_mechanisms, s));
+    GP_CUDA(cudaMemsetAsync(d->B.mech_fill, 0, sizeof(uint32_t) * (size_t)d->bounds.max_mechanisms, s));
     GP_CUDA(cudaMemsetAsync(d->B.gacc, 0, 2 * sizeof(unsigned long long) * std::max<uint32_t>(d->bounds.max_locations, 1), s));
     GP_CUDA(cudaMemsetAsync(d->B.records, 0xFF, sizeof(uint4) * L.rec_cap, s));
     GP_CUDA(cudaMemsetAsync(d->B.packed, 0, sizeof(uint2) * (d->bounds.max_ops + 4), s));
@@ -216,17 +231,83 @@ std::string describe(const Status &st) {
         if (a == 1) snprintf(buf, sizeof buf, "%u layer slots needed, bound allows %u", b, c);
         else if (a == 2) snprintf(buf, sizeof buf, "%u measurements, bound allows %u", b, c);
         else if (a == 3) snprintf(buf, sizeof buf, "%u mechanisms, bound allows %u", b, c);
-        else if (a == 4) snprintf(buf, sizeof buf, "mechanism %u has at least %u non-zero mask words; raise max_mask_words", b, c);
+        else if (a == 4) snprintf(buf, sizeof buf, "mechanism %u has %u non-zero mask words, more than max_mask_words", b, c);
         else if (a == 5) snprintf(buf, sizeof buf, "word column %u references %u (measurement, detector) pairs; at most %d", b, c, kMaxEntries);
         else if (a == 6) snprintf(buf, sizeof buf, "hash table of %u slots is full", c);
         else if (a == 7) snprintf(buf, sizeof buf, "%u detector ids in the hyperedges, bound allows %u", b, c);
-        else if (a == 8) snprintf(buf, sizeof buf, "mask-word record pool of %u entries is full", c);
+        else if (a == 8) snprintf(buf, sizeof buf, "mask-word pool of %u entries is full (it holds 4 words per mechanism of max_mechanisms on average)", c);
         else snprintf(buf, sizeof buf, "capacity exceeded (%u, %u, %u)", a, b, c);
         break;
     default:
         snprintf(buf, sizeof buf, "%s (%u, %u, %u)", stage_name(st.code), a, b, c);
     }
     return buf;
+}
+
+// Everything a compile runs on the device, with grid sizes fixed by the
+// bounds (work beyond the actual sizes exits at once), so the sequence can be
+// captured once and replayed: parameter upload, lowering, stage 1 (persistent
+// blocks over a work queue), grouping, compaction, status read-back.
+gp_status enqueue_pipeline(gp_driver *d, cudaStream_t s, uint32_t *kernels) {
+    const gp_bounds &bd = d->bounds;
+    const Layout &L = d->L;
+    const uint32_t grid2 = (uint32_t)d->n_sms * d->tuning.stage2_blocks_per_sm;
+    const size_t smem1 = stage1_smem_bytes(bd.max_qubits);
+    int occ = 1;
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage1_kernel_ptr(d->tuning.stage1_threads),
+                                                          (int)d->tuning.stage1_threads, smem1));
+    if (occ < 1) return fail(GP_ERR_CAPACITY, "stage 1 does not fit on an SM with these bounds");
+    const uint32_t bps = d->tuning.stage1_blocks_per_sm ? std::min<uint32_t>(d->tuning.stage1_blocks_per_sm, occ)
+                                                        : (uint32_t)occ;
+    const uint32_t grid1 = std::min<uint32_t>((uint32_t)d->n_sms * bps, std::max<uint32_t>(L.max_cols, 1u));
+    GP_CUDA(cudaMemcpyAsync(d->B.params, d->h_params, d->params_bytes, cudaMemcpyHostToDevice, s));
+    if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[0], s, cudaEventRecordExternal));
+    launch_lowering(d->B, L.max_tiles, L.max_layer_slots, bd.max_qubits, s, kernels);
+    if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[1], s, cudaEventRecordExternal));
+    launch_stage1(d->B, grid1, d->tuning.stage1_threads, bd.max_qubits, s, kernels);
+    if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[2], s, cudaEventRecordExternal));
+    launch_group(d->B, grid2, d->tuning.stage2_threads, bd.max_mechanisms, s, kernels);
+    if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[3], s, cudaEventRecordExternal));
+    launch_compact(d->B, grid2, d->tuning.stage2_threads, bd.max_mechanisms, s, kernels);
+    if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[4], s, cudaEventRecordExternal));
+    GP_CUDA(cudaGetLastError());
+    GP_CUDA(cudaMemcpyAsync(d->h_status, d->B.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(d->h_circ_edges, d->B.circ_edges, sizeof(uint32_t) * bd.max_circuits,
+                            cudaMemcpyDeviceToHost, s));
+    return GP_OK;
+}
+
+bool same_tuning(const gp_tuning &a, const gp_tuning &b) {
+    return a.stage1_threads == b.stage1_threads && a.stage1_blocks_per_sm == b.stage1_blocks_per_sm &&
+           a.stage2_threads == b.stage2_threads && a.stage2_blocks_per_sm == b.stage2_blocks_per_sm;
+}
+
+gp_status ensure_graph(gp_driver *d) {
+    if (d->exec && d->exec_timing == d->timing && same_tuning(d->exec_tuning, d->tuning)) return GP_OK;
+    if (d->exec) {
+        cudaGraphExecDestroy(d->exec);
+        d->exec = nullptr;
+    }
+    uint32_t kernels = 0;
+    GP_CUDA(cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const gp_status st = enqueue_pipeline(d, d->cap_stream, &kernels);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(d->cap_stream, &g);
+    if (st != GP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(GP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&d->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        d->exec = nullptr;
+        return fail(GP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+    }
+    d->exec_timing = d->timing;
+    d->exec_tuning = d->tuning;
+    d->graph_kernels = kernels;
+    return GP_OK;
 }
 
 }  // namespace
@@ -283,6 +364,8 @@ gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace, uint64_t 
         return cleanup(fail(GP_ERR_CUDA, "cudaMallocHost staging failed"));
     for (int i = 0; i < 5; i++)
         if (cudaEventCreate(&d->ev[i]) != cudaSuccess) return cleanup(fail(GP_ERR_CUDA, "cudaEventCreate failed"));
+    if (cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup(fail(GP_ERR_CUDA, "cudaStreamCreate failed"));
     // initial state of the self-cleaning structures
     cudaStream_t s = 0;
     gp_status st = full_reset(d, s);
@@ -308,6 +391,8 @@ void gp_driver_destroy(gp_driver *d) {
     if (d->h_noise) cudaFreeHost(d->h_noise);
     for (int i = 0; i < 5; i++)
         if (d->ev[i]) cudaEventDestroy(d->ev[i]);
+    if (d->exec) cudaGraphExecDestroy(d->exec);
+    if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
     delete d;
 }
 
@@ -473,30 +558,13 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     P->max_ops = (uint32_t)bd.max_ops;
     P->rec_cap = (uint32_t)L.rec_cap;
     P->max_qubits = bd.max_qubits;
-    GP_CUDA(cudaMemcpyAsync(d->B.params, d->h_params, d->params_bytes, cudaMemcpyHostToDevice, s));
-
-    // ---- pipeline ------------------------------------------------------------
-    const uint32_t grid2 = (uint32_t)d->n_sms * d->tuning.stage2_blocks_per_sm;
-    const size_t smem1 = stage1_smem_bytes(bd.max_qubits);
-    int occ = 1;
-    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage1_kernel_ptr(d->tuning.stage1_threads),
-                                                          (int)d->tuning.stage1_threads, smem1));
-    if (occ < 1) return fail(GP_ERR_CAPACITY, "stage 1 does not fit on an SM with these bounds");
-    uint32_t bps = d->tuning.stage1_blocks_per_sm ? std::min<uint32_t>(d->tuning.stage1_blocks_per_sm, occ) : (uint32_t)occ;
-    const uint32_t grid1 = std::max<uint32_t>(1u, std::min<uint32_t>(ni, (uint32_t)d->n_sms * bps));
-
-    if (d->timing) GP_CUDA(cudaEventRecord(d->ev[0], s));
-    launch_lowering(d->B, tiles_total, L.max_layer_slots, bd.max_qubits, s, &d->launches);
-    if (d->timing) GP_CUDA(cudaEventRecord(d->ev[1], s));
-    launch_stage1(d->B, grid1, d->tuning.stage1_threads, bd.max_qubits, s, &d->launches);
-    if (d->timing) GP_CUDA(cudaEventRecord(d->ev[2], s));
-    launch_group(d->B, grid2, d->tuning.stage2_threads, s, &d->launches);
-    if (d->timing) GP_CUDA(cudaEventRecord(d->ev[3], s));
-    launch_compact(d->B, grid2, d->tuning.stage2_threads, L.max_scan_blocks, bd.max_mechanisms, s, &d->launches);
-    if (d->timing) GP_CUDA(cudaEventRecord(d->ev[4], s));
-    GP_CUDA(cudaGetLastError());
-    GP_CUDA(cudaMemcpyAsync(d->h_status, d->B.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaMemcpyAsync(d->h_circ_edges, d->B.circ_edges, sizeof(uint32_t) * n_circuits, cudaMemcpyDeviceToHost, s));
+    // ---- pipeline: one graph launch ----------------------------------------------
+    {
+        const gp_status gs = ensure_graph(d);
+        if (gs != GP_OK) return gs;
+    }
+    GP_CUDA(cudaGraphLaunch(d->exec, s));
+    d->launches = d->graph_kernels;
     GP_CUDA(cudaStreamSynchronize(s));
     if (d->timing) {
         for (int i = 0; i < 4; i++) {

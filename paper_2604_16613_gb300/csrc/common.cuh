@@ -79,6 +79,16 @@ struct Status {
     uint32_t pad[6];
 };
 
+// one slot of the grouping hash table (one 32-byte sector)
+struct TabSlot {
+    unsigned long long entry;   // key_hi << 32 | claiming mechanism, or kEmpty
+    uint32_t min;               // smallest member mechanism
+    uint32_t cls;               // hyperedge index once compacted
+    unsigned long long acc_lo;  // 128-bit fixed-point sum of t over members
+    unsigned long long acc_hi;
+};
+static_assert(sizeof(TabSlot) == 32, "TabSlot is one sector");
+
 // all device buffers of a driver (pointers into the workspace)
 struct Buffers {
     Params *params;
@@ -101,17 +111,19 @@ struct Buffers {
     uint32_t *det_row;          // per detector: its row
     uint32_t *obs_rows;         // per circuit (at op_base): OBSERVABLE rows
     uint32_t *obs_count;        // per circuit
-    uint32_t *mech_cnt;         // per mechanism: mask words received
+    uint32_t *mech_cnt;         // per mechanism: mask words produced (stage 1)
+    uint32_t *mech_fill;        // per mechanism: words placed so far (scatter)
+    uint2 *mech_off;            // per mechanism: start of its words (.x), n + 1
     unsigned long long *mech_info;   // loc | kind << 32 | comp << 40 | circuit << 48
-    uint32_t *slot_col;         // [mech][S] column ids (kObsColFlag on obs)
-    unsigned long long *slot_word;   // [mech][S] mask words
+    uint32_t *slot_col;         // mask words in mechanism order: column ids
+                                // (kObsColFlag on the observable word)
+    unsigned long long *slot_word;   // ... and the words
     uint32_t *slot_of;          // per mechanism: hash-table slot or kNone
     int32_t *mech_class;        // per mechanism: edge or -1
-    unsigned long long *table;  // hash table entries (key_hi << 32 | rep)
-    uint32_t *tab_min;          // smallest member per slot
-    unsigned long long *tab_acc;// 128-bit fixed-point sums (lo, hi) per slot
-    uint32_t *tab_class;        // edge per slot
-    uint2 *blk_sums, *blk_off;  // compaction scan
+    TabSlot *table;             // grouping hash table
+    uint2 *scan_val;            // per mechanism: scan input
+    uint2 *comp_off;            // per mechanism: (edge, detector id) offsets, n + 1
+    uint2 *scan_bsum, *scan_bsum2, *scan_total;   // scan levels
     uint32_t *det_off;          // n_edges + 1
     uint32_t *det_idx;
     unsigned long long *obs_mask;
@@ -352,8 +364,9 @@ void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, u
 void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_qubits, cudaStream_t s, uint32_t *launches);
 size_t stage1_smem_bytes(uint32_t max_qubits);
 const void *stage1_kernel_ptr(uint32_t threads);
-void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches);
-void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_scan_blocks, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
+void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
+void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
+void launch_init_table(TabSlot *t, size_t n, cudaStream_t s);
 void launch_backward(const Buffers &b, const float *g_prob, const float *g_logodds, float *g_noise,
                      uint32_t n_mech, uint32_t n_loc, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches);
 }  // namespace gpdem

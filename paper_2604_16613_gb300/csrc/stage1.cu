@@ -171,8 +171,12 @@ __device__ __forceinline__ void emit_active(const Buffers &B, const Smem &s, Sha
                 s.st_word[pos] = w;
             } else {
                 const uint32_t g = atomicAdd(&B.status->rec_count, 1u);
-                if (g < rec_cap) B.records[g] = make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
-                else report(B.status, GP_ERR_CAPACITY, 8u, g, rec_cap);
+                if (g < rec_cap) {
+                    B.records[g] = make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+                    atomicAdd(&B.mech_cnt[mech], 1u);
+                } else {
+                    report(B.status, GP_ERR_CAPACITY, 8u, g, rec_cap);
+                }
             }
         }
     }
@@ -236,7 +240,9 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
         if (sh.chunk_end - sh.chunk_pos < n) return;    // capacity already reported
         for (uint32_t i = threadIdx.x; i < n; i += NT) {
             const unsigned long long w = s.st_word[i];
-            B.records[sh.chunk_pos + i] = make_uint4(s.st_mech[i], col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+            const uint32_t mech = s.st_mech[i];
+            B.records[sh.chunk_pos + i] = make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+            atomicAdd(&B.mech_cnt[mech], 1u);
         }
     };
 

@@ -1,36 +1,203 @@
 // stage2.cu -- probability aggregation (Sec. 3.2) and the adjoint.
 //
-// scatter    records of stage 1 {mechanism, column, word} are appended to
-//            per-mechanism slots (the pool cleans itself as it is read)
-// group      one thread per mechanism: sort its mask words by column, hash
-//            them, insert into an open-addressing table whose claims are
-//            verified word by word (so grouping is exact whatever the hash
-//            does), and add t_i = -log(1 - 2 q_i) to the class sum as an
-//            exact 128-bit fixed-point integer.  Sums of t give
-//            1 - 2P = prod(1 - 2 q_i) = exp(-sum t_i) (Eq. pmerge), and integer
-//            addition makes them independent of the order the atomics land.
-// compact    classes are numbered by their smallest mechanism id (a scan of
-//            "is leader" flags), then each leader writes its hyperedge: the
-//            ascending detector list, the observable word, P = -expm1(-T)/2 and
-//            w = log1p(-P) - log(P).
-// finalize   per-mechanism class ids; the table slots that were used are
-//            cleared for the next compile.
-// backward   dP/dp_i = (1 - 2P)/2 * dt_i/dp and dw/dP = -1 / (P (1 - P)),
-//            summed per noise location in fixed point.
+// Stage 1 leaves mask-word records {mechanism, column, word} in a pool and a
+// word count per mechanism.  Stage 2:
+//   offsets    exclusive scan of the counts -> per-mechanism word ranges (CSR)
+//   scatter    records -> their mechanism's range (the pool cleans itself)
+//   group      one thread per mechanism: sort its words by column, hash them,
+//              claim or join a slot of an open-addressing table whose claims
+//              are verified word by word (grouping is exact whatever the hash
+//              does), keep the smallest member, and add t_i = -log(1 - 2 q_i)
+//              to the class sum as an exact 128-bit fixed-point integer:
+//              1 - 2P = prod(1 - 2 q_i) = exp(-sum t_i) (Eq. pmerge), and
+//              integer addition makes the sum independent of the order in
+//              which the atomics land
+//   compact    classes are numbered by their smallest member (scan of
+//              "leader" flags and detector counts), each leader writes its
+//              hyperedge: ascending detector ids, observable word,
+//              P = -expm1(-T) / 2 and w = log1p(-P) - log(P)
+//   finalize   per-mechanism class ids; counters and used table slots are
+//              cleared for the next compile
+//   backward   dP/dp_i = (1 - 2P) / 2 * dt_i/dp and dw/dP = -1 / (P (1 - P)),
+//              summed per noise location in fixed point
+// The scans are three-level reduce-then-scan passes (2048 elements per
+// block) with every grid fixed by the driver's bounds, so the whole sequence
+// can be captured once and replayed.
 #include "common.cuh"
 
 namespace gpdem {
 
 namespace {
 
-// Load the mask words of mechanism m, sorted by column id (insertion sort;
-// masks hold a handful of words).
-__device__ __forceinline__ uint32_t load_sorted(const Buffers &B, uint32_t m, uint32_t S, uint32_t cnt,
-                                                uint32_t *col, unsigned long long *w) {
-    const size_t base = (size_t)m * S;
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;                          // elements per thread
+constexpr uint32_t kScanBlock = kScanThreads * kScanPer;
+
+__device__ __forceinline__ uint2 add2(uint2 a, uint2 b) { return make_uint2(a.x + b.x, a.y + b.y); }
+
+// block-wide exclusive scan of two channels
+__device__ __forceinline__ uint2 block_scan2(uint2 v, uint32_t *tmp, uint2 &total) {
+    uint32_t tx, ty;
+    const uint32_t ex = block_exclusive_scan<kScanThreads>(v.x, tmp, tx);
+    const uint32_t ey = block_exclusive_scan<kScanThreads>(v.y, tmp, ty);
+    total = make_uint2(tx, ty);
+    return make_uint2(ex, ey);
+}
+
+// ---- hierarchical exclusive scan of uint2 values ---------------------------
+// level 1: per block of 2048 values, the sum
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint2 *in, const uint32_t *n_ptr,
+                                                                   uint2 *bsum, const Status *st) {
+    if (st->code != 0u) return;
+    const uint32_t n = *n_ptr;
+    const uint32_t b0 = blockIdx.x * kScanBlock;
+    if (b0 >= n) return;
+    uint2 acc = make_uint2(0, 0);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+        if (i < n) acc = add2(acc, in[i]);
+    }
+    __shared__ uint32_t tmp[kScanThreads / 32];
+    uint2 tot;
+    block_scan2(acc, tmp, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// level 2: sums of chunks of 2048 block sums
+__global__ void __launch_bounds__(kScanThreads) scan_reduce2_kernel(const uint32_t *n_ptr, const uint2 *bsum,
+                                                                    uint2 *bsum2, const Status *st) {
+    if (st->code != 0u) return;
+    const uint32_t nb = (*n_ptr + kScanBlock - 1) / kScanBlock;
+    const uint32_t c0 = blockIdx.x * kScanBlock;
+    if (c0 >= nb) return;
+    uint2 acc = make_uint2(0, 0);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = c0 + threadIdx.x * kScanPer + k;
+        if (i < nb) acc = add2(acc, bsum[i]);
+    }
+    __shared__ uint32_t tmp[kScanThreads / 32];
+    uint2 tot;
+    block_scan2(acc, tmp, tot);
+    if (threadIdx.x == 0) bsum2[blockIdx.x] = tot;
+}
+
+// level 3: one block scans the chunk sums (at most 2048 of them) in place
+// and stores the grand total
+__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(const uint32_t *n_ptr, uint2 *bsum2,
+                                                                uint2 *total_out, const Status *st) {
+    if (st->code != 0u) return;
+    const uint32_t nb2 = ((*n_ptr + kScanBlock - 1) / kScanBlock + kScanBlock - 1) / kScanBlock;
+    uint2 v[kScanPer];
+    uint2 acc = make_uint2(0, 0);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = threadIdx.x * kScanPer + k;
+        v[k] = i < nb2 ? bsum2[i] : make_uint2(0, 0);
+        acc = add2(acc, v[k]);
+    }
+    __shared__ uint32_t tmp[kScanThreads / 32];
+    uint2 tot;
+    uint2 run = block_scan2(acc, tmp, tot);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = threadIdx.x * kScanPer + k;
+        if (i < nb2) bsum2[i] = run;
+        run = add2(run, v[k]);
+    }
+    if (threadIdx.x == 0) *total_out = tot;
+}
+
+// level 2 down: exclusive offsets of the block sums
+__global__ void __launch_bounds__(kScanThreads) scan_down2_kernel(const uint32_t *n_ptr, uint2 *bsum,
+                                                                  const uint2 *bsum2, const Status *st) {
+    if (st->code != 0u) return;
+    const uint32_t nb = (*n_ptr + kScanBlock - 1) / kScanBlock;
+    const uint32_t c0 = blockIdx.x * kScanBlock;
+    if (c0 >= nb) return;
+    uint2 v[kScanPer];
+    uint2 acc = make_uint2(0, 0);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = c0 + threadIdx.x * kScanPer + k;
+        v[k] = i < nb ? bsum[i] : make_uint2(0, 0);
+        acc = add2(acc, v[k]);
+    }
+    __shared__ uint32_t tmp[kScanThreads / 32];
+    uint2 tot;
+    uint2 run = add2(block_scan2(acc, tmp, tot), bsum2[blockIdx.x]);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = c0 + threadIdx.x * kScanPer + k;
+        if (i < nb) bsum[i] = run;
+        run = add2(run, v[k]);
+    }
+}
+
+// level 1 down: exclusive prefix of every value; out[n] = total
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in, const uint32_t *n_ptr,
+                                                                 const uint2 *bsum, const uint2 *total,
+                                                                 uint2 *out, const Status *st) {
+    if (st->code != 0u) return;
+    const uint32_t n = *n_ptr;
+    const uint32_t b0 = blockIdx.x * kScanBlock;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
+    if (b0 >= n) return;
+    uint2 v[kScanPer];
+    uint2 acc = make_uint2(0, 0);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+        v[k] = i < n ? in[i] : make_uint2(0, 0);
+        acc = add2(acc, v[k]);
+    }
+    __shared__ uint32_t tmp[kScanThreads / 32];
+    uint2 tot;
+    uint2 run = add2(block_scan2(acc, tmp, tot), bsum[blockIdx.x]);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+        if (i < n) out[i] = run;
+        run = add2(run, v[k]);
+    }
+}
+
+void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
+                 cudaStream_t s, uint32_t *launches) {
+    const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
+    const uint32_t g2 = (g1 + kScanBlock - 1) / kScanBlock;
+    const uint32_t grid1 = g1 ? g1 : 1u, grid2 = g2 ? g2 : 1u;
+    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.status);
+    scan_reduce2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
+    scan_top_kernel<<<1, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum2, B.scan_total, B.status);
+    scan_down2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
+    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.scan_total, out, B.status);
+    *launches += 5;
+}
+
+// ---- per-mechanism words ----------------------------------------------------
+// word counts as scan input
+__global__ void counts_kernel(Buffers B) {
+    if (B.status->code != 0u) return;
+    const uint32_t N = B.status->n_mech;
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x)
+        B.scan_val[m] = make_uint2(B.mech_cnt[m], 0u);
+}
+
+__global__ void scatter_kernel(Buffers B) {
+    if (B.status->code != 0u) return;
+    const Params &P = *B.params;
+    const uint32_t n = min(B.status->rec_count, P.rec_cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint4 r = B.records[i];
+        if (r.x == kNone) continue;
+        B.records[i].x = kNone;
+        const uint32_t pos = B.mech_off[r.x].x + atomicAdd(&B.mech_fill[r.x], 1u);
+        B.slot_col[pos] = r.y;
+        B.slot_word[pos] = ((unsigned long long)r.w << 32) | r.z;
+    }
+}
+
+// words of mechanism m sorted by column id (insertion sort: a handful)
+__device__ __forceinline__ uint32_t load_sorted(const Buffers &B, uint32_t m, uint32_t *col,
+                                                unsigned long long *w) {
+    const uint32_t o0 = B.mech_off[m].x, cnt = B.mech_off[m + 1].x - o0;
     for (uint32_t i = 0; i < cnt; i++) {
-        uint32_t c = B.slot_col[base + i];
-        unsigned long long x = B.slot_word[base + i];
+        const uint32_t c = B.slot_col[o0 + i];
+        const unsigned long long x = B.slot_word[o0 + i];
         uint32_t j = i;
         while (j > 0 && col[j - 1] > c) { col[j] = col[j - 1]; w[j] = w[j - 1]; j--; }
         col[j] = c;
@@ -39,44 +206,31 @@ __device__ __forceinline__ uint32_t load_sorted(const Buffers &B, uint32_t m, ui
     return cnt;
 }
 
-__device__ __forceinline__ bool same_mask(const Buffers &B, uint32_t rep, uint32_t S, uint32_t cnt,
-                                          const uint32_t *col, const unsigned long long *w) {
-    if (__ldcg(&B.mech_cnt[rep]) != cnt) return false;
+__device__ __forceinline__ bool same_mask(const Buffers &B, uint32_t rep, uint32_t cnt, const uint32_t *col,
+                                          const unsigned long long *w) {
+    if (B.mech_off[rep + 1].x - B.mech_off[rep].x != cnt) return false;
     uint32_t c2[kMaxMaskWords];
     unsigned long long w2[kMaxMaskWords];
-    load_sorted(B, rep, S, cnt, c2, w2);
+    load_sorted(B, rep, c2, w2);
     for (uint32_t i = 0; i < cnt; i++)
         if (c2[i] != col[i] || w2[i] != w[i]) return false;
     return true;
 }
 
-__global__ void scatter_kernel(Buffers B) {
-    if (*(volatile uint32_t *)&B.status->code != 0u) return;
-    const Params &P = *B.params;
-    const uint32_t n = min(B.status->rec_count, P.rec_cap), S = P.mask_words;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint4 r = B.records[i];
-        if (r.x == kNone) continue;
-        B.records[i].x = kNone;
-        const uint32_t pos = atomicAdd(&B.mech_cnt[r.x], 1u);
-        if (pos < S) {
-            B.slot_col[(size_t)r.x * S + pos] = r.y;
-            B.slot_word[(size_t)r.x * S + pos] = ((unsigned long long)r.w << 32) | r.z;
-        } else {
-            report(B.status, GP_ERR_CAPACITY, 4u, r.x, pos + 1);
-        }
-    }
-}
-
 __global__ void group_kernel(Buffers B) {
     const Params &P = *B.params;
-    if (*(volatile uint32_t *)&B.status->code != 0u) return;
+    if (B.status->code != 0u) return;
     const uint32_t N = B.status->n_mech, S = P.mask_words;
     const uint32_t cap_mask = (1u << P.table_log2) - 1u;
     const float *noise = P.noise;
     for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
-        const uint32_t cnt = B.mech_cnt[m];
-        if (cnt == 0u || cnt > S) { B.slot_of[m] = kNone; continue; }
+        const uint32_t cnt = B.mech_off[m + 1].x - B.mech_off[m].x;
+        if (cnt == 0u) { B.slot_of[m] = kNone; continue; }
+        if (cnt > S) {
+            report(B.status, GP_ERR_CAPACITY, 4u, m, cnt);
+            B.slot_of[m] = kNone;
+            continue;
+        }
         const unsigned long long info = B.mech_info[m];
         const uint32_t loc = (uint32_t)info;
         const uint32_t kind = (uint32_t)(info >> 32) & 0xFFu;
@@ -93,7 +247,7 @@ __global__ void group_kernel(Buffers B) {
         if (!(t < 1048576.0f)) t = 1048576.0f;     // q = 1/2 saturates P at 1/2
         uint32_t col[kMaxMaskWords];
         unsigned long long w[kMaxMaskWords];
-        load_sorted(B, m, S, cnt, col, w);
+        load_sorted(B, m, col, w);
         unsigned long long h = 0x243F6A8885A308D3ull;
         for (uint32_t i = 0; i < cnt; i++) {
             h = mix64(h ^ (0x9E3779B97F4A7C15ull * (col[i] + 1ull)));
@@ -103,13 +257,13 @@ __global__ void group_kernel(Buffers B) {
         const unsigned long long mine = ((unsigned long long)key_hi << 32) | m;
         uint32_t pos = (uint32_t)h & cap_mask, slot = kNone;
         for (uint32_t probe = 0; probe <= cap_mask; probe++) {
-            unsigned long long e = __ldcg(&B.table[pos]);
+            unsigned long long e = __ldcg(&B.table[pos].entry);
             if (e == kEmpty) {
-                const unsigned long long old = atomicCAS(&B.table[pos], kEmpty, mine);
+                const unsigned long long old = atomicCAS(&B.table[pos].entry, kEmpty, mine);
                 if (old == kEmpty) { slot = pos; break; }
                 e = old;
             }
-            if ((uint32_t)(e >> 32) == key_hi && same_mask(B, (uint32_t)e, S, cnt, col, w)) { slot = pos; break; }
+            if ((uint32_t)(e >> 32) == key_hi && same_mask(B, (uint32_t)e, cnt, col, w)) { slot = pos; break; }
             pos = (pos + 1u) & cap_mask;
         }
         if (slot == kNone) {
@@ -118,167 +272,110 @@ __global__ void group_kernel(Buffers B) {
             continue;
         }
         B.slot_of[m] = slot;
-        atomicMin(&B.tab_min[slot], m);
+        atomicMin(&B.table[slot].min, m);
         unsigned long long lo, hi;
         to_fixed(t, kProbShift, lo, hi);
-        acc128_add(&B.tab_acc[2 * (size_t)slot], lo, hi);
+        acc128_add(&B.table[slot].acc_lo, lo, hi);
     }
 }
 
 // leader flag and detector count of mechanism m
-__device__ __forceinline__ uint2 leader_info(const Buffers &B, uint32_t m, uint32_t S) {
+__device__ __forceinline__ uint2 leader_info(const Buffers &B, uint32_t m) {
     const uint32_t slot = B.slot_of[m];
-    if (slot == kNone || B.tab_min[slot] != m) return make_uint2(0, 0);
-    const uint32_t cnt = B.mech_cnt[m];
+    if (slot == kNone || B.table[slot].min != m) return make_uint2(0, 0);
+    const uint32_t o0 = B.mech_off[m].x, o1 = B.mech_off[m + 1].x;
     uint32_t dets = 0;
-    for (uint32_t i = 0; i < cnt; i++) {
-        const size_t sidx = (size_t)m * S + i;
-        if (!(B.slot_col[sidx] & kObsColFlag)) dets += __popcll(B.slot_word[sidx]);
-    }
+    for (uint32_t i = o0; i < o1; i++)
+        if (!(B.slot_col[i] & kObsColFlag)) dets += __popcll(B.slot_word[i]);
     return make_uint2(1, dets);
 }
 
-constexpr int kScanThreads = 256;
-constexpr int kPerThread = kMechPerBlockScan / kScanThreads;
-
-__global__ void __launch_bounds__(kScanThreads) compact_count_kernel(Buffers B) {
-    if (*(volatile uint32_t *)&B.status->code != 0u) return;
-    const uint32_t N = B.status->n_mech, S = B.params->mask_words;
-    const uint32_t m0 = blockIdx.x * kMechPerBlockScan;
-    if (m0 >= N) return;
-    uint2 acc = make_uint2(0, 0);
-    for (int i = 0; i < kPerThread; i++) {
-        const uint32_t m = m0 + threadIdx.x * kPerThread + i;
-        if (m < N) { const uint2 v = leader_info(B, m, S); acc.x += v.x; acc.y += v.y; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_down_sync(0xFFFFFFFFu, acc.x, o);
-        acc.y += __shfl_down_sync(0xFFFFFFFFu, acc.y, o);
-    }
-    __shared__ uint2 red[kScanThreads / 32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint2 s = make_uint2(0, 0);
-        for (int w = 0; w < kScanThreads / 32; w++) { s.x += red[w].x; s.y += red[w].y; }
-        B.blk_sums[blockIdx.x] = s;
-    }
-}
-
-// one block: exclusive scan of the per-block (edges, detector ids) counts
-__global__ void __launch_bounds__(kScanThreads) compact_scan_kernel(Buffers B) {
-    if (*(volatile uint32_t *)&B.status->code != 0u) return;
+__global__ void leaders_kernel(Buffers B) {
+    if (B.status->code != 0u) return;
     const uint32_t N = B.status->n_mech;
-    const uint32_t nb = (N + kMechPerBlockScan - 1) / kMechPerBlockScan;
-    __shared__ uint32_t warp_tmp[kScanThreads / 32];
-    __shared__ uint32_t carry_e, carry_d;
-    if (threadIdx.x == 0) { carry_e = 0; carry_d = 0; }
-    __syncthreads();
-    for (uint32_t base = 0; base < nb; base += kScanThreads) {
-        const uint32_t i = base + threadIdx.x;
-        const uint2 v = i < nb ? B.blk_sums[i] : make_uint2(0, 0);
-        uint32_t te, td;
-        const uint32_t oe = block_exclusive_scan<kScanThreads>(v.x, warp_tmp, te);
-        const uint32_t od = block_exclusive_scan<kScanThreads>(v.y, warp_tmp, td);
-        if (i < nb) B.blk_off[i] = make_uint2(carry_e + oe, carry_d + od);
-        __syncthreads();
-        if (threadIdx.x == 0) { carry_e += te; carry_d += td; }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        B.status->n_edges = carry_e;
-        B.status->n_det_entries = carry_d;
-        B.status->n_scan_blocks = nb;
-        if ((unsigned long long)carry_d > B.params->max_det_entries)
-            report(B.status, GP_ERR_CAPACITY, 7u, carry_d, (uint32_t)(B.params->max_det_entries > 0xFFFFFFFFull ? 0xFFFFFFFFull : B.params->max_det_entries));
-        else
-            B.det_off[carry_e] = carry_d;
-    }
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x)
+        B.scan_val[m] = leader_info(B, m);
 }
 
-__global__ void __launch_bounds__(kScanThreads) compact_write_kernel(Buffers B) {
-    if (*(volatile uint32_t *)&B.status->code != 0u) return;
-    const uint32_t N = B.status->n_mech, S = B.params->mask_words;
-    const uint32_t m0 = blockIdx.x * kMechPerBlockScan;
-    if (m0 >= N) return;
-    uint2 v[kPerThread];
-    uint32_t ne = 0, nd = 0;
-    for (int i = 0; i < kPerThread; i++) {
-        const uint32_t m = m0 + threadIdx.x * kPerThread + i;
-        v[i] = (m < N) ? leader_info(B, m, S) : make_uint2(0, 0);
-        ne += v[i].x;
-        nd += v[i].y;
+__global__ void compact_write_kernel(Buffers B) {
+    if (B.status->code != 0u) return;
+    const uint32_t N = B.status->n_mech;
+    const uint2 tot = B.comp_off[N];
+    if ((unsigned long long)tot.y > B.params->max_det_entries) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            report(B.status, GP_ERR_CAPACITY, 7u, tot.y,
+                   (uint32_t)(B.params->max_det_entries > 0xFFFFFFFFull ? 0xFFFFFFFFull : B.params->max_det_entries));
+        return;
     }
-    __shared__ uint32_t warp_tmp[kScanThreads / 32];
-    uint32_t te, td;
-    const uint2 boff = B.blk_off[blockIdx.x];
-    uint32_t e = block_exclusive_scan<kScanThreads>(ne, warp_tmp, te) + boff.x;
-    uint32_t d = block_exclusive_scan<kScanThreads>(nd, warp_tmp, td) + boff.y;
-    for (int i = 0; i < kPerThread; i++) {
-        if (!v[i].x) continue;
-        const uint32_t m = m0 + threadIdx.x * kPerThread + i;
-        const uint32_t slot = B.slot_of[m];
-        const unsigned long long info = B.mech_info[m];
-        const uint32_t b = (uint32_t)(info >> 48);
-        const uint32_t col_base = B.circ[b].col_base;
-        uint32_t col[kMaxMaskWords];
-        unsigned long long w[kMaxMaskWords];
-        const uint32_t cnt = load_sorted(B, m, S, B.mech_cnt[m], col, w);
-        unsigned long long obs = 0ull;
-        uint32_t dd = d;
-        for (uint32_t j = 0; j < cnt; j++) {
-            if (col[j] & kObsColFlag) { obs ^= w[j]; continue; }
-            unsigned long long x = w[j];
-            const uint32_t base_id = (col[j] - col_base) * 64u;
-            while (x) {
-                const int bit = __ffsll((long long)x) - 1;
-                B.det_idx[dd++] = base_id + (uint32_t)bit;
-                x &= x - 1ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        B.status->n_edges = tot.x;
+        B.status->n_det_entries = tot.y;
+        B.det_off[tot.x] = tot.y;
+    }
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < N; base += gridDim.x * blockDim.x) {
+        const uint32_t m = base + threadIdx.x;
+        const bool lead = m < N && B.scan_val[m].x != 0u;
+        uint32_t b = 0xFFFFFFFFu;
+        if (lead) {
+            const uint2 off = B.comp_off[m];
+            const uint32_t e = off.x;
+            uint32_t d = off.y;
+            const uint32_t slot = B.slot_of[m];
+            const unsigned long long info = B.mech_info[m];
+            b = (uint32_t)(info >> 48);
+            const uint32_t col_base = B.circ[b].col_base;
+            uint32_t col[kMaxMaskWords];
+            unsigned long long w[kMaxMaskWords];
+            const uint32_t cnt = load_sorted(B, m, col, w);
+            unsigned long long obs = 0ull;
+            for (uint32_t j = 0; j < cnt; j++) {
+                if (col[j] & kObsColFlag) { obs ^= w[j]; continue; }
+                unsigned long long x = w[j];
+                const uint32_t base_id = (col[j] - col_base) * 64u;
+                while (x) {
+                    const int bit = __ffsll((long long)x) - 1;
+                    B.det_idx[d++] = base_id + (uint32_t)bit;
+                    x &= x - 1ull;
+                }
             }
+            const TabSlot &ts = B.table[slot];
+            const float T = fixed_to_float(ts.acc_lo, ts.acc_hi, kProbShift);
+            const float Pc = -0.5f * expm1f(-T);
+            B.det_off[e] = off.y;
+            B.obs_mask[e] = obs;
+            B.prob[e] = Pc;
+            B.logodds[e] = log1pf(-Pc) - logf(Pc);
+            B.class_slot[e] = slot;
+            B.edge_circ[e] = b;
+            B.table[slot].cls = e;
         }
-        const float T = fixed_to_float(B.tab_acc[2 * (size_t)slot], B.tab_acc[2 * (size_t)slot + 1], kProbShift);
-        const float Pc = -0.5f * expm1f(-T);
-        B.det_off[e] = d;
-        B.obs_mask[e] = obs;
-        B.prob[e] = Pc;
-        B.logodds[e] = log1pf(-Pc) - logf(Pc);
-        B.class_slot[e] = slot;
-        B.edge_circ[e] = b;
-        B.tab_class[slot] = e;
-        d = dd;
-        e++;
-    }
-    // edges per circuit: one atomic per circuit present in the warp
-    for (int i = 0; i < kPerThread; i++) {
-        const uint32_t m = m0 + threadIdx.x * kPerThread + i;
-        const bool lead = v[i].x != 0u;
-        const uint32_t b = lead ? (uint32_t)(B.mech_info[m] >> 48) : 0xFFFFFFFFu;
+        // edges per circuit: one atomic per circuit present in the warp
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
-        if (lead && (__ffs(peers) - 1) == (int)(threadIdx.x & 31u))
-            atomicAdd(&B.circ_edges[b], (uint32_t)__popc(peers));
+        if (lead && (uint32_t)(__ffs(peers) - 1) == lane) atomicAdd(&B.circ_edges[b], (uint32_t)__popc(peers));
     }
 }
 
 __global__ void finalize_mech_kernel(Buffers B) {
-    if (*(volatile uint32_t *)&B.status->code != 0u) return;
+    if (B.status->code != 0u) return;
     const uint32_t N = B.status->n_mech;
     for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
         const uint32_t slot = B.slot_of[m];
-        B.mech_class[m] = (slot == kNone) ? -1 : (int32_t)B.tab_class[slot];
+        B.mech_class[m] = (slot == kNone) ? -1 : (int32_t)B.table[slot].cls;
         B.mech_cnt[m] = 0u;
+        B.mech_fill[m] = 0u;
     }
 }
 
 __global__ void finalize_table_kernel(Buffers B) {
-    if (*(volatile uint32_t *)&B.status->code != 0u) return;
+    if (B.status->code != 0u) return;
     const uint32_t E = B.status->n_edges;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        const uint32_t slot = B.class_slot[e];
-        B.table[slot] = kEmpty;
-        B.tab_min[slot] = kNone;
-        B.tab_acc[2 * (size_t)slot] = 0ull;
-        B.tab_acc[2 * (size_t)slot + 1] = 0ull;
+        TabSlot &ts = B.table[B.class_slot[e]];
+        ts.entry = kEmpty;
+        ts.min = kNone;
+        ts.acc_lo = 0ull;
+        ts.acc_hi = 0ull;
     }
 }
 
@@ -314,23 +411,35 @@ __global__ void backward_loc_kernel(Buffers B, float *g_noise, uint32_t n_loc) {
     }
 }
 
-}  // namespace
-
-void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches) {
-    scatter_kernel<<<grid, threads, 0, s>>>(b);
-    group_kernel<<<grid, threads, 0, s>>>(b);
-    *launches += 2;
+__global__ void init_table_kernel(TabSlot *t, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        t[i].entry = kEmpty;
+        t[i].min = kNone;
+        t[i].cls = 0;
+        t[i].acc_lo = 0ull;
+        t[i].acc_hi = 0ull;
+    }
 }
 
-void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_scan_blocks,
-                    uint32_t max_mech, cudaStream_t s, uint32_t *launches) {
-    (void)max_mech;
-    compact_count_kernel<<<max_scan_blocks, kScanThreads, 0, s>>>(b);
-    compact_scan_kernel<<<1, kScanThreads, 0, s>>>(b);
-    compact_write_kernel<<<max_scan_blocks, kScanThreads, 0, s>>>(b);
+}  // namespace
+
+void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
+                  uint32_t *launches) {
+    counts_kernel<<<grid, threads, 0, s>>>(b);
+    launch_scan(b, b.scan_val, &b.status->n_mech, b.mech_off, max_mech, s, launches);
+    scatter_kernel<<<grid, threads, 0, s>>>(b);
+    group_kernel<<<grid, threads, 0, s>>>(b);
+    *launches += 3;
+}
+
+void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
+                    uint32_t *launches) {
+    leaders_kernel<<<grid, threads, 0, s>>>(b);
+    launch_scan(b, b.scan_val, &b.status->n_mech, b.comp_off, max_mech, s, launches);
+    compact_write_kernel<<<grid, threads, 0, s>>>(b);
     finalize_mech_kernel<<<grid, threads, 0, s>>>(b);
     finalize_table_kernel<<<grid, threads, 0, s>>>(b);
-    *launches += 5;
+    *launches += 4;
 }
 
 void launch_backward(const Buffers &b, const float *g_prob, const float *g_logodds, float *g_noise,
@@ -339,6 +448,10 @@ void launch_backward(const Buffers &b, const float *g_prob, const float *g_logod
     backward_mech_kernel<<<grid, threads, 0, s>>>(b, g_prob, g_logodds, n_mech);
     backward_loc_kernel<<<grid, threads, 0, s>>>(b, g_noise, n_loc);
     *launches += 2;
+}
+
+void launch_init_table(TabSlot *t, size_t n, cudaStream_t s) {
+    init_table_kernel<<<1024, 256, 0, s>>>(t, n);
 }
 
 }  // namespace gpdem

@@ -46,7 +46,7 @@ class Bounds:
     max_detectors: int = 1 << 14
     max_locations: int = 1 << 16
     max_mechanisms: int = 1 << 18
-    max_mask_words: int = 8
+    max_mask_words: int = 16
     max_det_entries: int = 0
 
     def to_c(self) -> native.GpBounds:

@@ -1,0 +1,122 @@
+"""GPU parity on the other workloads of the paper: bivariate bicycle memory
+(forward and adjoint), adaptive [[4,2,2]]-concatenated branches compiled as
+one batch, the autotuner and the autograd function."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle
+from paper_2604_16613_gb300 import circuits as C
+from paper_2604_16613_gb300.autotune import autotune
+from paper_2604_16613_gb300.dem import DemFunction, DeviceCircuit, Driver
+
+from parity import compare_edges, oracle_edges
+
+pytestmark = pytest.mark.gpu
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32)
+
+
+@pytest.fixture(scope="module")
+def bb():
+    circ = C.bb_memory(12, C.NoiseModel.uniform(1e-3), seed=3)
+    noise = f32(circ.default_noise)
+    return circ, noise
+
+
+def test_bb_forward_parity(bb):
+    circ, noise = bb
+    drv = Driver.for_circuits([circ])
+    for level in ("L0", "L2"):
+        dem = drv.compile(DeviceCircuit(circ), torch.tensor(noise, device="cuda"), level)
+        compare_edges(dem.edges(), oracle_edges(circ, noise, level).edges(), f"bb/{level}")
+
+
+def _grad_setup(circ, noise, seed):
+    drv = Driver.for_circuits([circ])
+    dem = drv.compile(DeviceCircuit(circ), torch.tensor(noise, device="cuda"))
+    keys = list(dem.edges().keys())
+    ref = oracle_edges(circ, noise)
+    order = [ref.split_ids(ref.class_ids(c)) for c in range(ref.n_classes)]
+    rng = np.random.default_rng(seed)
+    gw = {k: float(v) for k, v in zip(order, rng.normal(size=len(order)).astype(np.float32))}
+    return drv, dem, keys, ref, order, gw
+
+
+def test_bb_adjoint_log_odds(bb):
+    """Config 3: gradient of sum_e gW_e w_e with respect to every location,
+    FP32 on the GPU against the FP64 oracle's analytic gradient (all
+    locations) and against FP64 central differences (h = 1e-7) of the oracle
+    on 64 seeded locations."""
+    circ, noise = bb
+    drv, dem, keys, ref, order, gw = _grad_setup(circ, noise, 13)
+    g_gpu = drv.backward(None, torch.tensor([gw[k] for k in keys], dtype=torch.float32,
+                                            device="cuda")).cpu().numpy().astype(np.float64)
+    g_ref = ref.gradient(np.zeros(ref.n_classes), np.array([gw[k] for k in order]), circ.n_locations)
+    floor = 1e-6 * np.abs(g_ref).max()
+    err = np.abs(g_gpu - g_ref)
+    assert np.all(err <= 1e-4 * np.abs(g_ref) + floor), f"worst {err.max():.3g}"
+    n64 = noise.astype(np.float64)
+    h = 1e-7
+    rng = np.random.default_rng(21)
+    for loc in rng.choice(circ.n_locations, size=64, replace=False):
+        up, dn = n64.copy(), n64.copy()
+        up[loc] += h
+        dn[loc] -= h
+        lu = sum(gw[k] * w for k, (P, w) in oracle.analyze_circuit(circ, up).edges().items())
+        ld = sum(gw[k] * w for k, (P, w) in oracle.analyze_circuit(circ, dn).edges().items())
+        fd = (lu - ld) / (2 * h)
+        assert g_gpu[loc] == pytest.approx(fd, rel=1e-3, abs=1e-5 * np.abs(g_ref).max())
+
+
+def test_dem_function_autograd():
+    circ = C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))
+    noise = torch.tensor(f32(C.log_uniform_noise(circ.n_locations, seed=7)), device="cuda", requires_grad=True)
+    drv = Driver.for_circuits([circ])
+    dc = DeviceCircuit(circ)
+    prob, logodds = DemFunction.apply(noise, drv, dc, "L2")
+    rng = np.random.default_rng(1)
+    a = torch.tensor(rng.normal(size=prob.numel()), dtype=torch.float32, device="cuda")
+    b = torch.tensor(rng.normal(size=prob.numel()) * 1e-3, dtype=torch.float32, device="cuda")
+    loss = (a * prob).sum() + (b * logodds).sum()
+    loss.backward()
+    drv.compile(dc, noise.detach())
+    g = drv.backward(a, b)
+    assert torch.equal(noise.grad, g)
+
+
+def test_concatenated_branches_one_batch():
+    lay4 = C.ConcatenatedLayout(4)
+    branches = [C.concatenated_adaptive_branch(4, n, seed=s, noise=C.NoiseModel.uniform(1e-3), layout=lay4)
+                for s, n in enumerate([3, 5, 4, 6, 2, 7])]
+    branches += [C.concatenated_adaptive_branch(10, 3, seed=99, noise=C.NoiseModel.uniform(1e-3))]
+    noises = [f32(b.default_noise) for b in branches]
+    drv = Driver.for_circuits(branches)
+    dem = drv.compile([DeviceCircuit(b) for b in branches], torch.tensor(np.concatenate(noises), device="cuda"))
+    host = dem.to_host()
+    for i, (b, nz) in enumerate(zip(branches, noises)):
+        compare_edges(dem.edges(i, host), oracle_edges(b, nz).edges(), f"branch {i}")
+
+
+def test_autotune_does_not_change_results():
+    circs = [C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3)),
+             C.concatenated_adaptive_branch(4, 4, seed=3, noise=C.NoiseModel.uniform(1e-3))]
+    noise = torch.tensor(f32(np.concatenate([c.default_noise for c in circs])), device="cuda")
+    dcs = [DeviceCircuit(c) for c in circs]
+    drv = Driver.for_circuits(circs)
+    base = drv.compile(dcs, noise).to_host()
+    best = autotune(drv, dcs, noise, repeats=2)
+    assert best["ms"] > 0
+    tuned = drv.compile(dcs, noise).to_host()
+    for k in base:
+        assert np.array_equal(base[k], tuned[k]), k
+    for shape in [(256, 1, 128, 16), (1024, 0, 512, 4)]:
+        drv.set_tuning(*shape)
+        other = drv.compile(dcs, noise).to_host()
+        for k in base:
+            assert np.array_equal(base[k], other[k]), (shape, k)
