@@ -120,17 +120,19 @@ def kernel_source_hash() -> str:
 
 
 def measured_traffic(kernel: str) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        rec = json.load(open(path))
-    except (OSError, ValueError):
-        return None
-    ent = rec.get(kernel)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
-        return None
-    return float(ent["dram_bytes_per_launch"])
+    """DRAM bytes per launch from the committed ncu summary of `kernel`
+    (profiles/<kernel>_*.md, lines `dram_bytes_per_launch:` and
+    `source_hash:`), if it was taken on the current kernel sources."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.strip().startswith(("dram_bytes_per_launch", "source_hash")):
+                k, v = line.strip().strip("`- ").split(":", 1)
+                fields[k.strip().strip("`")] = v.strip().strip("`")
+        if fields.get("source_hash") == kernel_source_hash() and "dram_bytes_per_launch" in fields:
+            return float(fields["dram_bytes_per_launch"])
+    return None
 
 
 def peaks() -> tuple[float, str]:
@@ -157,6 +159,74 @@ def cpu_baseline(circ, noise, budget_s: float = 12.0, max_runs: int = 40) -> dic
     return {"value": nm / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{runs} full oracle compiles of the d=25 workload ({el:.1f} s, 1 thread, "
                       f"{platform.machine()} host)"}
+
+
+def batch_section(args, world: int) -> dict:
+    """Adaptive [[4,2,2]]-concatenated surface code, outer distance 10: 256
+    realised branches of 10-30 cycles (block firing 5 % per cycle, refresh
+    every 5 cycles, p = 1e-3, level L2), compiled (a) as one batch through the
+    graph-captured pipeline with the autotuned launch shape and (b) one
+    branch at a time on a driver sized for one branch.  Per-cycle times:
+    batched = batch time / total cycles (per repetition); plain = branch
+    time / branch cycles (per branch)."""
+    import torch
+    from paper_2604_16613_gb300 import circuits as C
+    from paper_2604_16613_gb300.autotune import autotune
+    from paper_2604_16613_gb300.dem import Bounds, DeviceCircuit, Driver
+    n = args.batch_branches
+    branches = C.adaptive_branches(n=n, d=10, lo=10, hi=30, seed=4)
+    lay = C.ConcatenatedLayout(10)
+    cyc = np.array([b.n_cycles for b in branches])
+    noise = np.concatenate([b.default_noise for b in branches]).astype(np.float32)
+    nz = torch.tensor(noise, device="cuda")
+    dcs = [DeviceCircuit(b) for b in branches]
+    bd = Bounds.for_circuits(branches)
+    bd.max_det_entries = 8 * bd.max_mechanisms
+    drv = Driver(bd)
+    tune = autotune(drv, dcs, nz, repeats=2)
+    dem = drv.compile(dcs, nz)
+    n_mech = int((dem.mech_class >= 0).sum().item())
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = []
+    for _ in range(args.batch_reps):
+        e0.record(stream)
+        drv.compile(dcs, nz)
+        e1.record(stream)
+        e1.synchronize()
+        reps.append(e0.elapsed_time(e1))
+    total_cycles = int(cyc.sum())
+    batched_pc = np.array(reps) * 1e3 / total_cycles
+    del drv, dem
+    torch.cuda.empty_cache()
+    # plain: one branch at a time
+    one = Driver(Bounds.for_circuits(branches, batch=1))
+    loc0 = np.cumsum([0] + [b.n_locations for b in branches])
+    plain_pc, plain_ms = [], []
+    for i, dc in enumerate(dcs):
+        nzi = nz[loc0[i]:loc0[i + 1]]
+        one.compile(dc, nzi)
+        e0.record(stream)
+        one.compile(dc, nzi)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        plain_ms.append(ms)
+        plain_pc.append(ms * 1e3 / cyc[i])
+    plain_pc = np.array(plain_pc)
+    return {
+        "workload": "adaptive [[4,2,2]]-concatenated surface code d=10, %d branches of 10-30 cycles, p=1e-3, L2" % n,
+        "mechanisms": n_mech, "cycles": total_cycles, "qubits_per_branch": lay.n_qubits,
+        "batched": {"ms_per_batch_p50": float(np.median(reps)),
+                    "per_cycle_us_p50": float(np.percentile(batched_pc, 50)),
+                    "per_cycle_us_p99": float(np.percentile(batched_pc, 99)),
+                    "mechanisms_per_s": n_mech / (np.median(reps) / 1e3),
+                    "tuning": {k: v for k, v in tune.items() if k != "ms"}},
+        "plain": {"ms_per_branch_p50": float(np.median(plain_ms)),
+                  "per_cycle_us_p50": float(np.percentile(plain_pc, 50)),
+                  "per_cycle_us_p99": float(np.percentile(plain_pc, 99)),
+                  "mechanisms_per_s": n_mech / (sum(plain_ms) / 1e3)},
+    }
 
 
 def run_reference(args):
@@ -333,6 +403,10 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(circ, noise)
+        if args.batch_branches > 0:
+            del drv
+            torch.cuda.empty_cache()
+            result["batch"] = batch_section(args, world)
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -346,6 +420,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-branches", type=int, default=256,
+                    help="adaptive branches for the batched-vs-plain section (0 skips it)")
+    ap.add_argument("--batch-reps", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -1069,6 +1069,7 @@ def concatenated_adaptive_branch(d: int = 10, cycles: int = 20, seed: int = 0, f
             groups.append([drec[pos[q]] for q in sup] + [last[("o", i)]])
     c.detectors(groups)
     c.observable(0, [drec[pos[q]] for q in lay.z_logical])
+    c.n_cycles = cycles
     return c
 
 
