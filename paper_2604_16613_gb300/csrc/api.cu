@@ -38,6 +38,7 @@ struct Layout {
     // sizes derived from the bounds
     uint32_t max_tiles, max_cols, max_layer_slots, S, table_log2, max_scan_blocks;
     uint64_t max_det_entries;
+    uint64_t qidx_cap16;         // layer index arena, 16-byte units
     uint64_t rec_cap;
     // byte offsets in the workspace
     uint64_t total = 0;
@@ -64,6 +65,7 @@ bool bounds_ok(const gp_bounds &b, std::string &why) {
     if (b.max_mask_words > (uint32_t)kMaxMaskWords) { why = "bounds: max_mask_words above 16"; return false; }
     if (b.max_ops > 0xFFFFFFFFull || b.max_recs > 0xFFFFFFFFull) { why = "bounds: max_ops and max_recs must fit 32 bits"; return false; }
     if (b.max_mechanisms > 0x7FFFFFFFu) { why = "bounds: max_mechanisms too large"; return false; }
+    if (b.max_measurements > kMaxMeasurements) { why = "bounds: max_measurements above 2^28"; return false; }
     return true;
 }
 
@@ -82,8 +84,10 @@ Layout make_layout(const gp_bounds &b) {
     L.max_det_entries = b.max_det_entries ? b.max_det_entries : 16ull * b.max_mechanisms;
     // mask words over all mechanisms: four per mechanism on average (the
     // workloads here average 2 to 2.5), plus the unused chunk tails that
-    // stage-1 blocks may leave (at most 1024 blocks counted)
-    L.rec_cap = std::min<uint64_t>(4ull * b.max_mechanisms + 1024ull * kChunkRecs, 0xFFFFFFF0ull);
+    // stage-1 warps may leave
+    L.rec_cap = std::min<uint64_t>(4ull * b.max_mechanisms + kPoolSlack, 0xFFFFFFF0ull);
+    // one qubit index block per layer slot at the widest circuit
+    L.qidx_cap16 = (uint64_t)L.max_layer_slots * (layer_geo(b.max_qubits).bytes / 16u);
     return L;
 }
 
@@ -104,13 +108,14 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     B.recs_arena = c.take<uint32_t>(std::max<uint64_t>(bd.max_recs, 1));
     B.noise_arena = c.take<float>(std::max<uint32_t>(bd.max_locations, 1));
     B.aux = c.take<uint32_t>(bd.max_ops);
-    B.packed = c.take<uint2>(bd.max_ops + 4);
+    B.lists = c.take<uint2>(2ull * bd.max_ops + 4);
+    B.qidx = c.take<unsigned char>(16ull * L.qidx_cap16);
     B.layer_seg = c.take<uint4>(L.max_layer_slots + 1);
     B.records = c.take<uint4>(L.rec_cap);
     B.tile_sums = c.take<uint4>(L.max_tiles);
     B.tile_off = c.take<uint4>(L.max_tiles);
     B.layer_start = c.take<uint32_t>(L.max_layer_slots + 1);
-    B.meas_layer = c.take<uint32_t>(std::max<uint32_t>(bd.max_measurements, 1));
+    B.meas_lq = c.take<uint2>(std::max<uint32_t>(bd.max_measurements, 1));
     B.det_row = c.take<uint32_t>(std::max<uint32_t>(bd.max_detectors, 1));
     B.obs_rows = c.take<uint32_t>(bd.max_ops);
     B.obs_count = c.take<uint32_t>(bd.max_circuits);
@@ -155,6 +160,7 @@ struct gp_driver {
     gp_bounds bounds{};
     Layout L{};
     int device = 0, n_sms = 0;
+    size_t smem_limit = 0;          // dynamic shared memory a stage-1 block may take
     unsigned char *ws = nullptr;
     bool own_ws = false;
     uint64_t ws_bytes = 0, params_bytes = 0;
@@ -196,7 +202,8 @@ gp_status full_reset(gp_driver *d, cudaStream_t s) {
     GP_CUDA(cudaMemsetAsync(d->B.mech_fill, 0, sizeof(uint32_t) * (size_t)d->bounds.max_mechanisms, s));
     GP_CUDA(cudaMemsetAsync(d->B.gacc, 0, 2 * sizeof(unsigned long long) * std::max<uint32_t>(d->bounds.max_locations, 1), s));
     GP_CUDA(cudaMemsetAsync(d->B.records, 0xFF, sizeof(uint4) * L.rec_cap, s));
-    GP_CUDA(cudaMemsetAsync(d->B.packed, 0, sizeof(uint2) * (d->bounds.max_ops + 4), s));
+    GP_CUDA(cudaMemsetAsync(d->B.lists, 0, sizeof(uint2) * (2ull * d->bounds.max_ops + 4), s));
+    GP_CUDA(cudaMemsetAsync(d->B.qidx, 0, 16ull * L.qidx_cap16, s));
     GP_CUDA(cudaStreamSynchronize(s));
     return GP_OK;
 }
@@ -235,7 +242,9 @@ std::string describe(const Status &st) {
         else if (a == 5) snprintf(buf, sizeof buf, "word column %u references %u (measurement, detector) pairs; at most %d", b, c, kMaxEntries);
         else if (a == 6) snprintf(buf, sizeof buf, "hash table of %u slots is full", c);
         else if (a == 7) snprintf(buf, sizeof buf, "%u detector ids in the hyperedges, bound allows %u", b, c);
-        else if (a == 8) snprintf(buf, sizeof buf, "mask-word pool of %u entries is full (it holds 4 words per mechanism of max_mechanisms on average)", c);
+        else if (a == 8) snprintf(buf, sizeof buf, "mask-word pool of %u entries is full (it holds 4 words per mechanism of max_mechanisms on average plus 2^22 spare)", c);
+        else if (a == 9) snprintf(buf, sizeof buf, "circuit %u: the per-layer qubit index needs %u x 16 bytes, more than max_layers x max_qubits allow", b, c);
+        else if (a == 10) snprintf(buf, sizeof buf, "circuit %u layer %u: more than %u rows in one TICK layer", b, c, kMaxLayerRows);
         else snprintf(buf, sizeof buf, "capacity exceeded (%u, %u, %u)", a, b, c);
         break;
     default:
@@ -252,19 +261,21 @@ gp_status enqueue_pipeline(gp_driver *d, cudaStream_t s, uint32_t *kernels) {
     const gp_bounds &bd = d->bounds;
     const Layout &L = d->L;
     const uint32_t grid2 = (uint32_t)d->n_sms * d->tuning.stage2_blocks_per_sm;
-    const size_t smem1 = stage1_smem_bytes(bd.max_qubits);
+    // stage-1 blocks per SM: 0 = one block with the deepest window ring
+    const uint32_t want = d->tuning.stage1_blocks_per_sm ? d->tuning.stage1_blocks_per_sm : 1u;
+    const Stage1Shape shape1 = stage1_shape(bd.max_qubits, want, d->smem_limit);
+    if (shape1.smem > d->smem_limit) return fail(GP_ERR_CAPACITY, "stage 1 does not fit in shared memory with these bounds");
     int occ = 1;
     GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage1_kernel_ptr(d->tuning.stage1_threads),
-                                                          (int)d->tuning.stage1_threads, smem1));
+                                                          (int)d->tuning.stage1_threads, shape1.smem));
     if (occ < 1) return fail(GP_ERR_CAPACITY, "stage 1 does not fit on an SM with these bounds");
-    const uint32_t bps = d->tuning.stage1_blocks_per_sm ? std::min<uint32_t>(d->tuning.stage1_blocks_per_sm, occ)
-                                                        : (uint32_t)occ;
+    const uint32_t bps = std::min<uint32_t>(want, (uint32_t)occ);
     const uint32_t grid1 = std::min<uint32_t>((uint32_t)d->n_sms * bps, std::max<uint32_t>(L.max_cols, 1u));
     GP_CUDA(cudaMemcpyAsync(d->B.params, d->h_params, d->params_bytes, cudaMemcpyHostToDevice, s));
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[0], s, cudaEventRecordExternal));
     launch_lowering(d->B, L.max_tiles, L.max_layer_slots, bd.max_qubits, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[1], s, cudaEventRecordExternal));
-    launch_stage1(d->B, grid1, d->tuning.stage1_threads, bd.max_qubits, s, kernels);
+    launch_stage1(d->B, grid1, d->tuning.stage1_threads, bd.max_qubits, shape1, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[2], s, cudaEventRecordExternal));
     launch_group(d->B, grid2, d->tuning.stage2_threads, bd.max_mechanisms, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[3], s, cudaEventRecordExternal));
@@ -370,12 +381,17 @@ gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace, uint64_t 
     cudaStream_t s = 0;
     gp_status st = full_reset(d, s);
     if (st != GP_OK) return cleanup(st);
-    // stage-1 shared memory above the default 48 KB
-    const size_t smem = stage1_smem_bytes(bounds->max_qubits);
+    // shared memory above the default 48 KB: the stage-1 walk and the
+    // per-layer index kernel
+    d->smem_limit = stage1_dynamic_smem_limit(d->device);
+    if (d->smem_limit == 0) return cleanup(fail(GP_ERR_CUDA, "querying the shared-memory limit failed"));
     for (uint32_t t : {128u, 256u, 512u, 1024u}) {
-        if (cudaFuncSetAttribute(stage1_kernel_ptr(t), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(stage1_kernel_ptr(t), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)d->smem_limit) != cudaSuccess)
             return cleanup(fail(GP_ERR_CUDA, "cudaFuncSetAttribute(stage1 shared memory) failed"));
     }
+    if (lowering_setup(bounds->max_qubits) != cudaSuccess)
+        return cleanup(fail(GP_ERR_CUDA, "cudaFuncSetAttribute(layer index shared memory) failed"));
     *out = d;
     return GP_OK;
 }
@@ -558,6 +574,7 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     P->max_ops = (uint32_t)bd.max_ops;
     P->rec_cap = (uint32_t)L.rec_cap;
     P->max_qubits = bd.max_qubits;
+    P->qidx_cap16 = L.qidx_cap16;
     // ---- pipeline: one graph launch ----------------------------------------------
     {
         const gp_status gs = ensure_graph(d);

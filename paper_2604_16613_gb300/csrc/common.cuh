@@ -17,9 +17,7 @@ constexpr int kLowerThreads = 256;      // 16 rows per thread
 constexpr int kMaxEntries = 1024;       // (measurement, word) pairs per column
 constexpr int kMaxMaskWords = 16;       // hard cap of mask words per mechanism
 constexpr int kMechPerBlockScan = 1024; // mechanisms per compaction block
-constexpr int kRowBuf = 1920;           // packed rows per staged layer buffer
-constexpr int kStageRecs = 2048;        // staged mask records per block
-constexpr uint32_t kChunkRecs = 4096;   // records per global chunk of a block
+constexpr uint64_t kPoolSlack = 1ull << 22;  // record-pool slack for unused chunk tails
 constexpr int kPackThreads = 256;       // layer packing block size
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
@@ -42,7 +40,8 @@ struct CircuitDev {
     uint32_t n_layers, layer_base;
     uint32_t n_meas, meas_base;
     uint32_t n_mech, mech_base;
-    uint32_t pad[1];
+    uint32_t qidx_off;         // start of the circuit's layer index blocks
+                               // (16-byte units)
 };
 static_assert(sizeof(CircuitDev) % 16 == 0, "CircuitDev alignment");
 
@@ -64,6 +63,7 @@ struct Params {
     const float *noise;         // concatenated noise vectors
     uint32_t rec_cap;           // capacity of the record pool
     uint32_t max_qubits;
+    uint64_t qidx_cap16;        // capacity of the layer index arena (16-byte units)
 };
 
 // device status block (read back by the host after every compile)
@@ -100,14 +100,17 @@ struct Buffers {
     uint32_t *recs_arena;
     float *noise_arena;
     uint32_t *aux;              // per row (indexed by op_base + row)
-    uint2 *packed;              // per row: packed gate / noise rows, per layer
-                                // ordered gates | after-noise | before-noise
-    uint4 *layer_seg;           // per layer slot: {start, end of gates,
-                                // end of after-noise, end of before-noise}
+    uint2 *lists;               // two slots per row: the per-qubit lists of
+                                // packed noise rows of each layer (before-gate
+                                // lists at the layer's start, after-gate
+                                // lists ending at the layer's end)
+    unsigned char *qidx;        // per layer: qubit index block (layer_block)
+    uint4 *layer_seg;           // per layer slot: {first row, after-gate list
+                                // entries, before-gate list entries, 0}
     uint4 *records;             // mask-word records {mech, column, word lo, hi}
     uint4 *tile_sums, *tile_off;
     uint32_t *layer_start;      // per circuit: n_layers + 1 row offsets
-    uint32_t *meas_layer;       // per measurement: its layer
+    uint2 *meas_lq;             // per measurement: {layer, qubit | x-basis << 31}
     uint32_t *det_row;          // per detector: its row
     uint32_t *obs_rows;         // per circuit (at op_base): OBSERVABLE rows
     uint32_t *obs_count;        // per circuit
@@ -201,6 +204,38 @@ __host__ __device__ inline uint32_t row_a(uint2 r) { return (r.x >> 13) & 0x1FFF
 __host__ __device__ inline uint32_t row_b(uint2 r) { return r.x & 0x1FFFu; }
 
 // ---------------------------------------------------------------------------
+// per-layer qubit index (written by the lowering, read by the stage-1 walk)
+// ---------------------------------------------------------------------------
+// Block of layer L of a circuit with nq qubits, blocks of one circuit
+// consecutive (L = 0 .. n_layers, the last one for the end sentinel):
+//   boff[qb]   u16  before-gate list offsets of L: q's rows are entries
+//                   [boff[q], boff[q+1]) of the before-gate lists of L
+//   gate[nq4]  u32  q's gate in L as seen from q (gate_view), 0 for none
+//   aoff[qb]   u16  after-gate list offsets of L
+// with nq4 = nq rounded up to 4 and qb = nq + 1 rounded up to 8, so every
+// part is 16-byte aligned.  One walk step at L reads gate(L), aoff(L) and
+// boff(L + 1): a single contiguous range.
+struct LayerGeo {
+    uint32_t nq4, qb, bytes;    // bytes of one block (multiple of 16)
+};
+__host__ __device__ inline LayerGeo layer_geo(uint32_t nq) {
+    LayerGeo g;
+    g.nq4 = (nq + 3u) & ~3u;
+    g.qb = (nq + 1u + 7u) & ~7u;
+    g.bytes = 4u * g.nq4 + 4u * g.qb;
+    return g;
+}
+constexpr uint32_t kMaxLayerRows = 32767;   // rows of one TICK layer (u16 list offsets)
+
+// A gate seen from one of its qubits: kind (4 bits) << 28 | payload, payload
+// the measurement index for R/M/MR/RX/MX/MRX and the other qubit for the
+// two-qubit gates.  One-qubit kinds keep their row kind.
+enum GateView : uint32_t {
+    GV_NONE = 0, GV_CX_C = 10, GV_CZ_A = 11, GV_CX_T = 12, GV_CZ_B = 13
+};
+constexpr uint32_t kMaxMeasurements = 1u << 28;
+
+// ---------------------------------------------------------------------------
 // shared-memory barriers and 1-D bulk (TMA) copies
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -253,6 +288,17 @@ __device__ __forceinline__ void report(Status *st, uint32_t code, uint32_t a, ui
         st->info[1] = b;
         st->info[2] = c;
     }
+}
+
+// block-uniform test of the status code (every thread of the block gets
+// thread 0's reading, so an early return never splits a block that later
+// meets a barrier); call it where all threads of the block are present
+__device__ __forceinline__ bool status_set(Status *st) {
+    __shared__ uint32_t code;
+    __syncthreads();
+    if (threadIdx.x == 0) code = *(volatile uint32_t *)&st->code;
+    __syncthreads();
+    return code != 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -361,8 +407,19 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 namespace gpdem {
 void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, cudaStream_t s,
                      uint32_t *launches);
-void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_qubits, cudaStream_t s, uint32_t *launches);
-size_t stage1_smem_bytes(uint32_t max_qubits);
+cudaError_t lowering_setup(uint32_t max_qubits);
+// shared-memory shape of the stage-1 walk: window buffers, list entries a
+// buffer holds, bytes of a buffer and of the whole block
+struct Stage1Shape {
+    uint32_t nbuf, list_cap, wbytes;
+    size_t smem;
+};
+// limit: dynamic shared memory one block may take (opt-in maximum less the
+// kernel's static shared memory)
+Stage1Shape stage1_shape(uint32_t max_qubits, uint32_t blocks_per_sm, size_t limit);
+size_t stage1_dynamic_smem_limit(int device);
+void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_qubits, const Stage1Shape &shape,
+                   cudaStream_t s, uint32_t *launches);
 const void *stage1_kernel_ptr(uint32_t threads);
 void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);

@@ -11,11 +11,13 @@
 //                the scatters stage 1 reads (layer starts, record layers,
 //                detector rows, observable rows, per-row auxiliary index,
 //                per-mechanism location/kind/component)
-//   layer_pack   one block per TICK layer: checks that no qubit takes part
+//   layer_index  one block per TICK layer: checks that no qubit takes part
 //                in two gates, decides for every noise row whether it acts
 //                before or after the layer's gate on its qubit(s), and writes
-//                the layer as packed 8-byte rows ordered gates | noise after
-//                the gates | noise before the gates
+//                the layer's qubit index: each qubit's gate as seen from the
+//                qubit, and per qubit the lists of packed noise rows that
+//                touch it after and before the gates (CSR, a two-qubit row
+//                listed under both of its qubits)
 #include "common.cuh"
 
 namespace gpdem {
@@ -72,11 +74,12 @@ __global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
     const Params &P = *B.params;
     __shared__ uint32_t warp_tmp[kLowerThreads / 32];
     __shared__ uint32_t carry_layer, carry_meas, carry_mech;
-    if (threadIdx.x == 0) { carry_layer = 0; carry_meas = 0; carry_mech = 0; }
+    __shared__ unsigned long long carry_qidx;
+    if (threadIdx.x == 0) { carry_layer = 0; carry_meas = 0; carry_mech = 0; carry_qidx = 0; }
     __syncthreads();
     for (uint32_t base = 0; base < P.n_circuits; base += kLowerThreads) {
         const uint32_t b = base + threadIdx.x;
-        uint32_t layers = 0, meas = 0, mech = 0;
+        uint32_t layers = 0, meas = 0, mech = 0, qblocks = 0;
         if (b < P.n_circuits) {
             CircuitDev &C = B.circ[b];
             uint4 run = make_uint4(0, 0, 0, 0);
@@ -91,6 +94,9 @@ __global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
             layers = C.n_layers + 1;       // row offsets incl. the end sentinel
             meas = run.y;
             mech = run.w;
+            // index blocks for layers 0 .. n_layers, in 16-byte units
+            const unsigned long long qb = (unsigned long long)layers * (layer_geo(C.n_qubits).bytes / 16u);
+            qblocks = (uint32_t)min(qb, 0xFFFFFFFFull);
             B.obs_count[b] = 0;
             B.circ_edges[b] = 0;
         }
@@ -98,11 +104,24 @@ __global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
         const uint32_t off_l = block_exclusive_scan<kLowerThreads>(layers, warp_tmp, tot_l);
         const uint32_t off_m = block_exclusive_scan<kLowerThreads>(meas, warp_tmp, tot_m);
         const uint32_t off_x = block_exclusive_scan<kLowerThreads>(mech, warp_tmp, tot_x);
+        // 64-bit scan of the index blocks: a circuit's own count fits 32 bits
+        __shared__ unsigned long long qscan[kLowerThreads], qtot;
+        qscan[threadIdx.x] = qblocks;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long r = 0;
+            for (int i = 0; i < kLowerThreads; i++) { const unsigned long long v = qscan[i]; qscan[i] = r; r += v; }
+            qtot = r;
+        }
+        __syncthreads();
         if (b < P.n_circuits) {
             CircuitDev &C = B.circ[b];
             C.layer_base = carry_layer + off_l;
             C.meas_base = carry_meas + off_m;
             C.mech_base = carry_mech + off_x;
+            const unsigned long long qo = carry_qidx + qscan[threadIdx.x];
+            C.qidx_off = (uint32_t)min(qo, 0xFFFFFFFFull);
+            if (qo + qblocks > P.qidx_cap16) report(B.status, GP_ERR_CAPACITY, 9u, b, (uint32_t)min(qo + qblocks, 0xFFFFFFFFull));
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -113,12 +132,14 @@ __global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
             carry_layer = (uint32_t)min(L, 0xFFFFFFFFull);
             carry_meas = (uint32_t)min(Mm, 0xFFFFFFFFull);
             carry_mech = (uint32_t)min(X, 0xFFFFFFFFull);
+            carry_qidx += qtot;
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         if (carry_layer > P.max_layer_slots) report(B.status, GP_ERR_CAPACITY, 1u, carry_layer, P.max_layer_slots);
-        if (carry_meas > P.max_meas) report(B.status, GP_ERR_CAPACITY, 2u, carry_meas, P.max_meas);
+        if (carry_meas > P.max_meas || carry_meas > kMaxMeasurements)
+            report(B.status, GP_ERR_CAPACITY, 2u, carry_meas, min(P.max_meas, kMaxMeasurements));
         if (carry_mech > P.max_mech) report(B.status, GP_ERR_CAPACITY, 3u, carry_mech, P.max_mech);
         B.status->n_mech = carry_mech;
     }
@@ -137,7 +158,7 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
     const Params &P = *B.params;
     const uint32_t t = blockIdx.x;
     if (t >= P.n_tiles) return;
-    if (B.status->code != 0) return;
+    if (status_set(B.status)) return;
     const uint2 tile = B.tiles[t];
     const uint32_t b = tile.x;
     const CircuitDev &C = B.circ[b];
@@ -169,7 +190,7 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
         case K_M: case K_MR: case K_MX: case K_MRX:
             bad = op.y >= C.n_qubits;
             aux = meas;
-            if (!bad) B.meas_layer[C.meas_base + meas] = ticks;
+            if (!bad) B.meas_lq[C.meas_base + meas] = make_uint2(ticks, op.y | ((k == K_MX || k == K_MRX) ? 0x80000000u : 0u));
             break;
         case K_CX: case K_CZ:
             bad = op.y >= C.n_qubits || op.z >= C.n_qubits || op.y == op.z;
@@ -216,10 +237,15 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
 // One block per layer slot.  Slots are numbered across the batch; circuit b
 // owns slots [layer_base, layer_base + n_layers] (the last one is the end
 // sentinel, which has no rows).
-__global__ void __launch_bounds__(kPackThreads) layer_pack_kernel(Buffers B) {
-    extern __shared__ uint32_t gt[];          // qubit -> row of its gate in this layer
+//
+// Shared memory: gt[q] = row of q's gate in the layer; cnt[q] = q's list
+// lengths, after-gate entries in the low half and before-gate entries in
+// the high half (a layer has at most kMaxLayerRows rows, so neither half
+// can carry into the other), later turned into fill positions.
+__global__ void __launch_bounds__(kPackThreads) layer_index_kernel(Buffers B) {
+    extern __shared__ uint32_t lsm[];
     const Params &P = *B.params;
-    if (B.status->code != 0) return;
+    if (status_set(B.status)) return;
     const uint32_t g = blockIdx.x;
     // circuit owning slot g (circuits are laid out in slot order)
     uint32_t lo = 0, hi = P.n_circuits;
@@ -229,9 +255,21 @@ __global__ void __launch_bounds__(kPackThreads) layer_pack_kernel(Buffers B) {
     }
     const uint32_t b = lo;
     const CircuitDev &C = B.circ[b];
-    if (g < C.layer_base || g >= C.layer_base + C.n_layers) return;
+    if (g < C.layer_base || g > C.layer_base + C.n_layers) return;
+    if (g == C.layer_base + C.n_layers) {
+        // end sentinel: no rows, no before-gate noise
+        if (threadIdx.x == 0) B.layer_seg[g] = make_uint4(C.n_ops, 0, 0, 0);
+        return;
+    }
+    const uint32_t L = g - C.layer_base;
+    const uint32_t nq = C.n_qubits;
     const uint32_t rs = B.layer_start[g], re = B.layer_start[g + 1];
-    for (uint32_t q = threadIdx.x; q < C.n_qubits; q += kPackThreads) gt[q] = kNone;
+    if (re - rs > kMaxLayerRows) {
+        if (threadIdx.x == 0) report(B.status, GP_ERR_CAPACITY, 10u, b, L);
+        return;
+    }
+    uint32_t *gt = lsm, *cnt = lsm + P.max_qubits;
+    for (uint32_t q = threadIdx.x; q < nq; q += kPackThreads) { gt[q] = kNone; cnt[q] = 0u; }
     __syncthreads();
     for (uint32_t r = rs + threadIdx.x; r < re; r += kPackThreads) {
         const uint4 op = C.ops[r];
@@ -241,59 +279,94 @@ __global__ void __launch_bounds__(kPackThreads) layer_pack_kernel(Buffers B) {
         if (dup) report(B.status, GP_ERR_INVALID, 4u, b, r);
     }
     __syncthreads();
-    // category of a row: 0 none, 1 gate, 2 noise after the gates, 3 before
-    auto category = [&](uint32_t r, uint4 &op) -> uint32_t {
-        op = C.ops[r];
-        if (is_gate(op.x)) return 1u;
-        if (!is_noise(op.x)) return 0u;
+    // side of a noise row: 0 after the gates of its qubit(s), 1 before;
+    // 2 for rows that are not noise (or a two-qubit row split across sides)
+    auto side = [&](uint32_t r, const uint4 &op) -> uint32_t {
+        if (!is_noise(op.x)) return 2u;
         const uint32_t ga = gt[op.y];
         const bool bef = ga != kNone && ga > r;
         if (op.x == K_DEP2) {
             const uint32_t gb = gt[op.z];
             if ((gb != kNone && gb > r) != bef) {
                 report(B.status, GP_ERR_INVALID, 3u, b, r);
-                return 0u;
+                return 2u;
             }
         }
-        return bef ? 3u : 2u;
+        return bef ? 1u : 0u;
     };
-    __shared__ uint32_t warp_tmp[kPackThreads / 32];
-    // pass 1: totals per category
-    uint32_t cg = 0, ca = 0, cb = 0, tot;
     for (uint32_t r = rs + threadIdx.x; r < re; r += kPackThreads) {
-        uint4 op;
-        const uint32_t c = category(r, op);
-        cg += c == 1u;
-        ca += c == 2u;
-        cb += c == 3u;
+        const uint4 op = C.ops[r];
+        const uint32_t sd = side(r, op);
+        if (sd == 2u) continue;
+        const uint32_t inc = sd ? 0x10000u : 1u;
+        atomicAdd(&cnt[op.y], inc);
+        if (op.x == K_DEP2) atomicAdd(&cnt[op.z], inc);
     }
-    block_exclusive_scan<kPackThreads>(cg, warp_tmp, tot);
-    const uint32_t nG = tot;
-    block_exclusive_scan<kPackThreads>(ca, warp_tmp, tot);
-    const uint32_t nA = tot;
-    block_exclusive_scan<kPackThreads>(cb, warp_tmp, tot);
-    const uint32_t nB = tot;
-    // pass 2: chunks of kPackThreads consecutive rows keep row order; within
-    // a chunk the three counts fit 10-bit fields of one scanned word
-    uint32_t run[3] = {0, 0, 0};
-    const uint32_t seg0[3] = {rs, rs + nG, rs + nG + nA};
-    for (uint32_t base = rs; base < re; base += kPackThreads) {
-        const uint32_t r = base + threadIdx.x;
-        uint4 op = make_uint4(0, 0, 0, 0);
-        const uint32_t c = r < re ? category(r, op) : 0u;
-        const uint32_t v = c ? (1u << (10u * (c - 1u))) : 0u;
-        uint32_t ctot;
-        const uint32_t ex = block_exclusive_scan<kPackThreads>(v, warp_tmp, ctot);
-        if (c) {
-            const uint32_t rank = ((ex >> (10u * (c - 1u))) & 0x3FFu) + run[c - 1u];
-            const uint32_t aux = (is_measure(op.x) || is_noise(op.x)) ? B.aux[C.op_base + r] : 0u;
-            B.packed[C.op_base + seg0[c - 1u] + rank] = pack_row(op.x, op.y, op.z, aux);
+    __syncthreads();
+    // exclusive scan of the packed counts: each thread a contiguous run of
+    // qubits, one block scan over the runs
+    __shared__ uint32_t warp_tmp[kPackThreads / 32];
+    const uint32_t per = (nq + kPackThreads - 1) / kPackThreads;
+    const uint32_t q0 = min(threadIdx.x * per, nq), q1 = min(q0 + per, nq);
+    uint32_t local = 0;
+    for (uint32_t q = q0; q < q1; q++) local += cnt[q];
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan<kPackThreads>(local, warp_tmp, tot);
+    const uint32_t n_after = tot & 0xFFFFu, n_before = tot >> 16;
+    const LayerGeo geo = layer_geo(nq);
+    unsigned char *blk = B.qidx + (size_t)C.qidx_off * 16u + (size_t)L * geo.bytes;
+    uint16_t *boff = reinterpret_cast<uint16_t *>(blk);
+    uint32_t *gate = reinterpret_cast<uint32_t *>(blk + 2u * geo.qb);
+    uint16_t *aoff = reinterpret_cast<uint16_t *>(blk + 2u * geo.qb + 4u * geo.nq4);
+    for (uint32_t q = q0; q < q1; q++) {
+        const uint32_t c = cnt[q];
+        aoff[q] = (uint16_t)(run & 0xFFFFu);
+        boff[q] = (uint16_t)(run >> 16);
+        cnt[q] = run;
+        run += c;
+    }
+    if (threadIdx.x == 0) {
+        aoff[nq] = (uint16_t)n_after;
+        boff[nq] = (uint16_t)n_before;
+        B.layer_seg[g] = make_uint4(rs, n_after, n_before, 0u);
+    }
+    __syncthreads();
+    // each qubit's gate as seen from the qubit
+    for (uint32_t q = threadIdx.x; q < geo.nq4; q += kPackThreads) {
+        uint32_t v = GV_NONE;
+        const uint32_t r = q < nq ? gt[q] : kNone;
+        if (r != kNone) {
+            const uint4 op = C.ops[r];
+            if (op.x == K_CX) v = (op.y == q) ? (GV_CX_C << 28) | op.z : (GV_CX_T << 28) | op.y;
+            else if (op.x == K_CZ) v = (op.y == q) ? (GV_CZ_A << 28) | op.z : (GV_CZ_B << 28) | op.y;
+            else v = (op.x << 28) | (is_measure(op.x) ? B.aux[C.op_base + r] : 0u);
         }
-        run[0] += ctot & 0x3FFu;
-        run[1] += (ctot >> 10) & 0x3FFu;
-        run[2] += ctot >> 20;
+        gate[q] = v;
     }
-    if (threadIdx.x == 0) B.layer_seg[g] = make_uint4(rs, rs + nG, rs + nG + nA, rs + nG + nA + nB);
+    // fill the lists: before-gate lists start at the layer's first slot,
+    // after-gate lists end at its last
+    uint2 *before = B.lists + 2ull * (C.op_base + rs);
+    uint2 *after = B.lists + 2ull * (C.op_base + re) - n_after;
+    for (uint32_t r = rs + threadIdx.x; r < re; r += kPackThreads) {
+        const uint4 op = C.ops[r];
+        if (!is_noise(op.x)) continue;
+        const uint32_t ga = gt[op.y];
+        const bool bef = ga != kNone && ga > r;
+        if (op.x == K_DEP2) {
+            const uint32_t gb = gt[op.z];
+            if ((gb != kNone && gb > r) != bef) continue;     // reported above
+        }
+        // the second qubit field is meaningful (and validated) only for
+        // two-qubit noise
+        const uint2 row = pack_row(op.x, op.y, op.x == K_DEP2 ? op.z : 0u, B.aux[C.op_base + r]);
+        const uint32_t inc = bef ? 0x10000u : 1u;
+        const uint32_t pa = atomicAdd(&cnt[op.y], inc);
+        if (bef) before[pa >> 16] = row; else after[pa & 0xFFFFu] = row;
+        if (op.x == K_DEP2) {
+            const uint32_t pb = atomicAdd(&cnt[op.z], inc);
+            if (bef) before[pb >> 16] = row; else after[pb & 0xFFFFu] = row;
+        }
+    }
 }
 
 }  // namespace
@@ -304,8 +377,13 @@ void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, u
     tile_count_kernel<<<grid, kLowerThreads, 0, s>>>(b);
     tile_scan_kernel<<<1, kLowerThreads, 0, s>>>(b);
     tile_lower_kernel<<<grid, kLowerThreads, 0, s>>>(b);
-    layer_pack_kernel<<<layer_slots, kPackThreads, max_qubits * sizeof(uint32_t), s>>>(b);
+    layer_index_kernel<<<layer_slots, kPackThreads, 2u * max_qubits * sizeof(uint32_t), s>>>(b);
     *launches += 4;
+}
+
+cudaError_t lowering_setup(uint32_t max_qubits) {
+    return cudaFuncSetAttribute(layer_index_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2u * max_qubits * sizeof(uint32_t)));
 }
 
 }  // namespace gpdem

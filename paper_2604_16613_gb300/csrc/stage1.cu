@@ -8,67 +8,104 @@
 //   zs[q] bit j = the same for a Z error.
 // It walks the TICK layers backward from the latest measurement of the
 // column's detectors (Eq. init-slp seeds the bits there) and stops once every
-// plane is zero and no earlier measurement of the column remains, so a column
-// only pays for the layers its detecting regions cover.
+// plane is zero and no earlier measurement of the column remains.
 //
-// Layers arrive pre-packed by the lowering (gates | noise after the gates |
-// noise before the gates, 8 bytes a row).  Each layer is staged into shared
-// memory by a 1-D bulk copy (TMA) issued one layer ahead into a
-// double buffer and tracked by an mbarrier; layers larger than a buffer are
-// read from global memory directly.  Per layer L two barrier-separated
-// phases run:
-//   A  mask words of the noise rows acting after the gates of L and before
-//      the gates of L+1 (the planes hold the state between the two), and the
-//      termination test;
-//   B  the gates of L undone backward: H swaps the planes, S: x ^= z,
-//      CX(c,t): x_c ^= x_t and z_t ^= z_c, CZ(a,b): x_a ^= z_b and
-//      x_b ^= z_a; measurements XOR in the column's detector bits; resets
-//      clear the planes after checking that the detectors commute with them.
+// The walk is sparse: it touches only the qubits whose planes are non-zero
+// (the "active" qubits, a few per detector), never the whole layer.  A
+// candidate list holds every qubit whose planes may be non-zero (the active
+// qubits of the last layer plus the qubits the last layer's gates and
+// measurements touched); per layer L two barrier-separated phases run:
+//   A  each candidate whose planes are non-zero stays active; a half-warp
+//      evaluates the mask words of the noise rows touching it after the gates
+//      of L and before the gates of L+1 (the planes hold the state between
+//      the two), one Pauli component per lane.  A two-qubit row is listed
+//      under both of its qubits and evaluated from the first active one.
+//   B  the gates of L on active qubits are undone backward: H swaps the
+//      planes, S: x ^= z, CX(c,t): x_c ^= x_t and z_t ^= z_c, CZ(a,b):
+//      x_a ^= z_b and x_b ^= z_a; measurements XOR in the column's detector
+//      bits; resets clear the planes after checking that the detectors
+//      commute with them.  A two-qubit gate whose partner was inactive makes
+//      the partner a candidate, and so does a measurement of the column on
+//      an inactive qubit.
 // A component's mask word is the XOR of the planes its Pauli names (Y = X xor
 // Z, two-qubit terms combine both qubits: Sec. 2.3.4).  Non-zero words become
-// 16-byte records {mechanism, column, word}; they are staged in shared memory
-// during phase A and copied to the block's chunk of the global record pool
-// during phase B, so the walk never waits on a global atomic.
+// 16-byte records {mechanism, column, word} that every warp writes straight to
+// its own chunk of the global record pool (a warp-uniform running position;
+// the next chunk is requested ahead, so the walk never waits on a global
+// atomic).  The last warp of the block is a producer: it stages the layer
+// windows, concurrently with phase A of the other (consumer) warps, and
+// publishes with each window a descriptor of where its parts are.
+//
+// What a step at L reads -- the gates of L as seen from each qubit, the
+// after-gate list offsets of L, the before-gate list offsets of L+1 and the
+// list entries between them -- is contiguous in the lowering's layer index,
+// so it is staged into shared memory by two 1-D bulk copies (TMA) issued
+// several layers ahead into a ring of window buffers, each tracked by an
+// mbarrier.  Windows too large for a buffer are read from global memory.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gpdem {
 
 namespace {
 
-constexpr int kRowBufs = 3;         // layer buffers: L+1 (held), L, L-1 .. L-2 in flight
-constexpr int kSegCache = 256;      // layer segments cached in shared memory
-constexpr int kActive = 2 * kRowBuf; // noise rows examined per emission piece
+constexpr int kSegCache = 256;      // layer segments cached for the producer
+constexpr int kMaxBufs = 4;         // window ring slots at most
 
 struct Smem {
     unsigned long long *xs, *zs;
-    unsigned long long *ent_w;
-    unsigned long long *st_word;    // staged records: word
-    uint4 *segc;
-    uint2 *rows[kRowBufs];
-    uint32_t *ent_m;
-    uint32_t *st_mech;              // staged records: mechanism
-    uint16_t *act;                  // active noise rows of the current piece
+    unsigned long long *ent_w;      // entry words (merged per measurement)
+    uint4 *segc;                    // layer segments [seg_lo, seg_lo + kSegCache)
+    uint32_t *ent_m;                // entry measurement (sorted)
+    uint32_t *ent_l;                // entry layer
+    uint32_t *ent_q;                // entry qubit | x-basis << 31
+    uint16_t *cand0, *cand1;        // candidate lists (ping-pong)
+    unsigned char *bits;            // per qubit: on the list being built
+    unsigned char *win;             // window buffers
 };
 
+__host__ __device__ inline uint32_t round8(uint32_t x) { return (x + 7u) & ~7u; }
+
+// bytes of the fixed part of the layout (everything but the windows)
+__host__ __device__ inline size_t smem_base_bytes(uint32_t maxq) {
+    const size_t q8 = round8(maxq);
+    size_t b = 16 * q8                              // xs, zs
+               + 8 * (size_t)kMaxEntries            // ent_w
+               + 16 * (size_t)kSegCache             // segc
+               + 12 * (size_t)kMaxEntries           // ent_m, ent_l, ent_q
+               + 4 * q8                             // cand0, cand1
+               + q8;                                // bits
+    return (b + 127) & ~(size_t)127;
+}
+
+// bytes of the index part of a window buffer
+__host__ __device__ inline uint32_t window_index_bytes(uint32_t maxq) {
+    const uint32_t b = layer_geo(maxq).bytes;
+    return (b + 127u) & ~127u;
+}
+
 __device__ __forceinline__ Smem carve(unsigned char *base, uint32_t maxq) {
+    const uint32_t q8 = round8(maxq);
     Smem s;
     s.xs = reinterpret_cast<unsigned long long *>(base);
-    s.zs = s.xs + maxq;
-    s.ent_w = s.zs + maxq;
-    s.st_word = s.ent_w + kMaxEntries;
-    s.segc = reinterpret_cast<uint4 *>(s.st_word + kStageRecs);
-    uint2 *rw = reinterpret_cast<uint2 *>(s.segc + kSegCache);
-    for (int i = 0; i < kRowBufs; i++) s.rows[i] = rw + i * (kRowBuf + 2);
-    s.ent_m = reinterpret_cast<uint32_t *>(rw + kRowBufs * (kRowBuf + 2));
-    s.st_mech = s.ent_m + kMaxEntries;
-    s.act = reinterpret_cast<uint16_t *>(s.st_mech + kStageRecs);
+    s.zs = s.xs + q8;
+    s.ent_w = s.zs + q8;
+    s.segc = reinterpret_cast<uint4 *>(s.ent_w + kMaxEntries);
+    s.ent_m = reinterpret_cast<uint32_t *>(s.segc + kSegCache);
+    s.ent_l = s.ent_m + kMaxEntries;
+    s.ent_q = s.ent_l + kMaxEntries;
+    s.cand0 = reinterpret_cast<uint16_t *>(s.ent_q + kMaxEntries);
+    s.cand1 = s.cand0 + q8;
+    s.bits = reinterpret_cast<unsigned char *>(s.cand1 + q8);
+    s.win = base + smem_base_bytes(maxq);
     return s;
 }
 
+__device__ __forceinline__ uint16_t *cand_list(const Smem &s, uint32_t i) { return i ? s.cand1 : s.cand0; }
+
 // XOR of the entry words recorded for measurement m (entries sorted by m)
-__device__ __forceinline__ unsigned long long meas_word(const Smem &s, uint32_t n_ent, uint32_t m,
-                                                        uint32_t m_lo, uint32_t m_hi) {
-    if (m < m_lo || m > m_hi) return 0ull;
+__device__ __forceinline__ unsigned long long meas_word(const Smem &s, uint32_t n_ent, uint32_t m) {
     uint32_t lo = 0, hi = n_ent;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
@@ -79,170 +116,91 @@ __device__ __forceinline__ unsigned long long meas_word(const Smem &s, uint32_t 
     return w;
 }
 
-// rows of one layer: a base pointer (shared or global) and segment bounds
-struct LayerView {
-    const uint2 *rows;      // rows[0] is the layer's first packed row
-    uint32_t g, a, b;       // ends of the gate, after-noise, before-noise segments
+// what one walk step reads (shared or global memory), published by the
+// producer with the window
+struct Window {
+    const uint32_t *gate;       // gate of each qubit in L (step L >= 0)
+    const uint16_t *aoff;       // after-gate list offsets of L
+    const uint16_t *boff;       // before-gate list offsets of L + 1
+    const uint2 *lists;         // after-gate lists of L, then before-gate
+                                // lists of L + 1
+    uint32_t n_after;           // entries of the after-gate lists
 };
 
 struct Shared {
-    unsigned long long mbar[kRowBufs];
-    uint32_t cnt[2];        // staged records per epoch parity (one data buffer:
-                            // an epoch's records are copied out before the
-                            // next epoch stages any)
-    uint32_t chunk_pos, chunk_end;
-    uint32_t item, bail, nent, lmax, lmin, tmo;
-    uint32_t n_act;         // active rows listed for the current piece
-    uint32_t next_chunk;    // record chunk requested ahead (kNone: none)
+    unsigned long long mbar[kMaxBufs];
+    Window desc[kMaxBufs];
+    uint32_t item, bail, nent, lmax, tmo;
+    uint32_t n_act[2];      // per candidate list: qubits kept in phase A
+    uint32_t n_new[2];      // ... and qubits added in phase B
 };
 
-// The noise rows of one emission step are rows [g, a) of layer L (after its
-// gates) followed by rows [a', b') of layer L+1 (before its gates), indexed
-// 0 .. nA + nB - 1.
-__device__ __forceinline__ uint2 emission_row(const LayerView &cur, const LayerView &nxt, uint32_t nA, uint32_t i) {
-    return i < nA ? cur.rows[cur.g + i] : nxt.rows[nxt.a + (i - nA)];
-}
-
-// A1: list the rows of [p0, p1) whose planes are not all zero (warp-aggregated
-// appends to the shared list).
-template <int NT>
-__device__ __forceinline__ void list_active(const Smem &s, Shared &sh, const LayerView &cur, const LayerView &nxt,
-                                            uint32_t nA, uint32_t p0, uint32_t p1) {
-    const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t base = p0; base < p1; base += NT) {
-        const uint32_t i = base + threadIdx.x;
-        bool active = false;
-        if (i < p1) {
-            const uint2 r = emission_row(cur, nxt, nA, i);
-            const uint32_t a = row_a(r);
-            unsigned long long v = s.xs[a] | s.zs[a];
-            if (row_kind(r) == K_DEP2) {
-                const uint32_t bq = row_b(r);
-                v |= s.xs[bq] | s.zs[bq];
-            }
-            active = v != 0ull;
-        }
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, active);
-        if (m == 0u) continue;
-        uint32_t wbase = 0;
-        if (lane == 0u) wbase = atomicAdd(&sh.n_act, (uint32_t)__popc(m));
-        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
-        if (active) s.act[wbase + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(i - p0);
-    }
-}
-
-// A2: every half-warp takes one listed row and evaluates its Pauli
-// components one per lane; non-zero words are staged with one reservation per
-// warp (spilling straight to the pool if the stage is full).
-template <int NT>
-__device__ __forceinline__ void emit_active(const Buffers &B, const Smem &s, Shared &sh, const CircuitDev &C,
-                                            const LayerView &cur, const LayerView &nxt, uint32_t nA, uint32_t p0,
-                                            uint32_t n_act, uint32_t col_tag, uint32_t level, uint32_t sb,
-                                            uint32_t rec_cap) {
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t c = lane & 15u;
-    const uint32_t mech_base = C.mech_base;
-    for (uint32_t base = 2u * warp; base < n_act; base += 2u * (NT / 32)) {
-        const uint32_t idx = base + (lane >> 4);
-        unsigned long long w = 0ull;
-        uint32_t mech = 0;
-        if (idx < n_act) {
-            const uint2 r = emission_row(cur, nxt, nA, p0 + s.act[idx]);
-            const uint32_t kind = row_kind(r);
-            if (c < n_comp(kind, level)) {
-                const uint32_t code = comp_planes(kind, c);
-                const uint32_t a = row_a(r), bq = row_b(r);
-                if (code & 1u) w ^= s.xs[a];
-                if (code & 2u) w ^= s.zs[a];
-                if (code & 4u) w ^= s.xs[bq];
-                if (code & 8u) w ^= s.zs[bq];
-                mech = mech_base + r.y + c;
-            }
-        }
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, w != 0ull);
-        if (m == 0u) continue;
-        uint32_t wbase = 0;
-        if (lane == 0u) wbase = atomicAdd(&sh.cnt[sb], (uint32_t)__popc(m));
-        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
-        if (w != 0ull) {
-            const uint32_t pos = wbase + __popc(m & ((1u << lane) - 1u));
-            if (pos < (uint32_t)kStageRecs) {
-                s.st_mech[pos] = mech;
-                s.st_word[pos] = w;
-            } else {
-                const uint32_t g = atomicAdd(&B.status->rec_count, 1u);
-                if (g < rec_cap) {
-                    B.records[g] = make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
-                    atomicAdd(&B.mech_cnt[mech], 1u);
-                } else {
-                    report(B.status, GP_ERR_CAPACITY, 8u, g, rec_cap);
-                }
-            }
-        }
-    }
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
+__global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq, uint32_t nbuf, uint32_t list_cap,
+                                                       uint32_t wbytes, uint32_t wchunk) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Smem s = carve(smem_raw, maxq);
     __shared__ Shared sh;
+    constexpr uint32_t NW = NT / 32;               // warps
+    constexpr uint32_t NCW = NW - 1;               // consumer warps (the last one produces)
+    constexpr uint32_t NCT = NCW * 32;             // consumer threads
     const Params &P = *B.params;
     const uint32_t level = P.level, rec_cap = P.rec_cap;
-    const uint4 *layer_seg = B.layer_seg;
+    const uint32_t lane = threadIdx.x & 31u, l16 = lane & 15u, half = lane >> 4;
+    const uint32_t warp = threadIdx.x >> 5;
+    const bool producer = warp == NW - 1;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t windex = window_index_bytes(maxq);
+    // ring of window slots: window L in slot (L + 1) mod nring; windows are
+    // staged in shared memory only with nbuf >= 2 buffers
+    const uint32_t nring = nbuf >= 2u ? nbuf : 2u;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kRowBufs; i++) mbar_init(&sh.mbar[i], 1);
+        for (int i = 0; i < kMaxBufs; i++) mbar_init(&sh.mbar[i], 1);
         fence_mbar_init();
-        sh.cnt[0] = sh.cnt[1] = 0;
-        sh.chunk_pos = sh.chunk_end = 0;
         sh.tmo = 0;
-        sh.next_chunk = kNone;
-        sh.n_act = 0;
     }
     __syncthreads();
-    uint32_t phase_bits = 0u;         // mbarrier parity per row buffer (bit i)
-    uint32_t pend_bits = 0u;          // copies issued and not yet waited for
-    uint32_t epoch = 0;               // emission epochs alternate staging buffers
+    uint32_t phase_bits = 0u;         // mbarrier parity per ring slot (bit i)
     bool timed_out = false;
+    // this warp's chunk of the record pool [ck_pos, ck_end) and the next one,
+    // requested ahead (its base lives in lane 0 until it is taken)
+    uint32_t ck_pos = 0, ck_end = 0, ck_next = 0;
+    bool has_next = false;
+    // producer warp: first layer held by the segment cache
+    uint32_t seg_lo = 0xFFFFFFFFu;
 
-    // thread 0, at the start of every phase A: retire the previous epoch's
-    // staged records (copied during the last phase B) and make sure the
-    // block's chunk can take a full staging buffer
-    auto housekeeping = [&](uint32_t ep) {
-        if (threadIdx.x != 0) return;
-        if (ep > 0) {
-            const uint32_t pb = (ep - 1u) & 1u;
-            sh.chunk_pos += min(sh.cnt[pb], (uint32_t)kStageRecs);
-            sh.cnt[pb] = 0;
+    // room for `need` more records in this warp's chunk (warp-uniform);
+    // false once the pool is exhausted (reported)
+    auto warp_room = [&](uint32_t need) -> bool {
+        if (ck_end - ck_pos >= need) return true;
+        uint32_t nb = 0;
+        if (has_next) {
+            nb = __shfl_sync(0xFFFFFFFFu, ck_next, 0);
+        } else {
+            if (lane == 0u) nb = atomicAdd(&B.status->rec_count, wchunk);
+            nb = __shfl_sync(0xFFFFFFFFu, nb, 0);
         }
-        const uint32_t room = sh.chunk_end - sh.chunk_pos;
-        // ask for the next chunk while two stages still fit, so the atomic's
-        // latency is hidden behind later layers
-        if (room < 3u * (uint32_t)kStageRecs && sh.next_chunk == kNone)
-            sh.next_chunk = atomicAdd(&B.status->rec_count, kChunkRecs);
-        if (room < (uint32_t)kStageRecs) {
-            const uint32_t base = sh.next_chunk;
-            sh.next_chunk = kNone;
-            if (base == kNone || base + kChunkRecs > rec_cap || base + kChunkRecs < base) {
-                report(B.status, GP_ERR_CAPACITY, 8u, base, rec_cap);
-                sh.chunk_pos = sh.chunk_end = 0;   // nothing is flushed below
-            } else {
-                sh.chunk_pos = base;
-                sh.chunk_end = base + kChunkRecs;
-            }
+        has_next = false;
+        if (nb + wchunk > rec_cap || nb + wchunk < nb) {
+            if (lane == 0u) report(B.status, GP_ERR_CAPACITY, 8u, nb, rec_cap);
+            ck_pos = ck_end = 0;
+            return false;
         }
+        ck_pos = nb;
+        ck_end = nb + wchunk;
+        return true;
     };
-    // all threads, during phase B: copy epoch ep's staged records to the chunk
-    auto flush = [&](uint32_t ep, uint32_t col_tag) {
-        const uint32_t sb = ep & 1u;
-        const uint32_t n = min(sh.cnt[sb], (uint32_t)kStageRecs);
-        if (sh.chunk_end - sh.chunk_pos < n) return;    // capacity already reported
-        for (uint32_t i = threadIdx.x; i < n; i += NT) {
-            const unsigned long long w = s.st_word[i];
-            const uint32_t mech = s.st_mech[i];
-            B.records[sh.chunk_pos + i] = make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
-            atomicAdd(&B.mech_cnt[mech], 1u);
+    // once the warp holds a chunk, ask for the next one while half of it is
+    // left (the atomic's result is read only when the chunk is switched)
+    auto warp_prefetch = [&]() {
+        if (!has_next && ck_end != 0u && ck_end - ck_pos < wchunk / 2u) {
+            if (lane == 0u) ck_next = atomicAdd(&B.status->rec_count, wchunk);
+            has_next = true;
         }
     };
 
@@ -252,7 +210,8 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
             sh.bail = (*(volatile uint32_t *)&B.status->code) != 0u;
             sh.nent = 0;
             sh.lmax = 0;
-            sh.lmin = 0xFFFFFFFFu;
+            sh.n_act[0] = sh.n_act[1] = 0;
+            sh.n_new[0] = sh.n_new[1] = 0;
         }
         __syncthreads();
         const uint32_t item = sh.item;
@@ -264,10 +223,13 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
         const bool is_obs = (C.n_obs > 0u) && (local == C.n_cols - 1u);
         const uint32_t col_tag = gcol | (is_obs ? kObsColFlag : 0u);
         const uint32_t nq = C.n_qubits;
+        const uint32_t mech_base = C.mech_base;
+        seg_lo = 0xFFFFFFFFu;             // the segment cache belongs to the last column
 
         for (uint32_t q = threadIdx.x; q < nq; q += NT) {
             s.xs[q] = 0ull;
             s.zs[q] = 0ull;
+            s.bits[q] = 0;
         }
         // (measurement, word) entries of this column (Eq. init-slp)
         if (!is_obs) {
@@ -329,173 +291,299 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
                 __syncthreads();
             }
         }
+        // merge the entries of one measurement: the first of a run holds the
+        // XOR of the run, the rest hold zero (the layer array holds the merged
+        // words meanwhile)
+        unsigned long long *merged = reinterpret_cast<unsigned long long *>(s.ent_l);
+        static_assert(kMaxEntries % 2 == 0, "ent_l and ent_q hold one 64-bit word per entry");
         for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
-            const uint32_t L = B.meas_layer[C.meas_base + s.ent_m[i]];
-            atomicMax(&sh.lmax, L);
-            atomicMin(&sh.lmin, L);
+            unsigned long long w = 0ull;
+            if (i == 0u || s.ent_m[i] != s.ent_m[i - 1u]) {
+                for (uint32_t j = i; j < n_ent && s.ent_m[j] == s.ent_m[i]; j++) w ^= s.ent_w[j];
+            }
+            merged[i] = w;
         }
         __syncthreads();
-        const uint32_t lmax = sh.lmax, lmin = sh.lmin;
-        const uint32_t m_lo = s.ent_m[0], m_hi = s.ent_m[n_ent - 1];
-        const uint4 *seg_g = layer_seg + C.layer_base;
-        const uint2 *packed = B.packed + C.op_base;
-        // the column's layer segments, cached once
-        const uint32_t n_cache = min(lmax + 1u, (uint32_t)kSegCache);
-        for (uint32_t i = threadIdx.x; i < n_cache; i += NT) s.segc[i] = seg_g[i];
+        for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
+            const unsigned long long w = merged[i];
+            s.ent_w[i] = w;
+        }
         __syncthreads();
-        auto segL = [&](uint32_t L) -> uint4 { return L < (uint32_t)kSegCache ? s.segc[L] : seg_g[L]; };
-        auto staged = [&](const uint4 &sg) -> bool {
-            const uint32_t n = sg.w - sg.x;
-            return n != 0u && n <= (uint32_t)kRowBuf;
-        };
-        auto row_delta = [&](const uint4 &sg) -> uint32_t {
-            return (uint32_t)((reinterpret_cast<uintptr_t>(packed + sg.x) & 15u) >> 3);
-        };
-        // stage layer L into buffer L % 3 (thread 0 issues the bulk copy)
-        auto issue = [&](uint32_t L) {
-            const uint4 sg = segL(L);
-            if (!staged(sg)) return;
-            const uint32_t bi = L % (uint32_t)kRowBufs;
-            if (threadIdx.x == NT - 32) {
-                const uint32_t delta = row_delta(sg);
-                const uint32_t bytes = ((sg.w - sg.x + delta) * 8u + 15u) & ~15u;
-                fence_proxy_async_smem();
-                mbar_expect_tx(&sh.mbar[bi], bytes);
-                bulk_load(s.rows[bi], packed + sg.x - delta, bytes, &sh.mbar[bi]);
+        for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
+            const uint2 lq = B.meas_lq[C.meas_base + s.ent_m[i]];
+            s.ent_l[i] = lq.x;
+            s.ent_q[i] = lq.y;
+            if (s.ent_w[i] != 0ull) atomicMax(&sh.lmax, lq.x + 1u);
+        }
+        __syncthreads();
+        if (sh.lmax == 0u) { __syncthreads(); continue; }   // every word cancelled
+        const uint32_t lmax = sh.lmax - 1u;
+        const uint32_t lmin = s.ent_l[0];
+
+        // ---- layer index geometry of this circuit --------------------------
+        const LayerGeo geo = layer_geo(nq);
+        const unsigned char *qbase = B.qidx + (size_t)C.qidx_off * 16u;
+        const uint2 *lbase = B.lists + 2ull * C.op_base;
+        const uint4 *seg_g = B.layer_seg + C.layer_base;
+        auto slot_of = [&](int L) -> uint32_t { return (uint32_t)(L + 1) % nring; };
+        // producer warp: publish window L (L = -1: the before-gate noise of
+        // layer 0) in its slot -- descriptor, then the bulk copies (or a plain
+        // arrive when the window is read from global memory)
+        auto post = [&](int L) {
+            const uint32_t need = L > 0 ? (uint32_t)L : 0u;
+            if (seg_lo == 0xFFFFFFFFu || need < seg_lo || (uint32_t)L + 1u >= seg_lo + (uint32_t)kSegCache) {
+                seg_lo = (uint32_t)L + 2u > (uint32_t)kSegCache ? (uint32_t)L + 2u - (uint32_t)kSegCache : 0u;
+                const uint32_t n = min((uint32_t)kSegCache, C.n_layers + 1u - seg_lo);
+                __syncwarp();
+                for (uint32_t i = lane; i < n; i += 32u) s.segc[i] = seg_g[seg_lo + i];
+                __syncwarp();
             }
-            pend_bits |= 1u << bi;
+            if (lane != 0u) return;
+            const uint4 s1 = s.segc[L + 1 - (int)seg_lo];
+            const uint32_t n_after = L >= 0 ? s.segc[L - (int)seg_lo].y : 0u;
+            const uint32_t list_start = 2u * s1.x - n_after;
+            const uint32_t list_n = n_after + s1.z;
+            const uint32_t slot = slot_of(L);
+            Window &d = sh.desc[slot];
+            d.n_after = n_after;
+            if (nbuf >= 2u && list_n + 1u <= list_cap) {
+                unsigned char *dst = s.win + (size_t)slot * wbytes;
+                const unsigned char *qsrc = L >= 0 ? qbase + (size_t)L * geo.bytes + 2u * geo.qb : qbase;
+                const uint32_t qbytes = L >= 0 ? 4u * geo.nq4 + 4u * geo.qb : 2u * geo.qb;
+                const uint32_t delta = list_start & 1u;
+                const uint32_t lbytes = list_n ? ((list_n + delta) * 8u + 15u) & ~15u : 0u;
+                d.lists = reinterpret_cast<const uint2 *>(dst + windex) + delta;
+                if (L >= 0) {
+                    d.gate = reinterpret_cast<const uint32_t *>(dst);
+                    d.aoff = reinterpret_cast<const uint16_t *>(dst + 4u * geo.nq4);
+                    d.boff = d.aoff + geo.qb;
+                } else {
+                    d.gate = nullptr;
+                    d.aoff = nullptr;
+                    d.boff = reinterpret_cast<const uint16_t *>(dst);
+                }
+                mbar_expect_tx(&sh.mbar[slot], qbytes + lbytes);
+                bulk_load(dst, qsrc, qbytes, &sh.mbar[slot]);
+                if (lbytes) bulk_load(dst + windex, lbase + list_start - delta, lbytes, &sh.mbar[slot]);
+            } else {
+                d.lists = lbase + list_start;
+                if (L >= 0) {
+                    const unsigned char *p = qbase + (size_t)L * geo.bytes + 2u * geo.qb;
+                    d.gate = reinterpret_cast<const uint32_t *>(p);
+                    d.aoff = reinterpret_cast<const uint16_t *>(p + 4u * geo.nq4);
+                    d.boff = d.aoff + geo.qb;
+                } else {
+                    d.gate = nullptr;
+                    d.aoff = nullptr;
+                    d.boff = reinterpret_cast<const uint16_t *>(qbase);
+                }
+                mbar_arrive(&sh.mbar[slot]);
+            }
         };
-        // every thread waits for layer L's copy itself (no block barrier)
-        auto wait = [&](uint32_t L) {
-            const uint32_t bi = L % (uint32_t)kRowBufs;
-            if (!((pend_bits >> bi) & 1u)) return;
-            if (!mbar_wait_bounded(&sh.mbar[bi], (phase_bits >> bi) & 1u)) sh.tmo = 1u;
-            phase_bits ^= 1u << bi;
-            pend_bits &= ~(1u << bi);
-        };
-        auto view = [&](uint32_t L) -> LayerView {
-            const uint4 sg = segL(L);
-            LayerView v;
-            v.rows = staged(sg) ? s.rows[L % (uint32_t)kRowBufs] + row_delta(sg) : packed + sg.x;
-            v.g = sg.y - sg.x;
-            v.a = sg.z - sg.x;
-            v.b = sg.w - sg.x;
-            return v;
+        // every thread waits for the window of step L itself and reads its
+        // descriptor
+        auto wait = [&](int L) -> Window {
+            const uint32_t slot = slot_of(L);
+            if (!mbar_wait_bounded(&sh.mbar[slot], (phase_bits >> slot) & 1u)) sh.tmo = 1u;
+            phase_bits ^= 1u << slot;
+            return sh.desc[slot];
         };
 
-        // backward wave over the layers
-        uint32_t L = lmax;
+        // phase A for one candidate list (consumer warps): keep the non-zero
+        // candidates (appended to list `out`) and emit the mask words of their
+        // noise rows; with `after` false only the before-gate lists are read
+        // (step -1).  The two half-warps of a warp take two candidates in
+        // lockstep, so ballots span the whole warp.
+        auto phase_a = [&](const Window &v, const uint16_t *in, uint32_t n_in, uint32_t out, bool after,
+                           bool check_initial) {
+            uint16_t *outl = cand_list(s, out);
+            warp_prefetch();
+            for (uint32_t base = 2u * warp; base < n_in; base += 2u * NCW) {
+                const uint32_t c = base + half;
+                const bool valid = c < n_in;
+                const uint32_t q = valid ? in[c] : 0u;
+                const unsigned long long xq = valid ? s.xs[q] : 0ull, zq = valid ? s.zs[q] : 0ull;
+                const bool act = (xq | zq) != 0ull;
+                if (valid && !act && l16 == 0u) s.bits[q] = 0;
+                const unsigned am = __ballot_sync(0xFFFFFFFFu, act && l16 == 0u);
+                if (am) {
+                    uint32_t abase = 0;
+                    if (lane == 0u) abase = atomicAdd(&sh.n_act[out], (uint32_t)__popc(am));
+                    abase = __shfl_sync(0xFFFFFFFFu, abase, 0);
+                    if (act && l16 == 0u) {
+                        outl[abase + __popc(am & lt_mask)] = (uint16_t)q;
+                        if (check_initial && zq != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, 0xFFFFFFFFu, gcol);
+                    }
+                }
+                uint32_t a0 = 0, na = 0, b0 = 0, n = 0;
+                if (act) {
+                    if (after) { a0 = v.aoff[q]; na = v.aoff[q + 1u] - a0; }
+                    b0 = v.boff[q];
+                    n = na + (v.boff[q + 1u] - b0);
+                }
+                const uint32_t nmax = max(n, __shfl_xor_sync(0xFFFFFFFFu, n, 16));
+                for (uint32_t i = 0; i < nmax; i++) {
+                    bool has = i < n;
+                    uint2 r = make_uint2(0u, 0u);
+                    if (has) r = v.lists[i < na ? a0 + i : v.n_after + b0 + (i - na)];
+                    const uint32_t kind = row_kind(r), ra = row_a(r), rb = row_b(r);
+                    // a two-qubit row is evaluated from its first qubit when
+                    // that one is active
+                    if (has && kind == K_DEP2 && q == rb && (s.xs[ra] | s.zs[ra]) != 0ull) has = false;
+                    unsigned long long w = 0ull;
+                    if (has && l16 < n_comp(kind, level)) {
+                        const uint32_t code = comp_planes(kind, l16);
+                        if (code & 1u) w ^= s.xs[ra];
+                        if (code & 2u) w ^= s.zs[ra];
+                        if (code & 4u) w ^= s.xs[rb];
+                        if (code & 8u) w ^= s.zs[rb];
+                    }
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, w != 0ull);
+                    if (m == 0u) continue;
+                    const uint32_t cnt = (uint32_t)__popc(m);
+                    if (!warp_room(cnt)) continue;
+                    if (w != 0ull) {
+                        const uint32_t mech = mech_base + r.y + l16;
+                        B.records[ck_pos + __popc(m & lt_mask)] =
+                            make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+                        atomicAdd(&B.mech_cnt[mech], 1u);
+                    }
+                    ck_pos += cnt;
+                }
+            }
+        };
+        // append the qubits of the lanes with `add` set to the list being
+        // built (one shared atomic per warp)
+        auto append_new = [&](uint16_t *list, uint32_t n_keep, uint32_t o, bool add, uint32_t q) {
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, add);
+            if (m == 0u) return;
+            uint32_t nb = 0;
+            if (lane == 0u) nb = atomicAdd(&sh.n_new[o], (uint32_t)__popc(m));
+            nb = __shfl_sync(0xFFFFFFFFu, nb, 0);
+            if (add) list[n_keep + nb + __popc(m & lt_mask)] = (uint16_t)q;
+        };
+
+        // ---- backward wave over the layers ---------------------------------
+        // At the start of step L the producer refills the slot step L+1 used
+        // with window L - nring + 1, so nring - 1 windows are in flight ahead.
+        int L = (int)lmax;
+        uint32_t p = 0;                   // list read in this step
+        uint32_t n_in = 0;                // its length
+        uint32_t cur = n_ent;             // entries with layer <= L
         bool stopped = false;
-        issue(L);
-        if (L > 0u) issue(L - 1u);
-        wait(L);
-        LayerView vnext{};            // layer L+1 (held for its before-noise)
+        int posted = L + 1;               // lowest window published so far
+        for (int k = L; k >= L - (int)nring + 2 && k >= -1; k--) {
+            if (producer) post(k);
+            posted = k;
+        }
         for (;;) {
-            const LayerView vcur = view(L);
-            // phase A: noise after the gates of L and before the gates of L+1,
-            // in pieces of at most kActive rows (one piece for staged layers)
-            housekeeping(epoch);
-            const uint32_t sb = epoch & 1u;
-            const bool tmo_here = sh.tmo != 0u;
-            const uint32_t nA = (L < lmax) ? vcur.a - vcur.g : 0u;
-            const uint32_t total = (L < lmax && !tmo_here) ? nA + (vnext.b - vnext.a) : 0u;
-            const bool check = (L < lmax) && (L + 1u <= lmin);
-            int any = 1;
-            for (uint32_t p0 = 0;; p0 += (uint32_t)kActive) {
-                const uint32_t p1 = min(p0 + (uint32_t)kActive, total);
-                if (p0 < p1) list_active<NT>(s, sh, vcur, vnext, nA, p0, p1);
-                int nonzero = 0;
-                if (check && p0 == 0u) {
-                    for (uint32_t q = threadIdx.x; q < nq; q += NT)
-                        if ((s.xs[q] | s.zs[q]) != 0ull) { nonzero = 1; break; }
-                }
-                const int piece_any = __syncthreads_or(nonzero);
-                if (p0 == 0u) any = piece_any;
-                const uint32_t n_act = sh.n_act;
-                if (n_act) emit_active<NT>(B, s, sh, C, vcur, vnext, nA, p0, n_act, col_tag, level, sb, rec_cap);
-                __syncthreads();
-                if (threadIdx.x == 0) sh.n_act = 0;
-                if (p1 >= total) break;
-                __syncthreads();
+            if (L - (int)nring + 1 >= -1) {
+                if (producer) post(L - (int)nring + 1);
+                posted = L - (int)nring + 1;
             }
-            if (sh.tmo) { timed_out = true; break; }
-            // phase B: records of phase A flushed, the gates of L undone
-            flush(epoch, col_tag);
-            epoch++;
-            if (check && !any) { stopped = true; break; }
-            if (L >= 2u) issue(L - 2u);     // into the buffer layer L+1 held
-            for (uint32_t i = threadIdx.x; i < vcur.g; i += NT) {
-                const uint2 r = vcur.rows[i];
-                const uint32_t k = row_kind(r), a = row_a(r);
-                switch (k) {
-                case K_H: { const unsigned long long t = s.xs[a]; s.xs[a] = s.zs[a]; s.zs[a] = t; break; }
-                case K_S: s.xs[a] ^= s.zs[a]; break;
-                case K_CX: { const uint32_t t = row_b(r); s.xs[a] ^= s.xs[t]; s.zs[t] ^= s.zs[a]; break; }
-                case K_CZ: {
-                    const uint32_t t = row_b(r);
-                    const unsigned long long za = s.zs[a], zb = s.zs[t];
-                    s.xs[a] ^= zb;
-                    s.xs[t] ^= za;
-                    break;
-                }
-                case K_R: case K_M: case K_MR: {
-                    if (s.zs[a] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, L, gcol);
-                    if (k != K_M) { s.xs[a] = 0ull; s.zs[a] = 0ull; }
-                    if (k != K_R) s.xs[a] ^= meas_word(s, n_ent, r.y, m_lo, m_hi);
-                    break;
-                }
-                case K_RX: case K_MX: case K_MRX: {
-                    if (s.xs[a] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, L, gcol);
-                    if (k != K_MX) { s.xs[a] = 0ull; s.zs[a] = 0ull; }
-                    if (k != K_RX) s.zs[a] ^= meas_word(s, n_ent, r.y, m_lo, m_hi);
-                    break;
-                }
-                default: break;
-                }
-            }
+            const Window v = wait(L);
+            // phase A
+            if (!producer && !sh.tmo) phase_a(v, cand_list(s, p), n_in, p ^ 1u, true, false);
             __syncthreads();
-            if (L == 0u) break;
-            vnext = vcur;
+            if (sh.tmo) { timed_out = true; break; }
+            // phase B: the gates of L undone
+            const uint32_t o = p ^ 1u;
+            const uint32_t n_keep = sh.n_act[o];
+            uint16_t *const keep = cand_list(s, o);
+            if (threadIdx.x == 0) { sh.n_act[p] = 0; sh.n_new[p] = 0; }
+            if (!producer) {
+                for (uint32_t base = 0; base < n_keep; base += NCT) {
+                    const uint32_t i = base + threadIdx.x;
+                    uint32_t partner = kNone;
+                    if (i < n_keep) {
+                        const uint32_t q = keep[i];
+                        const uint32_t g = v.gate[q];
+                        const uint32_t k = g >> 28, pay = g & 0x0FFFFFFFu;
+                        switch (k) {
+                        case K_H: { const unsigned long long t = s.xs[q]; s.xs[q] = s.zs[q]; s.zs[q] = t; break; }
+                        case K_S: s.xs[q] ^= s.zs[q]; break;
+                        case GV_CX_C: s.xs[q] ^= s.xs[pay]; s.zs[pay] ^= s.zs[q]; partner = pay; break;
+                        case GV_CX_T:
+                            if (s.bits[pay]) break;               // undone from the active control
+                            s.xs[pay] ^= s.xs[q]; s.zs[q] ^= s.zs[pay]; partner = pay; break;
+                        case GV_CZ_B:
+                            if (s.bits[pay]) break;               // undone from the active first qubit
+                            // fall through
+                        case GV_CZ_A: {
+                            const unsigned long long za = s.zs[q], zb = s.zs[pay];
+                            s.xs[q] ^= zb;
+                            s.xs[pay] ^= za;
+                            partner = pay;
+                            break;
+                        }
+                        case K_R: case K_M: case K_MR:
+                            if (s.zs[q] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, (uint32_t)L, gcol);
+                            if (k != K_M) { s.xs[q] = 0ull; s.zs[q] = 0ull; }
+                            if (k != K_R) s.xs[q] ^= meas_word(s, n_ent, pay);
+                            break;
+                        case K_RX: case K_MX: case K_MRX:
+                            if (s.xs[q] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, (uint32_t)L, gcol);
+                            if (k != K_MX) { s.xs[q] = 0ull; s.zs[q] = 0ull; }
+                            if (k != K_RX) s.zs[q] ^= meas_word(s, n_ent, pay);
+                            break;
+                        default: break;
+                        }
+                    }
+                    const bool add = partner != kNone && !s.bits[partner];
+                    if (add) s.bits[partner] = 1;
+                    append_new(keep, n_keep, o, add, partner);
+                }
+            }
+            // measurements of the column at L on inactive qubits
+            uint32_t lo = cur;
+            if (cur > 0u && s.ent_l[cur - 1u] == (uint32_t)L) {
+                uint32_t l0 = 0, h0 = cur;
+                while (l0 < h0) {
+                    const uint32_t mid = (l0 + h0) >> 1;
+                    if (s.ent_l[mid] < (uint32_t)L) l0 = mid + 1; else h0 = mid;
+                }
+                lo = l0;
+                if (!producer) {
+                    for (uint32_t base = lo; base < cur; base += NCT) {
+                        const uint32_t i = base + threadIdx.x;
+                        bool add = false;
+                        uint32_t q = 0;
+                        if (i < cur) {
+                            const unsigned long long w = s.ent_w[i];
+                            const uint32_t qv = s.ent_q[i];
+                            q = qv & 0x7FFFFFFFu;
+                            // an active qubit had the word applied by its gate above
+                            if (w != 0ull && !s.bits[q]) {
+                                if (qv >> 31) s.zs[q] ^= w; else s.xs[q] ^= w;
+                                s.bits[q] = 1;
+                                add = true;
+                            }
+                        }
+                        append_new(keep, n_keep, o, add, q);
+                    }
+                }
+            }
+            cur = lo;
+            __syncthreads();
+            n_in = sh.n_act[o] + sh.n_new[o];
+            p = o;
+            if (L == 0) break;
+            if (n_in == 0u && (uint32_t)(L - 1) < lmin) { stopped = true; break; }
             L--;
-            wait(L);
         }
         if (!stopped && !timed_out) {
-            // before-gate noise of layer 0, then the |0> initial state
-            const LayerView v0 = view(0u);
-            housekeeping(epoch);
-            const uint32_t sb = epoch & 1u;
-            const uint32_t total = v0.b - v0.a;
-            LayerView none = v0;
-            none.g = none.a;             // empty "after" part: rows [a, a)
-            for (uint32_t p0 = 0;; p0 += (uint32_t)kActive) {
-                const uint32_t p1 = min(p0 + (uint32_t)kActive, total);
-                if (p0 < p1) list_active<NT>(s, sh, none, v0, 0u, p0, p1);
-                __syncthreads();
-                const uint32_t n_act = sh.n_act;
-                if (n_act) emit_active<NT>(B, s, sh, C, none, v0, 0u, p0, n_act, col_tag, level, sb, rec_cap);
-                __syncthreads();
-                if (threadIdx.x == 0) sh.n_act = 0;
-                if (p1 >= total) break;
-                __syncthreads();
-            }
-            for (uint32_t q = threadIdx.x; q < nq; q += NT)
-                if (s.zs[q] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, 0xFFFFFFFFu, gcol);
-            __syncthreads();
-            flush(epoch, col_tag);
-            epoch++;
+            // before-gate noise of layer 0 on the candidates, then the |0>
+            // initial state
+            L = -1;
+            const Window v = wait(-1);
+            if (!producer && !sh.tmo) phase_a(v, cand_list(s, p), n_in, p ^ 1u, false, true);
         }
-        // copies still in flight after an early stop land before the buffers
+        // windows published ahead of an early stop land before their slots
         // are reused
-        for (uint32_t i = 0; i < (uint32_t)kRowBufs; i++) {
-            if ((pend_bits >> i) & 1u) {
-                if (!mbar_wait_bounded(&sh.mbar[i], (phase_bits >> i) & 1u)) sh.tmo = 1u;
-                phase_bits ^= 1u << i;
-                pend_bits &= ~(1u << i);
-            }
-        }
+        for (int k = L - 1; k >= posted; k--) wait(k);
         __syncthreads();
         if (timed_out || sh.tmo) {
-            if (threadIdx.x == 0) report(B.status, GP_ERR_TIMEOUT, 1u, gcol, L);
+            if (threadIdx.x == 0) report(B.status, GP_ERR_TIMEOUT, 1u, gcol, (uint32_t)L);
             break;
         }
     }
@@ -503,9 +591,42 @@ __global__ void __launch_bounds__(NT) stage1_kernel(Buffers B, uint32_t maxq) {
 
 }  // namespace
 
-size_t stage1_smem_bytes(uint32_t maxq) {
-    return (size_t)maxq * 16 + (size_t)kMaxEntries * 12 + (size_t)kStageRecs * 12 + (size_t)kSegCache * 16 +
-           (size_t)(kRowBuf + 2) * kRowBufs * 8 + (size_t)kActive * 2;
+size_t stage1_dynamic_smem_limit(int device) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
+    cudaFuncAttributes fa{};
+    size_t stat = 0;
+    for (uint32_t t : {128u, 256u, 512u, 1024u}) {
+        if (cudaFuncGetAttributes(&fa, stage1_kernel_ptr(t)) != cudaSuccess) return 0;
+        stat = std::max(stat, fa.sharedSizeBytes);
+    }
+    return (size_t)optin > stat ? (size_t)optin - stat : 0;
+}
+
+Stage1Shape stage1_shape(uint32_t maxq, uint32_t blocks_per_sm, size_t limit) {
+    Stage1Shape sh{};
+    const size_t base = smem_base_bytes(maxq);
+    // k blocks per SM share the SM's shared memory (1 KB of it reserved per block)
+    const size_t per_sm = limit + 1024;
+    const size_t budget = blocks_per_sm > 1 ? std::min(limit, per_sm / blocks_per_sm - 1024) : limit;
+    const uint32_t wi = window_index_bytes(maxq);
+    for (uint32_t nbuf = 3; nbuf >= 2; nbuf--) {
+        if (budget < base + (size_t)nbuf * (wi + 512 * 8)) continue;
+        size_t cap = (budget - base) / nbuf;
+        cap = (cap - wi) / 8;
+        cap = std::min<size_t>(cap, 4096) & ~(size_t)15;
+        sh.nbuf = nbuf;
+        sh.list_cap = (uint32_t)cap;
+        sh.wbytes = wi + (uint32_t)cap * 8;
+        sh.smem = base + (size_t)nbuf * sh.wbytes;
+        return sh;
+    }
+    // no room for window buffers: every window is read from global memory
+    sh.nbuf = 0;
+    sh.list_cap = 0;
+    sh.wbytes = 0;
+    sh.smem = base;
+    return sh;
 }
 
 const void *stage1_kernel_ptr(uint32_t threads) {
@@ -517,14 +638,18 @@ const void *stage1_kernel_ptr(uint32_t threads) {
     }
 }
 
-void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t maxq, cudaStream_t s,
-                   uint32_t *launches) {
-    const size_t smem = stage1_smem_bytes(maxq);
+void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t maxq, const Stage1Shape &sh,
+                   cudaStream_t s, uint32_t *launches) {
+    // records per warp chunk: the chunk tails the warps may leave unused fit
+    // the pool's slack (kPoolSlack records)
+    const uint64_t warps = (uint64_t)grid * (threads / 32u - 1u);
+    uint32_t wchunk = (uint32_t)std::min<uint64_t>(256, kPoolSlack / std::max<uint64_t>(warps, 1)) & ~31u;
+    if (wchunk < 32u) wchunk = 32u;
     switch (threads) {
-    case 128: stage1_kernel<128><<<grid, 128, smem, s>>>(b, maxq); break;
-    case 256: stage1_kernel<256><<<grid, 256, smem, s>>>(b, maxq); break;
-    case 1024: stage1_kernel<1024><<<grid, 1024, smem, s>>>(b, maxq); break;
-    default: stage1_kernel<512><<<grid, 512, smem, s>>>(b, maxq); break;
+    case 128: stage1_kernel<128><<<grid, 128, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+    case 256: stage1_kernel<256><<<grid, 256, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+    case 1024: stage1_kernel<1024><<<grid, 1024, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+    default: stage1_kernel<512><<<grid, 512, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
     }
     *launches += 1;
 }
