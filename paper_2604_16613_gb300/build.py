@@ -20,8 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libgpdem.so")
-SOURCES = ["lower.cu", "stage1.cu", "stage2.cu", "api.cu", "noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(INCLUDE, "gpdem.h")]
+SOURCES = ["lower.cu", "stage1.cu", "stage2.cu", "api.cu", "noalloc.cu", "serve.cu"]
+HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(INCLUDE, "gpdem.h"), os.path.join(INCLUDE, "gpserve.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

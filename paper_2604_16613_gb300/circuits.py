@@ -84,6 +84,12 @@ class Circuit:
         self.n_observables = 0
         self.n_ticks = 0
         self._frozen: tuple | None = None
+        # cycle boundaries for serving: (rows, recs, locations, measurements,
+        # detectors) counted at the end of every cycle but the last
+        self.cycle_marks: list[tuple] = []
+        # declared logical operators: per observable, the qubits whose Z
+        # measurement defines it at a cycle boundary
+        self.logicals: list[np.ndarray] = []
 
     # -- raw appends -------------------------------------------------------
     def _append(self, rows: np.ndarray) -> None:
@@ -189,6 +195,37 @@ class Circuit:
             rows[:, 2] = t[:, 1]
         rows[:, 3] = location
         self._append(rows)
+
+    def mark_cycle(self) -> None:
+        """End the current cycle here (the serving stream cuts the circuit
+        at these marks)."""
+        self.cycle_marks.append((self.n_ops, self._n_recs, self.n_locations, self.n_measurements,
+                                 self.n_detectors))
+
+    def cycle_blocks(self) -> list[dict]:
+        """The circuit cut at its cycle marks, each piece self-contained:
+        detector and observable rows index the piece's own record array and
+        noise rows its own locations (record lookbacks stay relative and may
+        reach into earlier pieces).  Concatenating the pieces, with those
+        offsets added back, gives the circuit."""
+        ops, recs, p = self._freeze()
+        ends = list(self.cycle_marks) + [(ops.shape[0], recs.size, self.n_locations, self.n_measurements,
+                                          self.n_detectors)]
+        out, start = [], (0, 0, 0, 0, 0)
+        for i, end in enumerate(ends):
+            r0, c0, l0, m0, d0 = start
+            r1, c1, l1, m1, d1 = end
+            o = ops[r0:r1].copy()
+            k = o[:, 0]
+            ann = (k == DETECTOR) | (k == OBSERVABLE_INCLUDE)
+            o[ann, 1] -= np.uint32(c0)
+            nz = np.isin(k, NOISE_KINDS)
+            o[nz, 3] -= np.uint32(l0)
+            out.append(dict(ops=o, recs=recs[c0:c1].copy(), noise=p[l0:l1].copy(), n_detectors=d1 - d0,
+                            n_measurements=m1 - m0, n_locations=l1 - l0, n_ticks=int((k == TICK).sum()),
+                            final=i == len(ends) - 1))
+            start = end
+        return out
 
     # -- views -------------------------------------------------------------
     def _freeze(self):
@@ -614,6 +651,8 @@ def rotated_surface_code_memory(d: int, rounds: int | None = None,
             c.detectors([[m, pm] for m, pm in zip(rec, prev)])
         prev = rec
         c.tick()
+        if r < rounds - 1:
+            c.mark_cycle()
     L = _Layer(c, noise, allq)
     drec = L.measure(lay.data)
     L.close(tick=False)
@@ -622,6 +661,7 @@ def rotated_surface_code_memory(d: int, rounds: int | None = None,
         groups.append([drec[q] for q in nb if q >= 0] + [prev[n_x + i]])
     c.detectors(groups)
     c.observable(0, [drec[q] for q in lay.z_logical])
+    c.logicals = [np.asarray(lay.z_logical, dtype=np.int64)]
     return c
 
 
@@ -882,12 +922,15 @@ def css_memory_circuit(hx, hz, zlog, rounds: int, noise: NoiseModel | None, seed
             c.detectors([[m_, pm] for m_, pm in zip(rec, prev)])
         prev = rec
         c.tick()
+        if r < rounds - 1:
+            c.mark_cycle()
     L = _Layer(c, noise, allq)
     drec = L.measure(data)
     L.close(tick=False)
     c.detectors([[drec[j] for j in np.flatnonzero(hz[i])] + [prev[nx + i]] for i in range(nz)])
     for k, lg in enumerate(zlog):
         c.observable(k, [drec[j] for j in np.flatnonzero(lg)])
+    c.logicals = [np.flatnonzero(lg).astype(np.int64) for lg in zlog]
     return c
 
 
@@ -1057,6 +1100,8 @@ def concatenated_adaptive_branch(d: int = 10, cycles: int = 20, seed: int = 0, f
             fired = set(np.flatnonzero(rng.random(lay.n_blocks) < fire_rate).tolist())
             active = [oc for oc, tb in zip(outer, touches) if tb & fired]
         run_checks(active)
+        if t < cycles - 1:
+            c.mark_cycle()
     L = _Layer(c, noise, allq)
     drec = L.measure(phys)
     L.close(tick=False)
@@ -1069,6 +1114,7 @@ def concatenated_adaptive_branch(d: int = 10, cycles: int = 20, seed: int = 0, f
             groups.append([drec[pos[q]] for q in sup] + [last[("o", i)]])
     c.detectors(groups)
     c.observable(0, [drec[pos[q]] for q in lay.z_logical])
+    c.logicals = [np.asarray(lay.z_logical, dtype=np.int64)]
     c.n_cycles = cycles
     return c
 

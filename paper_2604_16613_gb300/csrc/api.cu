@@ -192,6 +192,13 @@ struct gp_driver {
     uint32_t launches = 0;
 };
 
+namespace gpdem {
+const Buffers &driver_buffers(const gp_driver *d) { return d->B; }
+uint32_t driver_max_det_entries(const gp_driver *d) {
+    return (uint32_t)std::min<uint64_t>(d->L.max_det_entries, 0xFFFFFFFFull);
+}
+}  // namespace gpdem
+
 namespace {
 
 gp_status full_reset(gp_driver *d, cudaStream_t s) {

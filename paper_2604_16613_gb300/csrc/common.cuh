@@ -424,6 +424,11 @@ const void *stage1_kernel_ptr(uint32_t threads);
 void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
 void launch_init_table(TabSlot *t, size_t n, cudaStream_t s);
+// the device buffers of a driver (for the server's selection kernels)
+const Buffers &driver_buffers(const gp_driver *d);
+uint32_t driver_max_det_entries(const gp_driver *d);
+void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
+                 cudaStream_t s, uint32_t *launches);
 void launch_backward(const Buffers &b, const float *g_prob, const float *g_logodds, float *g_noise,
                      uint32_t n_mech, uint32_t n_loc, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches);
 }  // namespace gpdem

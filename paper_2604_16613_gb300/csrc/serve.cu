@@ -1,0 +1,846 @@
+// serve.cu -- cycle-streaming server (include/gpserve.h).
+//
+// Host side: per-patch state (declared logicals, per-cycle sizes, pending
+// requests), pinned staging of submitted cycles, the scheduler step.
+// Device side, per step:
+//   - the new cycles are copied into their patches' resident rings;
+//   - assemble: one launch copies every window's cycles from the rings into
+//     the batch arena, shifting record and location indices to the window,
+//     emptying the detectors of records-only cycles (and zeroing their noise
+//     in a final window) and appending the rows that close a window with the
+//     declared logicals;
+//   - the windows are compiled as one batch (gp_compile_batch);
+//   - seal: a flag per hyperedge (its smallest detector lies in a cycle the
+//     step seals), a horizon test per window (no mechanism of a records-only
+//     cycle c flips a detector after cycle c + H: those detectors all lie in
+//     the window, so a violation shows), a scan, and a compaction of the
+//     sealed hyperedges with patch-global detector ids, which are copied to
+//     the host and split per request.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "gpserve.h"
+
+using namespace gpdem;
+
+namespace gpdem {
+void set_last_error(const std::string &msg);
+}
+
+namespace {
+
+gp_status sfail(gp_status code, const std::string &msg) {
+    set_last_error(msg);
+    return code;
+}
+
+#define SV_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return sfail(GP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// one cycle of one window, or the rows closing a window
+struct SegDesc {
+    const uint4 *ops;
+    const uint32_t *recs;
+    const float *noise;
+    uint32_t n_ops, n_recs, n_loc;
+    uint32_t dst_ops, dst_recs, dst_loc;
+    uint32_t rec_shift, loc_shift;
+    uint32_t flags;             // kSegRecordsOnly | kSegZeroNoise
+    uint32_t pad;
+};
+constexpr uint32_t kSegRecordsOnly = 1u, kSegZeroNoise = 2u;
+
+// what a window seals
+struct SealDesc {
+    uint32_t det_lo, det_hi;    // window-local detector range of the sealed cycles
+    uint32_t take_no_det;       // final window: also hyperedges without detectors
+    uint32_t det_base;          // patch-global id of window-local detector 0
+    uint32_t n_mech_rec;        // mechanisms of the records-only cycles (0: no check)
+    uint32_t n_rec;             // records-only cycles
+    uint32_t pad[2];
+};
+// per records-only cycle j of a window: (end of its mechanisms, first
+// window-local detector it may not flip)
+
+constexpr int kSegBlocksY = 8;
+
+__global__ void __launch_bounds__(256) assemble_kernel(const SegDesc *seg, uint32_t n_seg, uint4 *ops,
+                                                       uint32_t *recs, float *noise) {
+    const uint32_t s = blockIdx.x;
+    if (s >= n_seg) return;
+    const SegDesc d = seg[s];
+    const uint32_t stride = gridDim.y * blockDim.x, t0 = blockIdx.y * blockDim.x + threadIdx.x;
+    for (uint32_t i = t0; i < d.n_ops; i += stride) {
+        uint4 op = d.ops[i];
+        const uint32_t k = op.x;
+        if (k == K_DET || k == K_OBS) {
+            op.y += d.rec_shift;
+            if ((d.flags & kSegRecordsOnly) && k == K_DET) op.z = 0u;
+        } else if (is_noise(k)) {
+            op.w += d.loc_shift;
+        }
+        ops[d.dst_ops + i] = op;
+    }
+    for (uint32_t i = t0; i < d.n_recs; i += stride) recs[d.dst_recs + i] = d.recs[i];
+    for (uint32_t i = t0; i < d.n_loc; i += stride)
+        noise[d.dst_loc + i] = (d.flags & kSegZeroNoise) ? 0.0f : d.noise[i];
+}
+
+// scan input per hyperedge: (sealed, detector count)
+__global__ void seal_flags_kernel(Buffers B, const SealDesc *seal) {
+    const uint32_t E = B.status->n_edges;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        const uint32_t w = B.edge_circ[e];
+        const uint32_t o0 = B.det_off[e], o1 = B.det_off[e + 1];
+        bool sealed;
+        if (o1 > o0) {
+            const uint32_t d0 = B.det_idx[o0];          // detector lists are ascending
+            sealed = d0 >= seal[w].det_lo && d0 < seal[w].det_hi;
+        } else {
+            sealed = seal[w].take_no_det != 0u;
+        }
+        B.scan_val[e] = sealed ? make_uint2(1u, o1 - o0) : make_uint2(0u, 0u);
+    }
+}
+
+// a mechanism of records-only cycle c flipping a detector after cycle c + H:
+// the window's horizon was too short
+__global__ void seal_horizon_kernel(Buffers B, const SealDesc *seal, const uint2 *rec_tab, uint32_t max_h,
+                                    uint32_t n_win, uint32_t *horizon) {
+    for (uint32_t w = blockIdx.x; w < n_win; w += gridDim.x) {
+        const uint32_t m0 = B.circ[w].mech_base, n = seal[w].n_mech_rec, nr = seal[w].n_rec;
+        const uint2 *tab = rec_tab + (size_t)w * max_h;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const int32_t cls = B.mech_class[m0 + i];
+            if (cls < 0) continue;
+            const uint32_t o0 = B.det_off[cls], o1 = B.det_off[cls + 1];
+            if (o1 == o0) continue;
+            uint32_t j = 0;
+            while (j + 1u < nr && tab[j].x <= i) j++;
+            if (B.det_idx[o1 - 1u] >= tab[j].y) horizon[w] = 1u;
+        }
+    }
+}
+
+struct SealOut {
+    uint32_t *win, *doff, *det, *totals;
+    float *prob, *logodds;
+    unsigned long long *obs;
+};
+
+__global__ void seal_write_kernel(Buffers B, const SealDesc *seal, SealOut out) {
+    const uint32_t E = B.status->n_edges;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out.totals[0] = B.comp_off[E].x;
+        out.totals[1] = B.comp_off[E].y;
+    }
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        if (B.scan_val[e].x == 0u) continue;
+        const uint2 off = B.comp_off[e];
+        const uint32_t w = B.edge_circ[e];
+        out.win[off.x] = w;
+        out.prob[off.x] = B.prob[e];
+        out.logodds[off.x] = B.logodds[e];
+        out.obs[off.x] = B.obs_mask[e];
+        out.doff[off.x] = off.y;
+        const uint32_t o0 = B.det_off[e], o1 = B.det_off[e + 1], base = seal[w].det_base;
+        for (uint32_t i = o0; i < o1; i++) out.det[off.y + (i - o0)] = B.det_idx[i] + base;
+    }
+}
+
+uint32_t n_comp_host(uint32_t kind, uint32_t level) {
+    switch (kind) {
+    case K_XERR: case K_ZERR: return 1;
+    case K_DEP1: return level == 0 ? 2u : 3u;
+    case K_DEP2: return level == 0 ? 6u : (level == 1 ? 10u : 15u);
+    default: return 0;
+    }
+}
+
+struct CycleInfo {
+    uint32_t n_ops, n_recs, n_loc, n_meas, n_det, n_ticks;
+    uint32_t mech[3];           // mechanisms at L0, L1, L2
+    uint64_t det_base, meas_base;
+};
+
+struct Request {
+    uint64_t id = 0;
+    uint32_t patch = 0, cycle = 0;
+    bool final = false, done = false;
+    uint32_t stage = 0;          // pinned staging slot of the submitted cycle
+    gp_status status = GP_OK;
+    uint64_t t_arrival = 0, t_done = 0;
+    std::vector<uint32_t> det_offsets{0}, det_idx;
+    std::vector<uint64_t> obs;
+    std::vector<float> prob, logodds;
+};
+
+struct Patch {
+    bool open = false;
+    uint32_t n_qubits = 0, H = 1, n_obs = 0;
+    std::vector<uint32_t> virt_q;        // distinct logical qubits, measured in this order
+    std::vector<uint32_t> virt_recs;     // per logical: lookbacks into those measurements
+    std::vector<uint32_t> virt_off;      // n_obs + 1
+    uint4 *ring_ops = nullptr;
+    uint32_t *ring_recs = nullptr;
+    float *ring_noise = nullptr;
+    std::vector<CycleInfo> cycles;       // every submitted cycle
+    uint32_t next_step = 0;              // first cycle not yet stepped
+    bool final_submitted = false;
+    std::deque<uint64_t> pending;        // submitted, not yet stepped (cycle order)
+};
+
+}  // namespace
+
+struct gp_server {
+    gp_server_config cfg{};
+    uint32_t W = 0;                      // ring slots per patch: 3 max_horizon + K
+    uint32_t n_sms = 1;
+    uint32_t extra_ops = 0, extra_recs = 0;
+    gp_driver *drv = nullptr;
+    // device memory
+    unsigned char *dmem = nullptr;
+    uint4 *arena_ops = nullptr;
+    uint32_t *arena_recs = nullptr;
+    float *arena_noise = nullptr;
+    SegDesc *d_seg = nullptr;
+    SealDesc *d_seal = nullptr;
+    uint2 *d_rec_tab = nullptr;
+    uint4 *d_extra_ops = nullptr;
+    uint32_t *d_extra_recs = nullptr;
+    uint32_t *d_horizon = nullptr;
+    SealOut out{};
+    uint64_t out_edges_cap = 0, out_det_cap = 0;
+    // pinned host memory
+    unsigned char *h_desc = nullptr;     // segs | seals | extra ops | extra recs
+    size_t h_desc_bytes = 0;
+    uint4 *h_stage_ops = nullptr;
+    uint32_t *h_stage_recs = nullptr;
+    float *h_stage_noise = nullptr;
+    std::vector<uint32_t> free_stage;
+    uint32_t *h_horizon = nullptr;
+    uint32_t *h_totals = nullptr;
+    uint32_t *h_win = nullptr, *h_doff = nullptr, *h_det = nullptr;
+    float *h_prob = nullptr, *h_logodds = nullptr;
+    unsigned long long *h_obs = nullptr;
+    uint64_t h_edges_cap = 0, h_det_cap = 0;
+    // state
+    std::vector<Patch> patches;
+    std::unordered_map<uint64_t, Request> requests;
+    std::vector<uint64_t> completed;
+    uint64_t next_request = 1;
+    uint32_t n_pending = 0;
+};
+
+namespace {
+
+template <class T> T *carve_dev(unsigned char *base, uint64_t &off, uint64_t count) {
+    off = (off + 255) & ~255ull;
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+}
+
+void free_host(gp_server *s) {
+    void *ptrs[] = {s->h_desc, s->h_stage_ops, s->h_stage_recs, s->h_stage_noise, s->h_horizon, s->h_totals,
+                    s->h_win, s->h_doff, s->h_det, s->h_prob, s->h_logodds, s->h_obs};
+    for (void *p : ptrs)
+        if (p) cudaFreeHost(p);
+}
+
+gp_status grow_host_out(gp_server *s, uint64_t edges, uint64_t dets) {
+    if (edges <= s->h_edges_cap && dets <= s->h_det_cap) return GP_OK;
+    const uint64_t ne = std::max<uint64_t>(edges, s->h_edges_cap), nd = std::max<uint64_t>(dets, s->h_det_cap);
+    void *ptrs[] = {s->h_win, s->h_doff, s->h_det, s->h_prob, s->h_logodds, s->h_obs};
+    for (void *p : ptrs)
+        if (p) cudaFreeHost(p);
+    s->h_win = s->h_doff = s->h_det = nullptr;
+    s->h_prob = s->h_logodds = nullptr;
+    s->h_obs = nullptr;
+    s->h_edges_cap = s->h_det_cap = 0;
+    if (cudaMallocHost(&s->h_win, 4 * ne) != cudaSuccess || cudaMallocHost(&s->h_doff, 4 * (ne + 1)) != cudaSuccess ||
+        cudaMallocHost(&s->h_det, 4 * std::max<uint64_t>(nd, 1)) != cudaSuccess ||
+        cudaMallocHost(&s->h_prob, 4 * ne) != cudaSuccess || cudaMallocHost(&s->h_logodds, 4 * ne) != cudaSuccess ||
+        cudaMallocHost(&s->h_obs, 8 * ne) != cudaSuccess)
+        return sfail(GP_ERR_CUDA, "cudaMallocHost of the result staging failed");
+    s->h_edges_cap = ne;
+    s->h_det_cap = nd;
+    return GP_OK;
+}
+
+void finish(gp_server *s, Request &r, gp_status st, uint64_t t) {
+    r.status = st;
+    r.done = true;
+    r.t_done = t;
+    if (st != GP_OK) {
+        r.det_offsets.assign(1, 0);
+        r.det_idx.clear();
+        r.obs.clear();
+        r.prob.clear();
+        r.logodds.clear();
+    }
+    s->completed.push_back(r.id);
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
+    if (!config || !out) return sfail(GP_ERR_INVALID, "null argument");
+    *out = nullptr;
+    const gp_server_config &c = *config;
+    if (!c.max_patches || !c.max_batch || !c.max_cycles_per_step || !c.max_horizon || !c.max_pending ||
+        !c.max_qubits || !c.max_cycle_ops || !c.max_cycle_layers)
+        return sfail(GP_ERR_INVALID, "server config: every count must be positive (recs, locations, measurements, "
+                                     "detectors, mechanisms and logical qubits may be zero)");
+    if (c.max_qubits > 8192) return sfail(GP_ERR_INVALID, "server config: max_qubits above 8192");
+    if (c.max_batch > c.max_patches) return sfail(GP_ERR_INVALID, "server config: max_batch above max_patches");
+    gp_server *s = new (std::nothrow) gp_server();
+    if (!s) return sfail(GP_ERR_CAPACITY, "out of host memory");
+    auto cleanup = [&](gp_status st) { gp_server_destroy(s); return st; };
+    s->cfg = c;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return cleanup(sfail(GP_ERR_CUDA, "querying the device failed"));
+        s->n_sms = (uint32_t)std::max(sms, 1);
+    }
+    s->W = 3u * c.max_horizon + c.max_cycles_per_step;
+    s->extra_ops = 1u + c.max_logical_qubits + 64u;
+    s->extra_recs = c.max_logical_qubits;
+    const uint64_t W = s->W, Bt = c.max_batch;
+    gp_bounds b{};
+    b.max_circuits = c.max_batch;
+    b.max_qubits = c.max_qubits;
+    const uint64_t ops = Bt * (W * c.max_cycle_ops + s->extra_ops);
+    const uint64_t recs = Bt * (W * c.max_cycle_recs + s->extra_recs);
+    const uint64_t layers = Bt * (W * c.max_cycle_layers + 2);
+    const uint64_t meas = Bt * (W * c.max_cycle_measurements + c.max_logical_qubits);
+    const uint64_t dets = Bt * W * c.max_cycle_detectors;
+    const uint64_t locs = Bt * W * c.max_cycle_locations;
+    const uint64_t mech = Bt * W * std::max<uint32_t>(c.max_cycle_mechanisms, 1);
+    if (ops > 0xFFFFFFFFull || recs > 0xFFFFFFFFull || layers > 0xFFFFFFFFull || meas > (1ull << 28) ||
+        dets > 0xFFFFFFFFull || locs > 0xFFFFFFFFull || mech > 0x7FFFFFFFull)
+        return cleanup(sfail(GP_ERR_CAPACITY, "server config: a batch of windows exceeds the compiler's 32-bit sizes"));
+    b.max_ops = ops;
+    b.max_recs = std::max<uint64_t>(recs, 1);
+    b.max_layers = (uint32_t)layers;
+    b.max_measurements = (uint32_t)std::max<uint64_t>(meas, 1);
+    b.max_detectors = (uint32_t)std::max<uint64_t>(dets, 1);
+    b.max_locations = (uint32_t)std::max<uint64_t>(locs, 1);
+    b.max_mechanisms = (uint32_t)mech;
+    // device memory: driver workspace + rings + arena + descriptors + outputs
+    uint64_t ws = 0;
+    {
+        const gp_status st = gp_workspace_size(&b, &ws);
+        if (st != GP_OK) return cleanup(st);
+    }
+    const uint64_t max_det_entries = 16ull * b.max_mechanisms;
+    s->out_edges_cap = b.max_mechanisms;
+    s->out_det_cap = std::min<uint64_t>(max_det_entries, 0xFFFFFFFFull);
+    const uint64_t nseg = Bt * (W + 1);
+    auto layout = [&](unsigned char *base) {
+        uint64_t off = 0;
+        for (uint32_t p = 0; p < c.max_patches; p++) {
+            uint4 *o = carve_dev<uint4>(base, off, W * c.max_cycle_ops);
+            uint32_t *r = carve_dev<uint32_t>(base, off, std::max<uint64_t>(W * c.max_cycle_recs, 1));
+            float *n = carve_dev<float>(base, off, std::max<uint64_t>(W * c.max_cycle_locations, 1));
+            if (base) {
+                s->patches[p].ring_ops = o;
+                s->patches[p].ring_recs = r;
+                s->patches[p].ring_noise = n;
+            }
+        }
+        s->arena_ops = carve_dev<uint4>(base, off, ops);
+        s->arena_recs = carve_dev<uint32_t>(base, off, std::max<uint64_t>(recs, 1));
+        s->arena_noise = carve_dev<float>(base, off, std::max<uint64_t>(locs, 1));
+        s->d_seg = carve_dev<SegDesc>(base, off, nseg);
+        s->d_seal = carve_dev<SealDesc>(base, off, Bt);
+        s->d_rec_tab = carve_dev<uint2>(base, off, Bt * c.max_horizon);
+        s->d_extra_ops = carve_dev<uint4>(base, off, Bt * s->extra_ops);
+        s->d_extra_recs = carve_dev<uint32_t>(base, off, std::max<uint64_t>(Bt * s->extra_recs, 1));
+        s->d_horizon = carve_dev<uint32_t>(base, off, Bt);
+        s->out.win = carve_dev<uint32_t>(base, off, s->out_edges_cap);
+        s->out.doff = carve_dev<uint32_t>(base, off, s->out_edges_cap + 1);
+        s->out.det = carve_dev<uint32_t>(base, off, std::max<uint64_t>(s->out_det_cap, 1));
+        s->out.totals = carve_dev<uint32_t>(base, off, 2);
+        s->out.prob = carve_dev<float>(base, off, s->out_edges_cap);
+        s->out.logodds = carve_dev<float>(base, off, s->out_edges_cap);
+        s->out.obs = carve_dev<unsigned long long>(base, off, s->out_edges_cap);
+        return off;
+    };
+    s->patches.resize(c.max_patches);
+    const uint64_t own = layout(nullptr);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return cleanup(sfail(GP_ERR_CUDA, "cudaMemGetInfo failed"));
+    const uint64_t margin = 256ull << 20;
+    if (ws + own + margin > free_b)
+        return cleanup(sfail(GP_ERR_CAPACITY, "server needs " + std::to_string((ws + own) >> 20) +
+                                                  " MiB of device memory, " + std::to_string(free_b >> 20) + " MiB free"));
+    if (cudaMalloc(&s->dmem, own) != cudaSuccess) return cleanup(sfail(GP_ERR_CUDA, "cudaMalloc of the server arena failed"));
+    layout(s->dmem);
+    {
+        const gp_status st = gp_driver_create(&b, nullptr, 0, &s->drv);
+        if (st != GP_OK) return cleanup(st);
+    }
+    // pinned staging
+    s->h_desc_bytes = nseg * sizeof(SegDesc) + Bt * sizeof(SealDesc) + Bt * s->extra_ops * sizeof(uint4) +
+                      Bt * s->extra_recs * sizeof(uint32_t) + Bt * c.max_horizon * sizeof(uint2);
+    if (cudaMallocHost(&s->h_desc, s->h_desc_bytes) != cudaSuccess ||
+        cudaMallocHost(&s->h_stage_ops, sizeof(uint4) * (uint64_t)c.max_pending * c.max_cycle_ops) != cudaSuccess ||
+        cudaMallocHost(&s->h_stage_recs, sizeof(uint32_t) * std::max<uint64_t>((uint64_t)c.max_pending * c.max_cycle_recs, 1)) != cudaSuccess ||
+        cudaMallocHost(&s->h_stage_noise, sizeof(float) * std::max<uint64_t>((uint64_t)c.max_pending * c.max_cycle_locations, 1)) != cudaSuccess ||
+        cudaMallocHost(&s->h_horizon, sizeof(uint32_t) * Bt) != cudaSuccess ||
+        cudaMallocHost(&s->h_totals, sizeof(uint32_t) * 2) != cudaSuccess)
+        return cleanup(sfail(GP_ERR_CUDA, "cudaMallocHost of the server staging failed"));
+    for (uint32_t i = 0; i < c.max_pending; i++) s->free_stage.push_back(c.max_pending - 1 - i);
+    {
+        const gp_status st = grow_host_out(s, 1u << 16, 1u << 20);
+        if (st != GP_OK) return cleanup(st);
+    }
+    *out = s;
+    return GP_OK;
+}
+
+void gp_server_destroy(gp_server *s) {
+    if (!s) return;
+    if (s->drv) gp_driver_destroy(s->drv);
+    if (s->dmem) cudaFree(s->dmem);
+    free_host(s);
+    delete s;
+}
+
+gp_status gp_server_open_patch(gp_server *s, const gp_patch_spec *spec, uint32_t *patch) {
+    if (!s || !spec || !patch) return sfail(GP_ERR_INVALID, "null argument");
+    const gp_server_config &c = s->cfg;
+    if (spec->n_qubits == 0 || spec->n_qubits > c.max_qubits) return sfail(GP_ERR_INVALID, "patch: n_qubits outside 1..max_qubits");
+    if (spec->horizon == 0 || spec->horizon > c.max_horizon) return sfail(GP_ERR_INVALID, "patch: horizon outside 1..max_horizon");
+    if (spec->n_observables > 64) return sfail(GP_ERR_INVALID, "patch: at most 64 logicals");
+    if (spec->n_observables && (!spec->logical_qubits || !spec->logical_offsets))
+        return sfail(GP_ERR_INVALID, "patch: null logical arrays");
+    uint32_t slot = kNone;
+    for (uint32_t p = 0; p < c.max_patches; p++)
+        if (!s->patches[p].open) { slot = p; break; }
+    if (slot == kNone) return sfail(GP_ERR_CAPACITY, "all max_patches patches are open");
+    Patch np;
+    np.ring_ops = s->patches[slot].ring_ops;
+    np.ring_recs = s->patches[slot].ring_recs;
+    np.ring_noise = s->patches[slot].ring_noise;
+    np.open = true;
+    np.n_qubits = spec->n_qubits;
+    np.H = spec->horizon;
+    np.n_obs = spec->n_observables;
+    const uint32_t total = spec->n_observables ? spec->logical_offsets[spec->n_observables] : 0u;
+    if (total > c.max_logical_qubits) return sfail(GP_ERR_INVALID, "patch: logicals larger than max_logical_qubits");
+    std::vector<uint32_t> qs;
+    for (uint32_t k = 0; k < spec->n_observables; k++) {
+        if (spec->logical_offsets[k] > spec->logical_offsets[k + 1]) return sfail(GP_ERR_INVALID, "patch: logical offsets decrease");
+        for (uint32_t i = spec->logical_offsets[k]; i < spec->logical_offsets[k + 1]; i++) {
+            if (spec->logical_qubits[i] >= spec->n_qubits) return sfail(GP_ERR_INVALID, "patch: logical qubit out of range");
+            qs.push_back(spec->logical_qubits[i]);
+        }
+    }
+    std::sort(qs.begin(), qs.end());
+    qs.erase(std::unique(qs.begin(), qs.end()), qs.end());
+    np.virt_q = qs;
+    np.virt_off.push_back(0);
+    for (uint32_t k = 0; k < spec->n_observables; k++) {
+        for (uint32_t i = spec->logical_offsets[k]; i < spec->logical_offsets[k + 1]; i++) {
+            const uint32_t idx = (uint32_t)(std::lower_bound(qs.begin(), qs.end(), spec->logical_qubits[i]) - qs.begin());
+            np.virt_recs.push_back((uint32_t)qs.size() - idx);
+        }
+        np.virt_off.push_back((uint32_t)np.virt_recs.size());
+    }
+    s->patches[slot] = std::move(np);
+    *patch = slot;
+    return GP_OK;
+}
+
+gp_status gp_server_close_patch(gp_server *s, uint32_t patch) {
+    if (!s || patch >= s->cfg.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
+    Patch &p = s->patches[patch];
+    if (!p.pending.empty()) return sfail(GP_ERR_INVALID, "patch has pending cycles");
+    Patch empty;
+    empty.ring_ops = p.ring_ops;
+    empty.ring_recs = p.ring_recs;
+    empty.ring_noise = p.ring_noise;
+    p = std::move(empty);
+    return GP_OK;
+}
+
+gp_status gp_server_submit(gp_server *s, uint32_t patch, const gp_circuit *cyc, const float *noise, int final,
+                           uint64_t t_arrival_ns, uint64_t *request) {
+    if (!s || !cyc || !request) return sfail(GP_ERR_INVALID, "null argument");
+    const gp_server_config &c = s->cfg;
+    if (patch >= c.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
+    Patch &p = s->patches[patch];
+    if (p.final_submitted) return sfail(GP_ERR_INVALID, "patch already ended with a final cycle");
+    if (cyc->n_ops > c.max_cycle_ops || cyc->n_recs > c.max_cycle_recs || cyc->n_locations > c.max_cycle_locations ||
+        cyc->n_detectors > c.max_cycle_detectors)
+        return sfail(GP_ERR_CAPACITY, "cycle larger than the server's per-cycle bounds");
+    if (cyc->n_qubits > p.n_qubits) return sfail(GP_ERR_INVALID, "cycle uses more qubits than its patch");
+    if (cyc->n_observables != p.n_obs) return sfail(GP_ERR_INVALID, "cycle's n_observables differs from its patch's logicals");
+    if ((cyc->n_ops && !cyc->ops) || (cyc->n_recs && !cyc->recs) || (cyc->n_locations && !noise))
+        return sfail(GP_ERR_INVALID, "null cycle arrays");
+    if (s->free_stage.empty()) return sfail(GP_ERR_CAPACITY, "max_pending cycles are queued");
+    // sizes, mechanism counts and the record-horizon check
+    const uint4 *ops = reinterpret_cast<const uint4 *>(cyc->ops);
+    const uint32_t t = (uint32_t)p.cycles.size();
+    CycleInfo ci{};
+    ci.n_ops = (uint32_t)cyc->n_ops;
+    ci.n_recs = (uint32_t)cyc->n_recs;
+    ci.n_loc = cyc->n_locations;
+    ci.det_base = t ? p.cycles[t - 1].det_base + p.cycles[t - 1].n_det : 0;
+    ci.meas_base = t ? p.cycles[t - 1].meas_base + p.cycles[t - 1].n_meas : 0;
+    const uint64_t horizon_meas = t >= p.H ? p.cycles[t - p.H].meas_base : 0;
+    uint64_t meas = ci.meas_base;
+    uint32_t n_det = 0;
+    for (uint64_t i = 0; i < cyc->n_ops; i++) {
+        const uint4 op = ops[i];
+        const uint32_t k = op.x;
+        if (k == K_TICK) ci.n_ticks++;
+        else if (is_measure(k)) meas++;
+        else if (is_noise(k)) {
+            for (uint32_t l = 0; l < 3; l++) ci.mech[l] += n_comp_host(k, l);
+            if (op.w >= cyc->n_locations) return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(i) + ": location out of range");
+        } else if (k == K_DET || k == K_OBS) {
+            if (k == K_OBS && !final) return sfail(GP_ERR_INVALID, "observables are declared per patch; only a final cycle may define them");
+            if (k == K_DET) n_det++;
+            if ((uint64_t)op.y + op.z > cyc->n_recs) return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(i) + ": records out of range");
+            for (uint32_t j = 0; j < op.z; j++) {
+                const uint32_t lb = cyc->recs[op.y + j];
+                if (lb == 0 || lb > meas) return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(i) + ": record lookback refers to no earlier measurement");
+                if (meas - lb < horizon_meas)
+                    return sfail(GP_ERR_HORIZON, "cycle row " + std::to_string(i) + ": record lookback reaches more than H cycles back");
+            }
+        }
+    }
+    ci.n_meas = (uint32_t)(meas - ci.meas_base);
+    ci.n_det = n_det;
+    if (n_det != cyc->n_detectors) return sfail(GP_ERR_INVALID, "cycle's n_detectors differs from its DETECTOR rows");
+    if (ci.n_meas > c.max_cycle_measurements || ci.n_ticks + 1 > c.max_cycle_layers || ci.mech[2] > c.max_cycle_mechanisms)
+        return sfail(GP_ERR_CAPACITY, "cycle larger than the server's per-cycle bounds");
+    // stage the cycle (pinned) until its step uploads it
+    const uint32_t slot = s->free_stage.back();
+    s->free_stage.pop_back();
+    if (cyc->n_ops) memcpy(s->h_stage_ops + (uint64_t)slot * c.max_cycle_ops, cyc->ops, cyc->n_ops * sizeof(uint4));
+    if (cyc->n_recs) memcpy(s->h_stage_recs + (uint64_t)slot * c.max_cycle_recs, cyc->recs, cyc->n_recs * sizeof(uint32_t));
+    if (cyc->n_locations) memcpy(s->h_stage_noise + (uint64_t)slot * c.max_cycle_locations, noise, cyc->n_locations * sizeof(float));
+    p.cycles.push_back(ci);
+    if (final) p.final_submitted = true;
+    Request r;
+    r.id = s->next_request++;
+    *request = r.id;
+    r.patch = patch;
+    r.cycle = t;
+    r.final = final != 0;
+    r.stage = slot;
+    r.t_arrival = t_arrival_ns ? t_arrival_ns : now_ns();
+    p.pending.push_back(r.id);
+    s->requests.emplace(r.id, std::move(r));
+    s->n_pending++;
+    return GP_OK;
+}
+
+gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n_completed) {
+    if (!s) return sfail(GP_ERR_INVALID, "null argument");
+    if ((int)level < 0 || (int)level > 2) return sfail(GP_ERR_INVALID, "level must be GP_L0, GP_L1 or GP_L2");
+    if (n_completed) *n_completed = 0;
+    const gp_server_config &c = s->cfg;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // patches with pending cycles, oldest request first
+    std::vector<std::pair<uint64_t, uint32_t>> order;
+    for (uint32_t p = 0; p < c.max_patches; p++) {
+        const Patch &P = s->patches[p];
+        if (P.open && !P.pending.empty()) order.push_back({s->requests.at(P.pending.front()).t_arrival, p});
+    }
+    if (order.empty()) return GP_OK;
+    std::sort(order.begin(), order.end());
+    if (order.size() > c.max_batch) order.resize(c.max_batch);
+
+    struct Win {
+        uint32_t patch, t_a, t_b, c0, n_rec;
+        bool final;
+        std::vector<uint64_t> reqs;
+        std::vector<uint64_t> det_off;   // window-local detector offset per cycle c0..t_b+1
+    };
+    std::vector<Win> wins;
+    SegDesc *hseg = reinterpret_cast<SegDesc *>(s->h_desc);
+    const uint64_t nseg_cap = (uint64_t)c.max_batch * (s->W + 1);
+    SealDesc *hseal = reinterpret_cast<SealDesc *>(hseg + nseg_cap);
+    uint4 *hxops = reinterpret_cast<uint4 *>(hseal + c.max_batch);
+    uint32_t *hxrecs = reinterpret_cast<uint32_t *>(hxops + (uint64_t)c.max_batch * s->extra_ops);
+    uint2 *hrtab = reinterpret_cast<uint2 *>(hxrecs + (uint64_t)c.max_batch * s->extra_recs);
+    std::vector<gp_circuit> circ;
+    uint32_t nseg = 0;
+    uint64_t a_ops = 0, a_recs = 0, a_loc = 0, x_ops = 0, x_recs = 0;
+    for (const auto &pr : order) {
+        const uint32_t pi = pr.second;
+        Patch &P = s->patches[pi];
+        Win w;
+        w.patch = pi;
+        w.t_a = P.next_step;
+        w.t_b = w.t_a;
+        w.final = false;
+        for (uint64_t id : P.pending) {
+            const Request &r = s->requests.at(id);
+            if (r.cycle != w.t_a + (uint32_t)w.reqs.size() || w.reqs.size() >= c.max_cycles_per_step) break;
+            w.reqs.push_back(id);
+            w.t_b = r.cycle;
+            if (r.final) { w.final = true; break; }
+        }
+        w.c0 = w.t_a > 3u * P.H ? w.t_a - 3u * P.H : 0u;
+        w.n_rec = w.c0 > 0 ? P.H : 0u;
+        // upload the new cycles into their ring slots
+        for (uint64_t id : w.reqs) {
+            const Request &r = s->requests.at(id);
+            const CycleInfo &ci = P.cycles[r.cycle];
+            const uint32_t slot = r.cycle % s->W;
+            if (ci.n_ops)
+                SV_CUDA(cudaMemcpyAsync(P.ring_ops + (uint64_t)slot * c.max_cycle_ops, s->h_stage_ops + (uint64_t)r.stage * c.max_cycle_ops,
+                                        ci.n_ops * sizeof(uint4), cudaMemcpyHostToDevice, st));
+            if (ci.n_recs)
+                SV_CUDA(cudaMemcpyAsync(P.ring_recs + (uint64_t)slot * c.max_cycle_recs, s->h_stage_recs + (uint64_t)r.stage * c.max_cycle_recs,
+                                        ci.n_recs * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+            if (ci.n_loc)
+                SV_CUDA(cudaMemcpyAsync(P.ring_noise + (uint64_t)slot * c.max_cycle_locations,
+                                        s->h_stage_noise + (uint64_t)r.stage * c.max_cycle_locations, ci.n_loc * sizeof(float),
+                                        cudaMemcpyHostToDevice, st));
+        }
+        // segments of the window
+        gp_circuit g{};
+        const uint64_t ops0 = a_ops, recs0 = a_recs, loc0 = a_loc;
+        uint32_t n_det = 0, mech_rec = 0;
+        w.det_off.push_back(0);
+        for (uint32_t k = w.c0; k <= w.t_b; k++) {
+            const CycleInfo &ci = P.cycles[k];
+            const uint32_t slot = k % s->W;
+            SegDesc &d = hseg[nseg++];
+            d.ops = P.ring_ops + (uint64_t)slot * c.max_cycle_ops;
+            d.recs = P.ring_recs + (uint64_t)slot * c.max_cycle_recs;
+            d.noise = P.ring_noise + (uint64_t)slot * c.max_cycle_locations;
+            d.n_ops = ci.n_ops;
+            d.n_recs = ci.n_recs;
+            d.n_loc = ci.n_loc;
+            d.dst_ops = (uint32_t)a_ops;
+            d.dst_recs = (uint32_t)a_recs;
+            d.dst_loc = (uint32_t)a_loc;
+            d.rec_shift = (uint32_t)(a_recs - recs0);
+            d.loc_shift = (uint32_t)(a_loc - loc0);
+            const bool rec_only = k < w.c0 + w.n_rec;
+            d.flags = (rec_only ? kSegRecordsOnly : 0u) | (rec_only && w.final ? kSegZeroNoise : 0u);
+            d.pad = 0;
+            if (rec_only) mech_rec += ci.mech[(int)level];
+            a_ops += ci.n_ops;
+            a_recs += ci.n_recs;
+            a_loc += ci.n_loc;
+            n_det += ci.n_det;
+            w.det_off.push_back(n_det);
+        }
+        if (!w.final) {
+            // the rows closing the window: TICK, Z measurements of the logical
+            // qubits, one observable per logical
+            const uint64_t xo0 = x_ops, xr0 = x_recs;
+            hxops[x_ops++] = make_uint4(K_TICK, 0, 0, 0);
+            for (uint32_t q : P.virt_q) hxops[x_ops++] = make_uint4(K_M, q, 0, 0);
+            const uint32_t rbase = (uint32_t)(a_recs - recs0);
+            for (uint32_t k = 0; k < P.n_obs; k++)
+                hxops[x_ops++] = make_uint4(K_OBS, rbase + P.virt_off[k], P.virt_off[k + 1] - P.virt_off[k], k);
+            for (uint32_t v : P.virt_recs) hxrecs[x_recs++] = v;
+            SegDesc &d = hseg[nseg++];
+            d.ops = s->d_extra_ops + xo0;
+            d.recs = s->d_extra_recs + xr0;
+            d.noise = nullptr;
+            d.n_ops = (uint32_t)(x_ops - xo0);
+            d.n_recs = (uint32_t)(x_recs - xr0);
+            d.n_loc = 0;
+            d.dst_ops = (uint32_t)a_ops;
+            d.dst_recs = (uint32_t)a_recs;
+            d.dst_loc = (uint32_t)a_loc;
+            d.rec_shift = 0;
+            d.loc_shift = 0;
+            d.flags = 0;
+            d.pad = 0;
+            a_ops += d.n_ops;
+            a_recs += d.n_recs;
+        }
+        g.ops = reinterpret_cast<const uint32_t *>(s->arena_ops + ops0);
+        g.n_ops = a_ops - ops0;
+        g.recs = s->arena_recs + recs0;
+        g.n_recs = a_recs - recs0;
+        g.n_qubits = P.n_qubits;
+        g.n_detectors = n_det;
+        g.n_observables = P.n_obs;
+        g.n_locations = (uint32_t)(a_loc - loc0);
+        circ.push_back(g);
+        // sealed cycles [lo, hi)
+        SealDesc &sd = hseal[wins.size()];
+        const uint32_t lo = w.t_a > P.H ? w.t_a - P.H : 0u;
+        const uint32_t hi = w.final ? w.t_b + 1u : (w.t_b + 1u > P.H ? w.t_b + 1u - P.H : 0u);
+        if (hi > lo) {
+            sd.det_lo = (uint32_t)w.det_off[std::max(lo, w.c0) - w.c0];
+            sd.det_hi = (uint32_t)w.det_off[hi - w.c0];
+        } else {
+            sd.det_lo = sd.det_hi = 0;
+        }
+        sd.take_no_det = w.final ? 1u : 0u;
+        sd.det_base = (uint32_t)P.cycles[w.c0].det_base;
+        // the final window's records-only noise is zero: nothing to check
+        sd.n_mech_rec = w.final ? 0u : mech_rec;
+        sd.n_rec = w.n_rec;
+        sd.pad[0] = sd.pad[1] = 0;
+        {
+            uint32_t mend = 0;
+            for (uint32_t j = 0; j < w.n_rec; j++) {
+                mend += P.cycles[w.c0 + j].mech[(int)level];
+                hrtab[wins.size() * c.max_horizon + j] = make_uint2(mend, (uint32_t)w.det_off[j + P.H + 1]);
+            }
+        }
+        wins.push_back(std::move(w));
+    }
+    const uint32_t n_win = (uint32_t)wins.size();
+    // descriptors and closing rows: one copy each
+    SV_CUDA(cudaMemcpyAsync(s->d_seg, hseg, nseg * sizeof(SegDesc), cudaMemcpyHostToDevice, st));
+    SV_CUDA(cudaMemcpyAsync(s->d_seal, hseal, n_win * sizeof(SealDesc), cudaMemcpyHostToDevice, st));
+    SV_CUDA(cudaMemcpyAsync(s->d_rec_tab, hrtab, (size_t)n_win * c.max_horizon * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    if (x_ops) SV_CUDA(cudaMemcpyAsync(s->d_extra_ops, hxops, x_ops * sizeof(uint4), cudaMemcpyHostToDevice, st));
+    if (x_recs) SV_CUDA(cudaMemcpyAsync(s->d_extra_recs, hxrecs, x_recs * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    SV_CUDA(cudaMemsetAsync(s->d_horizon, 0, n_win * sizeof(uint32_t), st));
+    assemble_kernel<<<dim3(nseg, kSegBlocksY), 256, 0, st>>>(s->d_seg, nseg, s->arena_ops, s->arena_recs, s->arena_noise);
+    SV_CUDA(cudaGetLastError());
+    gp_dem_view view{};
+    gp_status cst = gp_compile_batch(s->drv, circ.data(), n_win, s->arena_noise, 1, level, stream, &view);
+    std::vector<uint32_t> win_status(n_win, GP_OK);
+    uint32_t n_sealed = 0, n_sdet = 0;
+    if (cst == GP_OK && view.n_edges) {
+        const Buffers &B = driver_buffers(s->drv);
+        const uint32_t grid = 4u * s->n_sms;
+        seal_flags_kernel<<<grid, 256, 0, st>>>(B, s->d_seal);
+        seal_horizon_kernel<<<n_win, 256, 0, st>>>(B, s->d_seal, s->d_rec_tab, c.max_horizon, n_win, s->d_horizon);
+        uint32_t launches = 0;
+        launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, st, &launches);
+        seal_write_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->out);
+        SV_CUDA(cudaGetLastError());
+        SV_CUDA(cudaMemcpyAsync(s->h_totals, s->out.totals, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        SV_CUDA(cudaMemcpyAsync(s->h_horizon, s->d_horizon, n_win * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        SV_CUDA(cudaStreamSynchronize(st));
+        n_sealed = s->h_totals[0];
+        n_sdet = s->h_totals[1];
+        {
+            const gp_status gs = grow_host_out(s, n_sealed + 1, n_sdet + 1);
+            if (gs != GP_OK) cst = gs;
+        }
+        if (cst == GP_OK && n_sealed) {
+            SV_CUDA(cudaMemcpyAsync(s->h_win, s->out.win, n_sealed * 4ull, cudaMemcpyDeviceToHost, st));
+            SV_CUDA(cudaMemcpyAsync(s->h_doff, s->out.doff, n_sealed * 4ull, cudaMemcpyDeviceToHost, st));
+            if (n_sdet) SV_CUDA(cudaMemcpyAsync(s->h_det, s->out.det, n_sdet * 4ull, cudaMemcpyDeviceToHost, st));
+            SV_CUDA(cudaMemcpyAsync(s->h_prob, s->out.prob, n_sealed * 4ull, cudaMemcpyDeviceToHost, st));
+            SV_CUDA(cudaMemcpyAsync(s->h_logodds, s->out.logodds, n_sealed * 4ull, cudaMemcpyDeviceToHost, st));
+            SV_CUDA(cudaMemcpyAsync(s->h_obs, s->out.obs, n_sealed * 8ull, cudaMemcpyDeviceToHost, st));
+            SV_CUDA(cudaStreamSynchronize(st));
+        }
+        for (uint32_t w = 0; w < n_win; w++)
+            if (s->h_horizon[w]) win_status[w] = GP_ERR_HORIZON;
+    }
+    // hand the sealed hyperedges to their requests
+    if (cst == GP_OK) {
+        for (uint32_t i = 0; i < n_sealed; i++) {
+            const uint32_t w = s->h_win[i];
+            if (w >= n_win || win_status[w] != GP_OK) continue;
+            const Win &W_ = wins[w];
+            const Patch &P = s->patches[W_.patch];
+            const uint32_t d0 = s->h_doff[i], d1 = (i + 1 < n_sealed) ? s->h_doff[i + 1] : n_sdet;
+            uint32_t owner;
+            if (d1 > d0) {
+                const uint64_t local = s->h_det[d0] - P.cycles[W_.c0].det_base;
+                const uint32_t k = W_.c0 + (uint32_t)(std::upper_bound(W_.det_off.begin(), W_.det_off.end(), local) -
+                                                      W_.det_off.begin()) - 1u;
+                owner = std::min(k + P.H, W_.t_b);
+            } else {
+                owner = W_.t_b;
+            }
+            if (owner < W_.t_a) continue;       // sealed by an earlier step (not selected)
+            Request &r = s->requests.at(W_.reqs[owner - W_.t_a]);
+            r.det_idx.insert(r.det_idx.end(), s->h_det + d0, s->h_det + d1);
+            r.det_offsets.push_back((uint32_t)r.det_idx.size());
+            r.obs.push_back(s->h_obs[i]);
+            r.prob.push_back(s->h_prob[i]);
+            r.logodds.push_back(s->h_logodds[i]);
+        }
+    }
+    const uint64_t t_done = now_ns();
+    uint32_t done = 0;
+    for (uint32_t w = 0; w < n_win; w++) {
+        Win &W_ = wins[w];
+        Patch &P = s->patches[W_.patch];
+        for (uint64_t id : W_.reqs) {
+            Request &r = s->requests.at(id);
+            finish(s, r, cst != GP_OK ? cst : (gp_status)win_status[w], t_done);
+            s->free_stage.push_back(r.stage);
+            P.pending.pop_front();
+            s->n_pending--;
+            done++;
+        }
+        P.next_step = W_.t_b + 1;
+    }
+    if (n_completed) *n_completed = done;
+    return cst;
+}
+
+gp_status gp_server_completed(gp_server *s, uint64_t *ids, uint32_t cap, uint32_t *n) {
+    if (!s || !n || (cap && !ids)) return sfail(GP_ERR_INVALID, "null argument");
+    const uint32_t k = (uint32_t)std::min<size_t>(cap, s->completed.size());
+    for (uint32_t i = 0; i < k; i++) ids[i] = s->completed[i];
+    s->completed.erase(s->completed.begin(), s->completed.begin() + k);
+    *n = k;
+    return GP_OK;
+}
+
+gp_status gp_server_result(const gp_server *s, uint64_t request, gp_sealed_view *out) {
+    if (!s || !out) return sfail(GP_ERR_INVALID, "null argument");
+    auto it = s->requests.find(request);
+    if (it == s->requests.end() || !it->second.done) return sfail(GP_ERR_INVALID, "unknown or pending request");
+    const Request &r = it->second;
+    out->request = r.id;
+    out->patch = r.patch;
+    out->cycle = r.cycle;
+    out->status = r.status;
+    out->n_edges = (uint32_t)r.prob.size();
+    out->n_det_entries = r.det_idx.size();
+    out->det_offsets = r.det_offsets.data();
+    out->det_idx = r.det_idx.data();
+    out->obs_mask = r.obs.data();
+    out->prob = r.prob.data();
+    out->logodds = r.logodds.data();
+    out->t_arrival_ns = r.t_arrival;
+    out->t_done_ns = r.t_done;
+    return GP_OK;
+}
+
+gp_status gp_server_release(gp_server *s, uint64_t request) {
+    if (!s) return sfail(GP_ERR_INVALID, "null argument");
+    auto it = s->requests.find(request);
+    if (it == s->requests.end() || !it->second.done) return sfail(GP_ERR_INVALID, "unknown or pending request");
+    s->requests.erase(it);
+    return GP_OK;
+}
+
+}  // extern "C"

@@ -155,18 +155,6 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in
     }
 }
 
-void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
-                 cudaStream_t s, uint32_t *launches) {
-    const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
-    const uint32_t g2 = (g1 + kScanBlock - 1) / kScanBlock;
-    const uint32_t grid1 = g1 ? g1 : 1u, grid2 = g2 ? g2 : 1u;
-    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.status);
-    scan_reduce2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
-    scan_top_kernel<<<1, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum2, B.scan_total, B.status);
-    scan_down2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
-    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.scan_total, out, B.status);
-    *launches += 5;
-}
 
 // ---- per-mechanism words ----------------------------------------------------
 // word counts as scan input
@@ -422,6 +410,21 @@ __global__ void init_table_kernel(TabSlot *t, size_t n) {
 }
 
 }  // namespace
+
+// exclusive scan of n (read on the device) uint2 values: out[i] = sum of
+// in[0..i), out[n] = the total; three levels of 2048-element blocks
+void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
+                 cudaStream_t s, uint32_t *launches) {
+    const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
+    const uint32_t g2 = (g1 + kScanBlock - 1) / kScanBlock;
+    const uint32_t grid1 = g1 ? g1 : 1u, grid2 = g2 ? g2 : 1u;
+    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.status);
+    scan_reduce2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
+    scan_top_kernel<<<1, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum2, B.scan_total, B.status);
+    scan_down2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
+    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.scan_total, out, B.status);
+    *launches += 5;
+}
 
 void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
                   uint32_t *launches) {

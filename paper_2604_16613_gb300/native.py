@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/gpdem.h (argument marshalling only).
+"""ctypes declarations of the C ABI in include/gpdem.h and include/gpserve.h
+(argument marshalling only).
 
 Loading fails loudly when ``_lib/libgpdem.so`` has not been built: there is no
 fallback implementation.
@@ -22,6 +23,8 @@ EXPORTED = [
     "gp_workspace_size", "gp_driver_create", "gp_driver_destroy", "gp_compile_batch", "gp_compile",
     "gp_backward", "gp_result_view", "gp_set_tuning", "gp_get_tuning", "gp_enable_timing",
     "gp_last_timing", "gp_last_launch_count", "gp_last_error", "gp_pmerge_noalloc",
+    "gp_server_create", "gp_server_destroy", "gp_server_open_patch", "gp_server_close_patch",
+    "gp_server_submit", "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release",
 ]
 
 
@@ -54,6 +57,28 @@ class GpDemView(ctypes.Structure):
 class GpTuning(ctypes.Structure):
     _fields_ = [("stage1_threads", ctypes.c_uint32), ("stage1_blocks_per_sm", ctypes.c_uint32),
                 ("stage2_threads", ctypes.c_uint32), ("stage2_blocks_per_sm", ctypes.c_uint32)]
+
+
+class GpServerConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "max_patches", "max_batch", "max_cycles_per_step", "max_horizon", "max_pending", "max_qubits",
+        "max_cycle_ops", "max_cycle_recs", "max_cycle_locations", "max_cycle_measurements",
+        "max_cycle_detectors", "max_cycle_mechanisms", "max_cycle_layers", "max_logical_qubits")]
+
+
+class GpPatchSpec(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_uint32), ("horizon", ctypes.c_uint32), ("n_observables", ctypes.c_uint32),
+                ("logical_qubits", ctypes.POINTER(ctypes.c_uint32)),
+                ("logical_offsets", ctypes.POINTER(ctypes.c_uint32))]
+
+
+class GpSealedView(ctypes.Structure):
+    _fields_ = [("request", ctypes.c_uint64), ("patch", ctypes.c_uint32), ("cycle", ctypes.c_uint32),
+                ("status", ctypes.c_int), ("n_edges", ctypes.c_uint32), ("n_det_entries", ctypes.c_uint64),
+                ("det_offsets", ctypes.POINTER(ctypes.c_uint32)), ("det_idx", ctypes.POINTER(ctypes.c_uint32)),
+                ("obs_mask", ctypes.POINTER(ctypes.c_uint64)), ("prob", ctypes.POINTER(ctypes.c_float)),
+                ("logodds", ctypes.POINTER(ctypes.c_float)), ("t_arrival_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64)]
 
 
 class GpError(RuntimeError):
@@ -94,6 +119,20 @@ def load(path: str = LIB_PATH):
         lib.gp_last_launch_count.restype = u32
         lib.gp_pmerge_noalloc.argtypes = [vp, vp, u32, u32, vp, vp, vp]
         lib.gp_pmerge_noalloc.restype = i32
+        lib.gp_server_create.argtypes = [ctypes.POINTER(GpServerConfig), ctypes.POINTER(vp)]
+        lib.gp_server_destroy.argtypes = [vp]
+        lib.gp_server_destroy.restype = None
+        lib.gp_server_open_patch.argtypes = [vp, ctypes.POINTER(GpPatchSpec), ctypes.POINTER(u32)]
+        lib.gp_server_close_patch.argtypes = [vp, u32]
+        lib.gp_server_submit.argtypes = [vp, u32, ctypes.POINTER(GpCircuit), vp, i32, u64,
+                                         ctypes.POINTER(u64)]
+        lib.gp_server_step.argtypes = [vp, i32, vp, ctypes.POINTER(u32)]
+        lib.gp_server_completed.argtypes = [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32)]
+        lib.gp_server_result.argtypes = [vp, u64, ctypes.POINTER(GpSealedView)]
+        lib.gp_server_release.argtypes = [vp, u64]
+        for name in ("gp_server_create", "gp_server_open_patch", "gp_server_close_patch", "gp_server_submit",
+                     "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release"):
+            getattr(lib, name).restype = i32
         lib.gp_last_error.argtypes = []
         lib.gp_last_error.restype = ctypes.c_char_p
         for name in ("gp_workspace_size", "gp_driver_create", "gp_compile_batch", "gp_compile",

@@ -1,6 +1,6 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads without a
-GPU, exports every entry point include/gpdem.h declares, and the ctypes
-structures match the C layouts."""
+GPU, exports every entry point include/gpdem.h and include/gpserve.h
+declare, and the ctypes structures match the C layouts."""
 import ctypes
 import os
 import re
@@ -10,13 +10,15 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "gpdem.h")
+HEADERS = [os.path.join(ROOT, "include", "gpdem.h"), os.path.join(ROOT, "include", "gpserve.h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(gp_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(gp_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -50,6 +52,22 @@ def test_struct_layouts_match_header(tmp_path):
     want = [ctypes.sizeof(native.GpBounds), ctypes.sizeof(native.GpCircuit), ctypes.sizeof(native.GpDemView),
             ctypes.sizeof(native.GpTuning), native.GpDemView.det_offsets.offset,
             native.GpBounds.max_det_entries.offset]
+    assert got == want
+
+
+def test_server_struct_layouts_match_header(tmp_path):
+    from paper_2604_16613_gb300 import native
+    src = tmp_path / "sz2.c"
+    src.write_text('#include "gpserve.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gp_server_config),'
+                   ' sizeof(gp_patch_spec), sizeof(gp_sealed_view), offsetof(gp_sealed_view, det_offsets),'
+                   ' offsetof(gp_sealed_view, t_arrival_ns), offsetof(gp_patch_spec, logical_qubits));return 0;}\n')
+    exe = tmp_path / "sz2"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(native.GpServerConfig), ctypes.sizeof(native.GpPatchSpec),
+            ctypes.sizeof(native.GpSealedView), native.GpSealedView.det_offsets.offset,
+            native.GpSealedView.t_arrival_ns.offset, native.GpPatchSpec.logical_qubits.offset]
     assert got == want
 
 

@@ -1,0 +1,142 @@
+"""GPU checks of the cycle-streaming server: a patch streamed cycle by cycle
+through the server delivers exactly the hyperedges of the full-circuit
+compile (the same GPU library bit for bit; the oracle within the parity
+tolerance), whatever the number of cycles merged per step and whatever
+other patches share the steps; a horizon that is too short is refused."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2604_16613_gb300 import circuits as C
+from paper_2604_16613_gb300 import native
+from paper_2604_16613_gb300.dem import Driver
+from paper_2604_16613_gb300.serve import Server
+
+from parity import compare_edges, oracle_edges
+from test_serve_semantics import delay_line
+
+pytestmark = pytest.mark.gpu
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32)
+
+
+def gpu_full(circ, level="L2"):
+    drv = Driver.for_circuits([circ])
+    return drv.compile(circ, f32(circ.default_noise), level).edges()
+
+
+def log_uniform(circ, seed):
+    circ._p = [C.log_uniform_noise(circ.n_locations, seed=seed)]
+    circ._frozen = None
+    return circ
+
+
+def workloads():
+    return {
+        "surface3": (C.rotated_surface_code_memory(3, 6, C.NoiseModel.uniform(1e-3)), 1),
+        "surface5": (log_uniform(C.rotated_surface_code_memory(5, 7, C.NoiseModel.uniform(1e-3)), 3), 1),
+        "bb": (C.bb_memory(4, C.NoiseModel.uniform(1e-3), seed=3), 1),
+        "adaptive": (C.concatenated_adaptive_branch(4, 9, seed=5, noise=C.NoiseModel.uniform(1e-3),
+                                                    layout=C.ConcatenatedLayout(4)), 2),
+        "delay": (delay_line(9), 3),
+    }
+
+
+@pytest.fixture(scope="module")
+def wl():
+    return workloads()
+
+
+@pytest.mark.parametrize("name", ["surface3", "surface5", "bb", "adaptive", "delay"])
+@pytest.mark.parametrize("K", [1, 3])
+def test_stream_equals_full_compile(wl, name, K):
+    circ, H = wl[name]
+    srv = Server.for_circuits([circ], max_cycles_per_step=K, max_horizon=H)
+    got = srv.stream([circ], [H])[0]
+    ref = gpu_full(circ)
+    assert set(got) == set(ref)
+    for k, (p, w) in ref.items():
+        assert got[k][0] == p and got[k][1] == w, k
+    compare_edges(got, oracle_edges(circ, f32(circ.default_noise)).edges(), f"{name} K={K}")
+
+
+def test_levels(wl):
+    circ, H = wl["surface5"]
+    srv = Server.for_circuits([circ], max_cycles_per_step=2, max_horizon=H)
+    for level in ("L0", "L1"):
+        got = srv.stream([circ], [H], level=level)[0]
+        compare_edges(got, oracle_edges(circ, f32(circ.default_noise), level).edges(), level)
+
+
+def test_mix_equals_alone(wl):
+    """Patches sharing steps (batch smaller than the patch count, cycles
+    interleaved) get the same hyperedges as each patch served alone."""
+    names = ["surface3", "surface5", "bb", "adaptive", "delay", "surface3"]
+    circs = [wl[n][0] for n in names]
+    hs = [wl[n][1] for n in names]
+    mixed = Server.for_circuits(circs, max_batch=4, max_cycles_per_step=2, max_horizon=max(hs),
+                                max_pending=64).stream(circs, hs)
+    for n, c, h, got in zip(names, circs, hs, mixed):
+        alone = Server.for_circuits([c], max_cycles_per_step=1, max_horizon=h).stream([c], [h])[0]
+        assert got == alone, n
+
+
+def test_record_horizon_refused_at_submit(wl):
+    circ, _ = wl["adaptive"]          # outer detectors look two cycles back
+    srv = Server.for_circuits([circ], max_horizon=2)
+    pid = srv.open_circuit_patch(circ, horizon=1)
+    blocks = circ.cycle_blocks()
+    with pytest.raises(native.GpError) as e:
+        for b in blocks:
+            srv.submit(pid, b)
+    assert e.value.code == native.GP_ERR_HORIZON
+
+
+def test_reach_horizon_found_on_the_device(wl):
+    """The bucket brigade's records reach one cycle back, its errors three:
+    with H = 1 the submissions pass and the windows report the horizon."""
+    circ, _ = wl["delay"]
+    srv = Server.for_circuits([circ], max_horizon=1, max_pending=32)
+    pid = srv.open_circuit_patch(circ, horizon=1)
+    ids = [srv.submit(pid, b) for b in circ.cycle_blocks()]
+    statuses = []
+    while len(statuses) < len(ids):
+        srv.step()
+        for r in srv.completed():
+            statuses.append(srv.result(r, raise_on_error=False)["status"])
+    assert native.GP_ERR_HORIZON in statuses
+    # the server stays usable
+    good = Server.for_circuits([circ], max_horizon=3).stream([circ], [3])[0]
+    assert set(good) == set(gpu_full(circ))
+
+
+def test_api_errors(wl):
+    circ, _ = wl["surface3"]
+    srv = Server.for_circuits([circ], max_patches=1)
+    pid = srv.open_circuit_patch(circ)
+    with pytest.raises(native.GpError) as e:
+        srv.open_circuit_patch(circ)
+    assert e.value.code == native.GP_ERR_CAPACITY
+    blocks = circ.cycle_blocks()
+    with pytest.raises(native.GpError):
+        srv.submit(pid, blocks[-1], final=False)      # observables only in a final cycle
+    big = dict(blocks[0])
+    big["ops"] = np.concatenate([blocks[0]["ops"]] * 3)
+    with pytest.raises(native.GpError) as e:
+        srv.submit(pid, big)
+    assert e.value.code == native.GP_ERR_CAPACITY
+    rid = srv.submit(pid, blocks[0])
+    with pytest.raises(native.GpError):
+        srv.close_patch(pid)                          # pending cycle
+    with pytest.raises(native.GpError):
+        srv.result(rid)                               # not finished
+    assert srv.step() == 1
+    assert srv.completed() == [rid]
+    assert srv.result(rid)["cycle"] == 0
+    srv.release(rid)
+    srv.close_patch(pid)
