@@ -113,6 +113,23 @@ gp_status gp_server_close_patch(gp_server *srv, uint32_t patch);
 gp_status gp_server_submit(gp_server *srv, uint32_t patch, const gp_circuit *cycle, const float *noise,
                            int final, uint64_t t_arrival_ns, uint64_t *request);
 
+/* Register a cycle a patch repeats (a steady-state syndrome round): it is
+ * copied once into pinned host memory and submitted by id, with the same
+ * checks as gp_server_submit at every submission.  *cycle_id receives its
+ * id.  The registered cycles of a patch are freed when it closes. */
+gp_status gp_server_register_cycle(gp_server *srv, uint32_t patch, const gp_circuit *cycle, const float *noise,
+                                   uint32_t *cycle_id);
+gp_status gp_server_submit_registered(gp_server *srv, uint32_t patch, uint32_t cycle_id, int final,
+                                      uint64_t t_arrival_ns, uint64_t *request);
+
+/* Submit n registered cycles at once (patches[i], cycle_ids[i], finals[i],
+ * t_arrival_ns[i]; host arrays).  Stops at the first failure: *n_done
+ * receives how many were queued, requests[0 .. *n_done) their ids, and the
+ * failure is returned. */
+gp_status gp_server_submit_registered_many(gp_server *srv, uint32_t n, const uint32_t *patches,
+                                           const uint32_t *cycle_ids, const uint8_t *finals,
+                                           const uint64_t *t_arrival_ns, uint64_t *requests, uint32_t *n_done);
+
 /* One scheduling step: up to max_batch patches with pending cycles (oldest
  * first), up to K cycles each, compiled in one batched launch on the
  * caller's stream; returns when their results are on the host.
@@ -122,9 +139,22 @@ gp_status gp_server_submit(gp_server *srv, uint32_t patch, const gp_circuit *cyc
  * returned. */
 gp_status gp_server_step(gp_server *srv, gp_level level, void *stream, uint32_t *n_completed);
 
+/* Microseconds of the last step: host wall clock of building the windows
+ * and uploading cycles and descriptors, of the batched compile, of selecting
+ * and copying back the sealed hyperedges and of handing them to the
+ * requests; then the compile's device stages (lowering, stage 1, grouping,
+ * compaction) as gp_last_timing reports them. */
+gp_status gp_server_last_timing(const gp_server *srv, float times_us[8]);
+
 /* Ids of requests finished since the last call (at most cap; *n receives
  * the count). */
 gp_status gp_server_completed(gp_server *srv, uint64_t *ids, uint32_t cap, uint32_t *n);
+
+/* Finished requests, oldest first, at most cap: id, arrival and completion
+ * times, hyperedges delivered and status (host arrays of cap entries); their
+ * results are released.  *n receives the count. */
+gp_status gp_server_drain(gp_server *srv, uint32_t cap, uint64_t *ids, uint64_t *t_arrival_ns, uint64_t *t_done_ns,
+                          uint32_t *n_edges, int32_t *status, uint32_t *n);
 
 /* Result of a finished request (GP_ERR_INVALID for an unknown or pending
  * one). */

@@ -10,12 +10,14 @@
 //     in a final window) and appending the rows that close a window with the
 //     declared logicals;
 //   - the windows are compiled as one batch (gp_compile_batch);
-//   - seal: a flag per hyperedge (its smallest detector lies in a cycle the
-//     step seals), a horizon test per window (no mechanism of a records-only
-//     cycle c flips a detector after cycle c + H: those detectors all lie in
-//     the window, so a violation shows), a scan, and a compaction of the
-//     sealed hyperedges with patch-global detector ids, which are copied to
-//     the host and split per request.
+//   - seal: a horizon test per window (no mechanism of a records-only cycle
+//     c flips a detector after cycle c + H: those detectors all lie in the
+//     window, so a violation shows); then, for each request slot r of the
+//     windows (their r-th merged cycle), a flag per hyperedge (sealed, and
+//     its smallest detector lies in the cycle that request seals), a scan
+//     and a compaction of those hyperedges with patch-global detector ids.
+//     Every request's hyperedges thus come out contiguous and are copied to
+//     the host in slices.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -74,7 +76,10 @@ struct SealDesc {
     uint32_t det_base;          // patch-global id of window-local detector 0
     uint32_t n_mech_rec;        // mechanisms of the records-only cycles (0: no check)
     uint32_t n_rec;             // records-only cycles
-    uint32_t pad[2];
+    uint32_t n_cyc;             // cycles of the window (entries of its cycle table - 1)
+    int32_t r_off;              // request slot of cycle j of the window: min(j + r_off, r_max)
+    uint32_t r_max;
+    uint32_t pad[3];
 };
 // per records-only cycle j of a window: (end of its mechanisms, first
 // window-local detector it may not flip)
@@ -103,21 +108,64 @@ __global__ void __launch_bounds__(256) assemble_kernel(const SegDesc *seg, uint3
         noise[d.dst_loc + i] = (d.flags & kSegZeroNoise) ? 0.0f : d.noise[i];
 }
 
-// scan input per hyperedge: (sealed, detector count)
-__global__ void seal_flags_kernel(Buffers B, const SealDesc *seal) {
+// scan input per hyperedge: (delivered with request slot r, detector count)
+__global__ void seal_flags_kernel(Buffers B, const SealDesc *seal, const uint32_t *cyc_tab, uint32_t tab_stride,
+                                  uint32_t r) {
     const uint32_t E = B.status->n_edges;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         const uint32_t w = B.edge_circ[e];
+        const SealDesc &sd = seal[w];
         const uint32_t o0 = B.det_off[e], o1 = B.det_off[e + 1];
-        bool sealed;
+        bool take;
         if (o1 > o0) {
             const uint32_t d0 = B.det_idx[o0];          // detector lists are ascending
-            sealed = d0 >= seal[w].det_lo && d0 < seal[w].det_hi;
+            take = d0 >= sd.det_lo && d0 < sd.det_hi;
+            if (take) {
+                // cycle of d0 within the window: last j with tab[j] <= d0
+                const uint32_t *tab = cyc_tab + (size_t)w * tab_stride;
+                uint32_t lo = 0, hi = sd.n_cyc;
+                while (hi - lo > 1u) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (tab[mid] <= d0) lo = mid; else hi = mid;
+                }
+                const int32_t slot = min((int32_t)lo + sd.r_off, (int32_t)sd.r_max);
+                take = slot == (int32_t)r;
+            }
         } else {
-            sealed = seal[w].take_no_det != 0u;
+            take = sd.take_no_det != 0u && sd.r_max == r;
         }
-        B.scan_val[e] = sealed ? make_uint2(1u, o1 - o0) : make_uint2(0u, 0u);
+        B.scan_val[e] = take ? make_uint2(1u, o1 - o0) : make_uint2(0u, 0u);
     }
+}
+
+// first hyperedge of every window (from the compile's per-circuit counts)
+__global__ void win_edges_kernel(Buffers B, uint32_t n_win, uint32_t *win_e0) {
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (uint32_t w = 0; w < n_win; w++) {
+            win_e0[w] = run;
+            run += B.circ_edges[w];
+        }
+        win_e0[n_win] = run;
+    }
+}
+
+// after the scan of slot r: where its hyperedges and detector ids start for
+// every window (after those of slots 0 .. r-1); the last detector offset of
+// every request (r, w) -- offsets are per request, and request (r, w) is the
+// (r n_win + w)-th, so its offsets sit r n_win + w entries after its edges
+__global__ void slot_starts_kernel(Buffers B, uint32_t n_win, const uint32_t *win_e0, uint32_t r, uint2 *starts,
+                                   uint32_t *doff) {
+    const uint32_t E = B.status->n_edges;
+    const uint2 base = r ? starts[(size_t)(r - 1u) * (n_win + 1u) + n_win] : make_uint2(0u, 0u);
+    uint2 *row = starts + (size_t)r * (n_win + 1u);
+    for (uint32_t w = threadIdx.x; w <= n_win; w += blockDim.x) {
+        const uint2 c = B.comp_off[w < n_win ? win_e0[w] : E];
+        row[w] = make_uint2(base.x + c.x, base.y + c.y);
+    }
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < n_win; w += blockDim.x)
+        doff[row[w + 1].x + r * n_win + w] = row[w + 1].y - row[w].y;
 }
 
 // a mechanism of records-only cycle c flipping a detector after cycle c + H:
@@ -140,28 +188,25 @@ __global__ void seal_horizon_kernel(Buffers B, const SealDesc *seal, const uint2
 }
 
 struct SealOut {
-    uint32_t *win, *doff, *det, *totals;
+    uint32_t *doff, *det;
     float *prob, *logodds;
     unsigned long long *obs;
 };
 
-__global__ void seal_write_kernel(Buffers B, const SealDesc *seal, SealOut out) {
+__global__ void seal_write_kernel(Buffers B, const SealDesc *seal, SealOut out, const uint2 *row, uint32_t r,
+                                  uint32_t n_win) {
     const uint32_t E = B.status->n_edges;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        out.totals[0] = B.comp_off[E].x;
-        out.totals[1] = B.comp_off[E].y;
-    }
+    const uint2 base = row[0];
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         if (B.scan_val[e].x == 0u) continue;
         const uint2 off = B.comp_off[e];
-        const uint32_t w = B.edge_circ[e];
-        out.win[off.x] = w;
-        out.prob[off.x] = B.prob[e];
-        out.logodds[off.x] = B.logodds[e];
-        out.obs[off.x] = B.obs_mask[e];
-        out.doff[off.x] = off.y;
-        const uint32_t o0 = B.det_off[e], o1 = B.det_off[e + 1], base = seal[w].det_base;
-        for (uint32_t i = o0; i < o1; i++) out.det[off.y + (i - o0)] = B.det_idx[i] + base;
+        const uint32_t w = B.edge_circ[e], pos = base.x + off.x, dpos = base.y + off.y;
+        out.prob[pos] = B.prob[e];
+        out.logodds[pos] = B.logodds[e];
+        out.obs[pos] = B.obs_mask[e];
+        out.doff[pos + r * n_win + w] = dpos - row[w].y;
+        const uint32_t o0 = B.det_off[e], o1 = B.det_off[e + 1], db = seal[w].det_base;
+        for (uint32_t i = o0; i < o1; i++) out.det[dpos + (i - o0)] = B.det_idx[i] + db;
     }
 }
 
@@ -178,18 +223,51 @@ struct CycleInfo {
     uint32_t n_ops, n_recs, n_loc, n_meas, n_det, n_ticks;
     uint32_t mech[3];           // mechanisms at L0, L1, L2
     uint64_t det_base, meas_base;
+    // where the cycle lives on the device once stepped (ring slot or
+    // registered copy)
+    const uint4 *src_ops;
+    const uint32_t *src_recs;
+    const float *src_noise;
 };
+
+// a cycle registered once by its patch: pinned host copies (for the checks)
+// and device copies (the windows read it from there)
+struct Registered {
+    uint4 *ops = nullptr;
+    uint32_t *recs = nullptr;
+    float *noise = nullptr;
+    uint4 *d_ops = nullptr;
+    uint32_t *d_recs = nullptr;
+    float *d_noise = nullptr;
+    gp_circuit meta{};
+};
+
+// pinned host copy of one step's delivered hyperedges, shared by the
+// requests it serves until they are released
+struct OutBuf {
+    uint32_t *doff = nullptr, *det = nullptr;
+    float *prob = nullptr, *logodds = nullptr;
+    unsigned long long *obs = nullptr;
+    uint64_t edges_cap = 0, det_cap = 0;    // doff holds edges_cap + offs_extra entries
+    uint32_t refs = 0;
+};
+const uint32_t kNoOffsets[1] = {0};
 
 struct Request {
     uint64_t id = 0;
     uint32_t patch = 0, cycle = 0;
     bool final = false, done = false;
     uint32_t stage = 0;          // pinned staging slot of the submitted cycle
+    int32_t reg = -1;            // or the registered cycle it repeats
     gp_status status = GP_OK;
     uint64_t t_arrival = 0, t_done = 0;
-    std::vector<uint32_t> det_offsets{0}, det_idx;
-    std::vector<uint64_t> obs;
-    std::vector<float> prob, logodds;
+    // delivered hyperedges: a slice of a shared step buffer
+    OutBuf *buf = nullptr;
+    uint32_t n_edges = 0;
+    uint64_t n_det = 0;
+    const uint32_t *det_offsets = kNoOffsets, *det_idx = nullptr;
+    const unsigned long long *obs = nullptr;
+    const float *prob = nullptr, *logodds = nullptr;
 };
 
 struct Patch {
@@ -202,6 +280,7 @@ struct Patch {
     uint32_t *ring_recs = nullptr;
     float *ring_noise = nullptr;
     std::vector<CycleInfo> cycles;       // every submitted cycle
+    std::vector<Registered> registered;
     uint32_t next_step = 0;              // first cycle not yet stepped
     bool final_submitted = false;
     std::deque<uint64_t> pending;        // submitted, not yet stepped (cycle order)
@@ -226,6 +305,11 @@ struct gp_server {
     uint4 *d_extra_ops = nullptr;
     uint32_t *d_extra_recs = nullptr;
     uint32_t *d_horizon = nullptr;
+    uint32_t *d_cyc_tab = nullptr;       // per window: detector offset of each cycle
+    uint32_t *d_win_e0 = nullptr;        // per window: first hyperedge
+    uint2 *d_starts = nullptr;           // per request slot and window: output starts
+    float times[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // last step: build, compile, select, hand-out,
+                                                 // then the compile's device stages (us)
     SealOut out{};
     uint64_t out_edges_cap = 0, out_det_cap = 0;
     // pinned host memory
@@ -236,11 +320,8 @@ struct gp_server {
     float *h_stage_noise = nullptr;
     std::vector<uint32_t> free_stage;
     uint32_t *h_horizon = nullptr;
-    uint32_t *h_totals = nullptr;
-    uint32_t *h_win = nullptr, *h_doff = nullptr, *h_det = nullptr;
-    float *h_prob = nullptr, *h_logodds = nullptr;
-    unsigned long long *h_obs = nullptr;
-    uint64_t h_edges_cap = 0, h_det_cap = 0;
+    uint2 *h_starts = nullptr;           // per request slot and window: output starts
+    std::vector<OutBuf *> out_pool;
     // state
     std::vector<Patch> patches;
     std::unordered_map<uint64_t, Request> requests;
@@ -258,44 +339,71 @@ template <class T> T *carve_dev(unsigned char *base, uint64_t &off, uint64_t cou
     return p;
 }
 
-void free_host(gp_server *s) {
-    void *ptrs[] = {s->h_desc, s->h_stage_ops, s->h_stage_recs, s->h_stage_noise, s->h_horizon, s->h_totals,
-                    s->h_win, s->h_doff, s->h_det, s->h_prob, s->h_logodds, s->h_obs};
-    for (void *p : ptrs)
-        if (p) cudaFreeHost(p);
+void free_registered(Patch &p) {
+    for (Registered &r : p.registered) {
+        if (r.ops) cudaFreeHost(r.ops);
+        if (r.recs) cudaFreeHost(r.recs);
+        if (r.noise) cudaFreeHost(r.noise);
+        if (r.d_ops) cudaFree(r.d_ops);
+        if (r.d_recs) cudaFree(r.d_recs);
+        if (r.d_noise) cudaFree(r.d_noise);
+    }
+    p.registered.clear();
 }
 
-gp_status grow_host_out(gp_server *s, uint64_t edges, uint64_t dets) {
-    if (edges <= s->h_edges_cap && dets <= s->h_det_cap) return GP_OK;
-    const uint64_t ne = std::max<uint64_t>(edges, s->h_edges_cap), nd = std::max<uint64_t>(dets, s->h_det_cap);
-    void *ptrs[] = {s->h_win, s->h_doff, s->h_det, s->h_prob, s->h_logodds, s->h_obs};
+void free_outbuf(OutBuf *b) {
+    if (!b) return;
+    void *ptrs[] = {b->doff, b->det, b->prob, b->logodds, b->obs};
     for (void *p : ptrs)
         if (p) cudaFreeHost(p);
-    s->h_win = s->h_doff = s->h_det = nullptr;
-    s->h_prob = s->h_logodds = nullptr;
-    s->h_obs = nullptr;
-    s->h_edges_cap = s->h_det_cap = 0;
-    if (cudaMallocHost(&s->h_win, 4 * ne) != cudaSuccess || cudaMallocHost(&s->h_doff, 4 * (ne + 1)) != cudaSuccess ||
-        cudaMallocHost(&s->h_det, 4 * std::max<uint64_t>(nd, 1)) != cudaSuccess ||
-        cudaMallocHost(&s->h_prob, 4 * ne) != cudaSuccess || cudaMallocHost(&s->h_logodds, 4 * ne) != cudaSuccess ||
-        cudaMallocHost(&s->h_obs, 8 * ne) != cudaSuccess)
-        return sfail(GP_ERR_CUDA, "cudaMallocHost of the result staging failed");
-    s->h_edges_cap = ne;
-    s->h_det_cap = nd;
-    return GP_OK;
+    delete b;
+}
+
+void free_host(gp_server *s) {
+    for (Patch &p : s->patches) free_registered(p);
+    void *ptrs[] = {s->h_desc, s->h_stage_ops, s->h_stage_recs, s->h_stage_noise, s->h_horizon, s->h_starts};
+    for (void *p : ptrs)
+        if (p) cudaFreeHost(p);
+    for (OutBuf *b : s->out_pool) free_outbuf(b);
+    s->out_pool.clear();
+}
+
+// a free step buffer holding `edges` hyperedges (plus `extra` detector
+// offsets) and `dets` detector ids, allocated when none fits
+OutBuf *take_outbuf(gp_server *s, uint64_t edges, uint64_t extra, uint64_t dets) {
+    for (OutBuf *b : s->out_pool)
+        if (b->refs == 0 && b->edges_cap >= edges + extra && b->det_cap >= dets) return b;
+    OutBuf *b = new (std::nothrow) OutBuf();
+    if (!b) return nullptr;
+    const uint64_t ne = std::max<uint64_t>(edges + extra, 1u << 16) * 5 / 4, nd = std::max<uint64_t>(dets, 1u << 18) * 5 / 4;
+    if (cudaMallocHost(&b->doff, 4 * ne) != cudaSuccess || cudaMallocHost(&b->det, 4 * nd) != cudaSuccess ||
+        cudaMallocHost(&b->prob, 4 * ne) != cudaSuccess || cudaMallocHost(&b->logodds, 4 * ne) != cudaSuccess ||
+        cudaMallocHost(&b->obs, 8 * ne) != cudaSuccess) {
+        free_outbuf(b);
+        return nullptr;
+    }
+    b->edges_cap = ne;
+    b->det_cap = nd;
+    s->out_pool.push_back(b);
+    return b;
+}
+
+void drop_result(Request &r) {
+    if (r.buf) r.buf->refs--;
+    r.buf = nullptr;
+    r.n_edges = 0;
+    r.n_det = 0;
+    r.det_offsets = kNoOffsets;
+    r.det_idx = nullptr;
+    r.obs = nullptr;
+    r.prob = r.logodds = nullptr;
 }
 
 void finish(gp_server *s, Request &r, gp_status st, uint64_t t) {
     r.status = st;
     r.done = true;
     r.t_done = t;
-    if (st != GP_OK) {
-        r.det_offsets.assign(1, 0);
-        r.det_idx.clear();
-        r.obs.clear();
-        r.prob.clear();
-        r.logodds.clear();
-    }
+    if (st != GP_OK) drop_result(r);
     s->completed.push_back(r.id);
 }
 
@@ -378,10 +486,11 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
         s->d_extra_ops = carve_dev<uint4>(base, off, Bt * s->extra_ops);
         s->d_extra_recs = carve_dev<uint32_t>(base, off, std::max<uint64_t>(Bt * s->extra_recs, 1));
         s->d_horizon = carve_dev<uint32_t>(base, off, Bt);
-        s->out.win = carve_dev<uint32_t>(base, off, s->out_edges_cap);
-        s->out.doff = carve_dev<uint32_t>(base, off, s->out_edges_cap + 1);
+        s->out.doff = carve_dev<uint32_t>(base, off, s->out_edges_cap + (uint64_t)c.max_cycles_per_step * (Bt + 1));
         s->out.det = carve_dev<uint32_t>(base, off, std::max<uint64_t>(s->out_det_cap, 1));
-        s->out.totals = carve_dev<uint32_t>(base, off, 2);
+        s->d_cyc_tab = carve_dev<uint32_t>(base, off, Bt * (W + 1));
+        s->d_win_e0 = carve_dev<uint32_t>(base, off, Bt + 1);
+        s->d_starts = carve_dev<uint2>(base, off, (uint64_t)c.max_cycles_per_step * (Bt + 1));
         s->out.prob = carve_dev<float>(base, off, s->out_edges_cap);
         s->out.logodds = carve_dev<float>(base, off, s->out_edges_cap);
         s->out.obs = carve_dev<unsigned long long>(base, off, s->out_edges_cap);
@@ -400,22 +509,20 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
     {
         const gp_status st = gp_driver_create(&b, nullptr, 0, &s->drv);
         if (st != GP_OK) return cleanup(st);
+        gp_enable_timing(s->drv, 1);
     }
     // pinned staging
     s->h_desc_bytes = nseg * sizeof(SegDesc) + Bt * sizeof(SealDesc) + Bt * s->extra_ops * sizeof(uint4) +
-                      Bt * s->extra_recs * sizeof(uint32_t) + Bt * c.max_horizon * sizeof(uint2);
+                      Bt * s->extra_recs * sizeof(uint32_t) + Bt * c.max_horizon * sizeof(uint2) +
+                      Bt * (W + 1) * sizeof(uint32_t);
     if (cudaMallocHost(&s->h_desc, s->h_desc_bytes) != cudaSuccess ||
         cudaMallocHost(&s->h_stage_ops, sizeof(uint4) * (uint64_t)c.max_pending * c.max_cycle_ops) != cudaSuccess ||
         cudaMallocHost(&s->h_stage_recs, sizeof(uint32_t) * std::max<uint64_t>((uint64_t)c.max_pending * c.max_cycle_recs, 1)) != cudaSuccess ||
         cudaMallocHost(&s->h_stage_noise, sizeof(float) * std::max<uint64_t>((uint64_t)c.max_pending * c.max_cycle_locations, 1)) != cudaSuccess ||
         cudaMallocHost(&s->h_horizon, sizeof(uint32_t) * Bt) != cudaSuccess ||
-        cudaMallocHost(&s->h_totals, sizeof(uint32_t) * 2) != cudaSuccess)
+        cudaMallocHost(&s->h_starts, sizeof(uint2) * (uint64_t)c.max_cycles_per_step * (Bt + 1)) != cudaSuccess)
         return cleanup(sfail(GP_ERR_CUDA, "cudaMallocHost of the server staging failed"));
     for (uint32_t i = 0; i < c.max_pending; i++) s->free_stage.push_back(c.max_pending - 1 - i);
-    {
-        const gp_status st = grow_host_out(s, 1u << 16, 1u << 20);
-        if (st != GP_OK) return cleanup(st);
-    }
     *out = s;
     return GP_OK;
 }
@@ -478,6 +585,7 @@ gp_status gp_server_close_patch(gp_server *s, uint32_t patch) {
     if (!s || patch >= s->cfg.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
     Patch &p = s->patches[patch];
     if (!p.pending.empty()) return sfail(GP_ERR_INVALID, "patch has pending cycles");
+    free_registered(p);
     Patch empty;
     empty.ring_ops = p.ring_ops;
     empty.ring_recs = p.ring_recs;
@@ -486,12 +594,14 @@ gp_status gp_server_close_patch(gp_server *s, uint32_t patch) {
     return GP_OK;
 }
 
-gp_status gp_server_submit(gp_server *s, uint32_t patch, const gp_circuit *cyc, const float *noise, int final,
-                           uint64_t t_arrival_ns, uint64_t *request) {
-    if (!s || !cyc || !request) return sfail(GP_ERR_INVALID, "null argument");
+}  // extern "C"
+
+namespace {
+
+// checks of a cycle about to become patch p's next one; fills its sizes
+gp_status check_cycle(const gp_server *s, const Patch &p, const gp_circuit *cyc, const float *noise, bool final,
+                      CycleInfo &ci) {
     const gp_server_config &c = s->cfg;
-    if (patch >= c.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
-    Patch &p = s->patches[patch];
     if (p.final_submitted) return sfail(GP_ERR_INVALID, "patch already ended with a final cycle");
     if (cyc->n_ops > c.max_cycle_ops || cyc->n_recs > c.max_cycle_recs || cyc->n_locations > c.max_cycle_locations ||
         cyc->n_detectors > c.max_cycle_detectors)
@@ -500,11 +610,9 @@ gp_status gp_server_submit(gp_server *s, uint32_t patch, const gp_circuit *cyc, 
     if (cyc->n_observables != p.n_obs) return sfail(GP_ERR_INVALID, "cycle's n_observables differs from its patch's logicals");
     if ((cyc->n_ops && !cyc->ops) || (cyc->n_recs && !cyc->recs) || (cyc->n_locations && !noise))
         return sfail(GP_ERR_INVALID, "null cycle arrays");
-    if (s->free_stage.empty()) return sfail(GP_ERR_CAPACITY, "max_pending cycles are queued");
-    // sizes, mechanism counts and the record-horizon check
     const uint4 *ops = reinterpret_cast<const uint4 *>(cyc->ops);
     const uint32_t t = (uint32_t)p.cycles.size();
-    CycleInfo ci{};
+    ci = CycleInfo{};
     ci.n_ops = (uint32_t)cyc->n_ops;
     ci.n_recs = (uint32_t)cyc->n_recs;
     ci.n_loc = cyc->n_locations;
@@ -538,25 +646,110 @@ gp_status gp_server_submit(gp_server *s, uint32_t patch, const gp_circuit *cyc, 
     if (n_det != cyc->n_detectors) return sfail(GP_ERR_INVALID, "cycle's n_detectors differs from its DETECTOR rows");
     if (ci.n_meas > c.max_cycle_measurements || ci.n_ticks + 1 > c.max_cycle_layers || ci.mech[2] > c.max_cycle_mechanisms)
         return sfail(GP_ERR_CAPACITY, "cycle larger than the server's per-cycle bounds");
+    return GP_OK;
+}
+
+uint64_t enqueue(gp_server *s, uint32_t patch, const CycleInfo &ci, bool final, uint32_t stage, int32_t reg,
+                 uint64_t t_arrival_ns) {
+    Patch &p = s->patches[patch];
+    p.cycles.push_back(ci);
+    if (final) p.final_submitted = true;
+    Request r;
+    r.id = s->next_request++;
+    r.patch = patch;
+    r.cycle = (uint32_t)p.cycles.size() - 1u;
+    r.final = final;
+    r.stage = stage;
+    r.reg = reg;
+    r.t_arrival = t_arrival_ns ? t_arrival_ns : now_ns();
+    const uint64_t id = r.id;
+    p.pending.push_back(id);
+    s->requests.emplace(id, std::move(r));
+    s->n_pending++;
+    return id;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_server_submit(gp_server *s, uint32_t patch, const gp_circuit *cyc, const float *noise, int final,
+                           uint64_t t_arrival_ns, uint64_t *request) {
+    if (!s || !cyc || !request) return sfail(GP_ERR_INVALID, "null argument");
+    const gp_server_config &c = s->cfg;
+    if (patch >= c.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
+    CycleInfo ci;
+    {
+        const gp_status st = check_cycle(s, s->patches[patch], cyc, noise, final != 0, ci);
+        if (st != GP_OK) return st;
+    }
+    if (s->free_stage.empty()) return sfail(GP_ERR_CAPACITY, "max_pending cycles are queued");
     // stage the cycle (pinned) until its step uploads it
     const uint32_t slot = s->free_stage.back();
     s->free_stage.pop_back();
     if (cyc->n_ops) memcpy(s->h_stage_ops + (uint64_t)slot * c.max_cycle_ops, cyc->ops, cyc->n_ops * sizeof(uint4));
     if (cyc->n_recs) memcpy(s->h_stage_recs + (uint64_t)slot * c.max_cycle_recs, cyc->recs, cyc->n_recs * sizeof(uint32_t));
     if (cyc->n_locations) memcpy(s->h_stage_noise + (uint64_t)slot * c.max_cycle_locations, noise, cyc->n_locations * sizeof(float));
-    p.cycles.push_back(ci);
-    if (final) p.final_submitted = true;
-    Request r;
-    r.id = s->next_request++;
-    *request = r.id;
-    r.patch = patch;
-    r.cycle = t;
-    r.final = final != 0;
-    r.stage = slot;
-    r.t_arrival = t_arrival_ns ? t_arrival_ns : now_ns();
-    p.pending.push_back(r.id);
-    s->requests.emplace(r.id, std::move(r));
-    s->n_pending++;
+    *request = enqueue(s, patch, ci, final != 0, slot, -1, t_arrival_ns);
+    return GP_OK;
+}
+
+gp_status gp_server_register_cycle(gp_server *s, uint32_t patch, const gp_circuit *cyc, const float *noise,
+                                   uint32_t *cycle_id) {
+    if (!s || !cyc || !cycle_id) return sfail(GP_ERR_INVALID, "null argument");
+    const gp_server_config &c = s->cfg;
+    if (patch >= c.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
+    if (cyc->n_ops > c.max_cycle_ops || cyc->n_recs > c.max_cycle_recs || cyc->n_locations > c.max_cycle_locations)
+        return sfail(GP_ERR_CAPACITY, "cycle larger than the server's per-cycle bounds");
+    if ((cyc->n_ops && !cyc->ops) || (cyc->n_recs && !cyc->recs) || (cyc->n_locations && !noise))
+        return sfail(GP_ERR_INVALID, "null cycle arrays");
+    Registered r;
+    r.meta = *cyc;
+    if (cudaMallocHost(&r.ops, sizeof(uint4) * std::max<uint64_t>(cyc->n_ops, 1)) != cudaSuccess ||
+        cudaMallocHost(&r.recs, sizeof(uint32_t) * std::max<uint64_t>(cyc->n_recs, 1)) != cudaSuccess ||
+        cudaMallocHost(&r.noise, sizeof(float) * std::max<uint32_t>(cyc->n_locations, 1)) != cudaSuccess) {
+        if (r.ops) cudaFreeHost(r.ops);
+        if (r.recs) cudaFreeHost(r.recs);
+        if (r.noise) cudaFreeHost(r.noise);
+        return sfail(GP_ERR_CUDA, "cudaMallocHost of a registered cycle failed");
+    }
+    if (cyc->n_ops) memcpy(r.ops, cyc->ops, cyc->n_ops * sizeof(uint4));
+    if (cyc->n_recs) memcpy(r.recs, cyc->recs, cyc->n_recs * sizeof(uint32_t));
+    if (cyc->n_locations) memcpy(r.noise, noise, cyc->n_locations * sizeof(float));
+    r.meta.ops = reinterpret_cast<const uint32_t *>(r.ops);
+    r.meta.recs = r.recs;
+    if (cudaMalloc(&r.d_ops, sizeof(uint4) * std::max<uint64_t>(cyc->n_ops, 1)) != cudaSuccess ||
+        cudaMalloc(&r.d_recs, sizeof(uint32_t) * std::max<uint64_t>(cyc->n_recs, 1)) != cudaSuccess ||
+        cudaMalloc(&r.d_noise, sizeof(float) * std::max<uint32_t>(cyc->n_locations, 1)) != cudaSuccess ||
+        cudaMemcpy(r.d_ops, r.ops, sizeof(uint4) * cyc->n_ops, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(r.d_recs, r.recs, sizeof(uint32_t) * cyc->n_recs, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(r.d_noise, r.noise, sizeof(float) * cyc->n_locations, cudaMemcpyHostToDevice) != cudaSuccess) {
+        Patch tmp;
+        tmp.registered.push_back(r);
+        free_registered(tmp);
+        return sfail(GP_ERR_CUDA, "device copy of a registered cycle failed");
+    }
+    Patch &p = s->patches[patch];
+    p.registered.push_back(r);
+    *cycle_id = (uint32_t)p.registered.size() - 1u;
+    return GP_OK;
+}
+
+gp_status gp_server_submit_registered(gp_server *s, uint32_t patch, uint32_t cycle_id, int final,
+                                      uint64_t t_arrival_ns, uint64_t *request) {
+    if (!s || !request) return sfail(GP_ERR_INVALID, "null argument");
+    const gp_server_config &c = s->cfg;
+    if (patch >= c.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
+    Patch &p = s->patches[patch];
+    if (cycle_id >= p.registered.size()) return sfail(GP_ERR_INVALID, "no such registered cycle");
+    if (s->n_pending >= c.max_pending) return sfail(GP_ERR_CAPACITY, "max_pending cycles are queued");
+    const Registered &r = p.registered[cycle_id];
+    CycleInfo ci;
+    {
+        const gp_status st = check_cycle(s, p, &r.meta, r.noise, final != 0, ci);
+        if (st != GP_OK) return st;
+    }
+    *request = enqueue(s, patch, ci, final != 0, 0u, (int32_t)cycle_id, t_arrival_ns);
     return GP_OK;
 }
 
@@ -564,6 +757,7 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     if (!s) return sfail(GP_ERR_INVALID, "null argument");
     if ((int)level < 0 || (int)level > 2) return sfail(GP_ERR_INVALID, "level must be GP_L0, GP_L1 or GP_L2");
     if (n_completed) *n_completed = 0;
+    const uint64_t t_start = now_ns();
     const gp_server_config &c = s->cfg;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // patches with pending cycles, oldest request first
@@ -589,6 +783,7 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     uint4 *hxops = reinterpret_cast<uint4 *>(hseal + c.max_batch);
     uint32_t *hxrecs = reinterpret_cast<uint32_t *>(hxops + (uint64_t)c.max_batch * s->extra_ops);
     uint2 *hrtab = reinterpret_cast<uint2 *>(hxrecs + (uint64_t)c.max_batch * s->extra_recs);
+    uint32_t *hctab = reinterpret_cast<uint32_t *>(hrtab + (uint64_t)c.max_batch * c.max_horizon);
     std::vector<gp_circuit> circ;
     uint32_t nseg = 0;
     uint64_t a_ops = 0, a_recs = 0, a_loc = 0, x_ops = 0, x_recs = 0;
@@ -612,8 +807,19 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         // upload the new cycles into their ring slots
         for (uint64_t id : w.reqs) {
             const Request &r = s->requests.at(id);
-            const CycleInfo &ci = P.cycles[r.cycle];
+            CycleInfo &ci = P.cycles[r.cycle];
+            if (r.reg >= 0) {
+                // a registered cycle is read from its device copy
+                const Registered &g = P.registered[r.reg];
+                ci.src_ops = g.d_ops;
+                ci.src_recs = g.d_recs;
+                ci.src_noise = g.d_noise;
+                continue;
+            }
             const uint32_t slot = r.cycle % s->W;
+            ci.src_ops = P.ring_ops + (uint64_t)slot * c.max_cycle_ops;
+            ci.src_recs = P.ring_recs + (uint64_t)slot * c.max_cycle_recs;
+            ci.src_noise = P.ring_noise + (uint64_t)slot * c.max_cycle_locations;
             if (ci.n_ops)
                 SV_CUDA(cudaMemcpyAsync(P.ring_ops + (uint64_t)slot * c.max_cycle_ops, s->h_stage_ops + (uint64_t)r.stage * c.max_cycle_ops,
                                         ci.n_ops * sizeof(uint4), cudaMemcpyHostToDevice, st));
@@ -632,11 +838,10 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         w.det_off.push_back(0);
         for (uint32_t k = w.c0; k <= w.t_b; k++) {
             const CycleInfo &ci = P.cycles[k];
-            const uint32_t slot = k % s->W;
             SegDesc &d = hseg[nseg++];
-            d.ops = P.ring_ops + (uint64_t)slot * c.max_cycle_ops;
-            d.recs = P.ring_recs + (uint64_t)slot * c.max_cycle_recs;
-            d.noise = P.ring_noise + (uint64_t)slot * c.max_cycle_locations;
+            d.ops = ci.src_ops;
+            d.recs = ci.src_recs;
+            d.noise = ci.src_noise;
             d.n_ops = ci.n_ops;
             d.n_recs = ci.n_recs;
             d.n_loc = ci.n_loc;
@@ -706,7 +911,11 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         // the final window's records-only noise is zero: nothing to check
         sd.n_mech_rec = w.final ? 0u : mech_rec;
         sd.n_rec = w.n_rec;
-        sd.pad[0] = sd.pad[1] = 0;
+        sd.n_cyc = w.t_b - w.c0 + 1u;
+        sd.r_off = (int32_t)(w.c0 + P.H) - (int32_t)w.t_a;
+        sd.r_max = w.t_b - w.t_a;
+        sd.pad[0] = sd.pad[1] = sd.pad[2] = 0;
+        for (uint32_t j = 0; j <= sd.n_cyc; j++) hctab[wins.size() * (s->W + 1u) + j] = (uint32_t)w.det_off[j];
         {
             uint32_t mend = 0;
             for (uint32_t j = 0; j < w.n_rec; j++) {
@@ -721,69 +930,73 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     SV_CUDA(cudaMemcpyAsync(s->d_seg, hseg, nseg * sizeof(SegDesc), cudaMemcpyHostToDevice, st));
     SV_CUDA(cudaMemcpyAsync(s->d_seal, hseal, n_win * sizeof(SealDesc), cudaMemcpyHostToDevice, st));
     SV_CUDA(cudaMemcpyAsync(s->d_rec_tab, hrtab, (size_t)n_win * c.max_horizon * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    SV_CUDA(cudaMemcpyAsync(s->d_cyc_tab, hctab, (size_t)n_win * (s->W + 1u) * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     if (x_ops) SV_CUDA(cudaMemcpyAsync(s->d_extra_ops, hxops, x_ops * sizeof(uint4), cudaMemcpyHostToDevice, st));
     if (x_recs) SV_CUDA(cudaMemcpyAsync(s->d_extra_recs, hxrecs, x_recs * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     SV_CUDA(cudaMemsetAsync(s->d_horizon, 0, n_win * sizeof(uint32_t), st));
     assemble_kernel<<<dim3(nseg, kSegBlocksY), 256, 0, st>>>(s->d_seg, nseg, s->arena_ops, s->arena_recs, s->arena_noise);
     SV_CUDA(cudaGetLastError());
+    const uint64_t t_built = now_ns();
     gp_dem_view view{};
     gp_status cst = gp_compile_batch(s->drv, circ.data(), n_win, s->arena_noise, 1, level, stream, &view);
+    const uint64_t t_compiled = now_ns();
     std::vector<uint32_t> win_status(n_win, GP_OK);
-    uint32_t n_sealed = 0, n_sdet = 0;
+    uint32_t n_pass = 0;
+    for (const Win &w : wins) n_pass = std::max<uint32_t>(n_pass, (uint32_t)w.reqs.size());
+    const uint32_t rs = n_win + 1u;             // entries of one slot's row of starts
+    OutBuf *ob = nullptr;
     if (cst == GP_OK && view.n_edges) {
         const Buffers &B = driver_buffers(s->drv);
         const uint32_t grid = 4u * s->n_sms;
-        seal_flags_kernel<<<grid, 256, 0, st>>>(B, s->d_seal);
         seal_horizon_kernel<<<n_win, 256, 0, st>>>(B, s->d_seal, s->d_rec_tab, c.max_horizon, n_win, s->d_horizon);
+        win_edges_kernel<<<1, 32, 0, st>>>(B, n_win, s->d_win_e0);
         uint32_t launches = 0;
-        launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, st, &launches);
-        seal_write_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->out);
+        for (uint32_t r = 0; r < n_pass; r++) {
+            seal_flags_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->d_cyc_tab, s->W + 1u, r);
+            launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, st, &launches);
+            slot_starts_kernel<<<1, 256, 0, st>>>(B, n_win, s->d_win_e0, r, s->d_starts, s->out.doff);
+            seal_write_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->out, s->d_starts + (size_t)r * rs, r, n_win);
+        }
         SV_CUDA(cudaGetLastError());
-        SV_CUDA(cudaMemcpyAsync(s->h_totals, s->out.totals, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        SV_CUDA(cudaMemcpyAsync(s->h_starts, s->d_starts, (size_t)n_pass * rs * sizeof(uint2), cudaMemcpyDeviceToHost, st));
         SV_CUDA(cudaMemcpyAsync(s->h_horizon, s->d_horizon, n_win * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         SV_CUDA(cudaStreamSynchronize(st));
-        n_sealed = s->h_totals[0];
-        n_sdet = s->h_totals[1];
-        {
-            const gp_status gs = grow_host_out(s, n_sealed + 1, n_sdet + 1);
-            if (gs != GP_OK) cst = gs;
-        }
-        if (cst == GP_OK && n_sealed) {
-            SV_CUDA(cudaMemcpyAsync(s->h_win, s->out.win, n_sealed * 4ull, cudaMemcpyDeviceToHost, st));
-            SV_CUDA(cudaMemcpyAsync(s->h_doff, s->out.doff, n_sealed * 4ull, cudaMemcpyDeviceToHost, st));
-            if (n_sdet) SV_CUDA(cudaMemcpyAsync(s->h_det, s->out.det, n_sdet * 4ull, cudaMemcpyDeviceToHost, st));
-            SV_CUDA(cudaMemcpyAsync(s->h_prob, s->out.prob, n_sealed * 4ull, cudaMemcpyDeviceToHost, st));
-            SV_CUDA(cudaMemcpyAsync(s->h_logodds, s->out.logodds, n_sealed * 4ull, cudaMemcpyDeviceToHost, st));
-            SV_CUDA(cudaMemcpyAsync(s->h_obs, s->out.obs, n_sealed * 8ull, cudaMemcpyDeviceToHost, st));
+        const uint2 tot = s->h_starts[(size_t)(n_pass - 1u) * rs + n_win];
+        const uint64_t n_offs = tot.x + (uint64_t)n_pass * n_win;
+        ob = take_outbuf(s, tot.x, (uint64_t)n_pass * n_win, tot.y);
+        if (!ob) cst = sfail(GP_ERR_CUDA, "cudaMallocHost of a result buffer failed");
+        if (cst == GP_OK) {
+            SV_CUDA(cudaMemcpyAsync(ob->doff, s->out.doff, n_offs * 4ull, cudaMemcpyDeviceToHost, st));
+            if (tot.y) SV_CUDA(cudaMemcpyAsync(ob->det, s->out.det, tot.y * 4ull, cudaMemcpyDeviceToHost, st));
+            if (tot.x) {
+                SV_CUDA(cudaMemcpyAsync(ob->prob, s->out.prob, tot.x * 4ull, cudaMemcpyDeviceToHost, st));
+                SV_CUDA(cudaMemcpyAsync(ob->logodds, s->out.logodds, tot.x * 4ull, cudaMemcpyDeviceToHost, st));
+                SV_CUDA(cudaMemcpyAsync(ob->obs, s->out.obs, tot.x * 8ull, cudaMemcpyDeviceToHost, st));
+            }
             SV_CUDA(cudaStreamSynchronize(st));
         }
         for (uint32_t w = 0; w < n_win; w++)
             if (s->h_horizon[w]) win_status[w] = GP_ERR_HORIZON;
     }
-    // hand the sealed hyperedges to their requests
-    if (cst == GP_OK) {
-        for (uint32_t i = 0; i < n_sealed; i++) {
-            const uint32_t w = s->h_win[i];
-            if (w >= n_win || win_status[w] != GP_OK) continue;
+    const uint64_t t_selected = now_ns();
+    // every request's hyperedges are one slice of the step buffer
+    if (cst == GP_OK && ob) {
+        for (uint32_t w = 0; w < n_win; w++) {
+            if (win_status[w] != GP_OK) continue;
             const Win &W_ = wins[w];
-            const Patch &P = s->patches[W_.patch];
-            const uint32_t d0 = s->h_doff[i], d1 = (i + 1 < n_sealed) ? s->h_doff[i + 1] : n_sdet;
-            uint32_t owner;
-            if (d1 > d0) {
-                const uint64_t local = s->h_det[d0] - P.cycles[W_.c0].det_base;
-                const uint32_t k = W_.c0 + (uint32_t)(std::upper_bound(W_.det_off.begin(), W_.det_off.end(), local) -
-                                                      W_.det_off.begin()) - 1u;
-                owner = std::min(k + P.H, W_.t_b);
-            } else {
-                owner = W_.t_b;
+            for (uint32_t r = 0; r < (uint32_t)W_.reqs.size(); r++) {
+                const uint2 a = s->h_starts[(size_t)r * rs + w], z = s->h_starts[(size_t)r * rs + w + 1];
+                Request &q = s->requests.at(W_.reqs[r]);
+                q.buf = ob;
+                ob->refs++;
+                q.n_edges = z.x - a.x;
+                q.n_det = z.y - a.y;
+                q.det_offsets = ob->doff + a.x + r * n_win + w;
+                q.det_idx = ob->det + a.y;
+                q.obs = ob->obs + a.x;
+                q.prob = ob->prob + a.x;
+                q.logodds = ob->logodds + a.x;
             }
-            if (owner < W_.t_a) continue;       // sealed by an earlier step (not selected)
-            Request &r = s->requests.at(W_.reqs[owner - W_.t_a]);
-            r.det_idx.insert(r.det_idx.end(), s->h_det + d0, s->h_det + d1);
-            r.det_offsets.push_back((uint32_t)r.det_idx.size());
-            r.obs.push_back(s->h_obs[i]);
-            r.prob.push_back(s->h_prob[i]);
-            r.logodds.push_back(s->h_logodds[i]);
         }
     }
     const uint64_t t_done = now_ns();
@@ -794,7 +1007,7 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         for (uint64_t id : W_.reqs) {
             Request &r = s->requests.at(id);
             finish(s, r, cst != GP_OK ? cst : (gp_status)win_status[w], t_done);
-            s->free_stage.push_back(r.stage);
+            if (r.reg < 0) s->free_stage.push_back(r.stage);
             P.pending.pop_front();
             s->n_pending--;
             done++;
@@ -802,7 +1015,58 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         P.next_step = W_.t_b + 1;
     }
     if (n_completed) *n_completed = done;
+    s->times[0] = (float)(t_built - t_start) * 1e-3f;
+    s->times[1] = (float)(t_compiled - t_built) * 1e-3f;
+    s->times[2] = (float)(t_selected - t_compiled) * 1e-3f;
+    s->times[3] = (float)(t_done - t_selected) * 1e-3f;
+    gp_last_timing(s->drv, s->times + 4);
     return cst;
+}
+
+gp_status gp_server_last_timing(const gp_server *s, float times_us[8]) {
+    if (!s || !times_us) return sfail(GP_ERR_INVALID, "null argument");
+    for (int i = 0; i < 8; i++) times_us[i] = s->times[i];
+    return GP_OK;
+}
+
+gp_status gp_server_submit_registered_many(gp_server *s, uint32_t n, const uint32_t *patches,
+                                           const uint32_t *cycle_ids, const uint8_t *finals,
+                                           const uint64_t *t_arrival_ns, uint64_t *requests, uint32_t *n_done) {
+    if (!s || !n_done || (n && (!patches || !cycle_ids || !requests))) return sfail(GP_ERR_INVALID, "null argument");
+    *n_done = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const gp_status st = gp_server_submit_registered(s, patches[i], cycle_ids[i], finals ? finals[i] : 0,
+                                                         t_arrival_ns ? t_arrival_ns[i] : 0, &requests[i]);
+        if (st != GP_OK) return st;
+        *n_done = i + 1;
+    }
+    return GP_OK;
+}
+
+gp_status gp_server_drain(gp_server *s, uint32_t cap, uint64_t *ids, uint64_t *t_arrival_ns, uint64_t *t_done_ns,
+                          uint32_t *n_edges, int32_t *status, uint32_t *n) {
+    if (!s || !n || (cap && (!ids || !t_arrival_ns || !t_done_ns || !n_edges || !status)))
+        return sfail(GP_ERR_INVALID, "null argument");
+    const uint32_t k = (uint32_t)std::min<size_t>(cap, s->completed.size());
+    for (uint32_t i = 0; i < k; i++) {
+        auto it = s->requests.find(s->completed[i]);
+        ids[i] = s->completed[i];
+        if (it == s->requests.end()) {
+            t_arrival_ns[i] = t_done_ns[i] = 0;
+            n_edges[i] = 0;
+            status[i] = GP_ERR_INVALID;
+            continue;
+        }
+        t_arrival_ns[i] = it->second.t_arrival;
+        t_done_ns[i] = it->second.t_done;
+        n_edges[i] = it->second.n_edges;
+        status[i] = (int32_t)it->second.status;
+        drop_result(it->second);
+        s->requests.erase(it);
+    }
+    s->completed.erase(s->completed.begin(), s->completed.begin() + k);
+    *n = k;
+    return GP_OK;
 }
 
 gp_status gp_server_completed(gp_server *s, uint64_t *ids, uint32_t cap, uint32_t *n) {
@@ -823,13 +1087,13 @@ gp_status gp_server_result(const gp_server *s, uint64_t request, gp_sealed_view 
     out->patch = r.patch;
     out->cycle = r.cycle;
     out->status = r.status;
-    out->n_edges = (uint32_t)r.prob.size();
-    out->n_det_entries = r.det_idx.size();
-    out->det_offsets = r.det_offsets.data();
-    out->det_idx = r.det_idx.data();
-    out->obs_mask = r.obs.data();
-    out->prob = r.prob.data();
-    out->logodds = r.logodds.data();
+    out->n_edges = r.n_edges;
+    out->n_det_entries = r.n_det;
+    out->det_offsets = r.det_offsets;
+    out->det_idx = r.det_idx;
+    out->obs_mask = reinterpret_cast<const uint64_t *>(r.obs);
+    out->prob = r.prob;
+    out->logodds = r.logodds;
     out->t_arrival_ns = r.t_arrival;
     out->t_done_ns = r.t_done;
     return GP_OK;
@@ -839,6 +1103,7 @@ gp_status gp_server_release(gp_server *s, uint64_t request) {
     if (!s) return sfail(GP_ERR_INVALID, "null argument");
     auto it = s->requests.find(request);
     if (it == s->requests.end() || !it->second.done) return sfail(GP_ERR_INVALID, "unknown or pending request");
+    drop_result(it->second);
     s->requests.erase(it);
     return GP_OK;
 }

@@ -25,6 +25,8 @@ EXPORTED = [
     "gp_last_timing", "gp_last_launch_count", "gp_last_error", "gp_pmerge_noalloc",
     "gp_server_create", "gp_server_destroy", "gp_server_open_patch", "gp_server_close_patch",
     "gp_server_submit", "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release",
+    "gp_server_register_cycle", "gp_server_submit_registered", "gp_server_submit_registered_many",
+    "gp_server_drain", "gp_server_last_timing",
 ]
 
 
@@ -130,8 +132,15 @@ def load(path: str = LIB_PATH):
         lib.gp_server_completed.argtypes = [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32)]
         lib.gp_server_result.argtypes = [vp, u64, ctypes.POINTER(GpSealedView)]
         lib.gp_server_release.argtypes = [vp, u64]
+        lib.gp_server_register_cycle.argtypes = [vp, u32, ctypes.POINTER(GpCircuit), vp, ctypes.POINTER(u32)]
+        lib.gp_server_submit_registered.argtypes = [vp, u32, u32, i32, u64, ctypes.POINTER(u64)]
+        lib.gp_server_submit_registered_many.argtypes = [vp, u32, vp, vp, vp, vp, vp, ctypes.POINTER(u32)]
+        lib.gp_server_drain.argtypes = [vp, u32, vp, vp, vp, vp, vp, ctypes.POINTER(u32)]
+        lib.gp_server_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         for name in ("gp_server_create", "gp_server_open_patch", "gp_server_close_patch", "gp_server_submit",
-                     "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release"):
+                     "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release",
+                     "gp_server_register_cycle", "gp_server_submit_registered",
+                     "gp_server_submit_registered_many", "gp_server_drain", "gp_server_last_timing"):
             getattr(lib, name).restype = i32
         lib.gp_last_error.argtypes = []
         lib.gp_last_error.restype = ctypes.c_char_p

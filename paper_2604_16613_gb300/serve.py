@@ -111,11 +111,72 @@ class Server:
                                                int(t_arrival_ns), ctypes.byref(rid)))
         return rid.value
 
+    def register_cycle(self, patch: int, block: dict) -> int:
+        """Register a cycle the patch repeats; returns its id."""
+        n_qubits, n_obs = self._patches[patch]
+        ops = np.ascontiguousarray(block["ops"], dtype=np.uint32)
+        recs = np.ascontiguousarray(block["recs"], dtype=np.uint32)
+        noise = np.ascontiguousarray(block["noise"], dtype=np.float32)
+        g = native.GpCircuit(ops.ctypes.data if ops.size else None, ops.shape[0],
+                             recs.ctypes.data if recs.size else None, recs.size, n_qubits,
+                             int(block["n_detectors"]), n_obs, int(block["n_locations"]))
+        cid = ctypes.c_uint32()
+        native.check(self.lib.gp_server_register_cycle(self.handle, int(patch), ctypes.byref(g),
+                                                       noise.ctypes.data if noise.size else None,
+                                                       ctypes.byref(cid)))
+        return cid.value
+
+    def submit_registered(self, patch: int, cycle_id: int, final: bool = False, t_arrival_ns: int = 0) -> int:
+        rid = ctypes.c_uint64()
+        native.check(self.lib.gp_server_submit_registered(self.handle, int(patch), int(cycle_id), int(bool(final)),
+                                                          int(t_arrival_ns), ctypes.byref(rid)))
+        return rid.value
+
+    def submit_registered_many(self, patches, cycle_ids, finals=None, t_arrival_ns=None,
+                               stop_when_full: bool = False) -> np.ndarray:
+        """Submit many registered cycles (numpy arrays); returns the ids of
+        those queued.  With ``stop_when_full`` a full queue ends the call
+        early instead of raising."""
+        p = np.ascontiguousarray(patches, dtype=np.uint32)
+        c = np.ascontiguousarray(cycle_ids, dtype=np.uint32)
+        f = None if finals is None else np.ascontiguousarray(finals, dtype=np.uint8)
+        t = None if t_arrival_ns is None else np.ascontiguousarray(t_arrival_ns, dtype=np.uint64)
+        ids = np.zeros(p.size, dtype=np.uint64)
+        n = ctypes.c_uint32()
+        code = self.lib.gp_server_submit_registered_many(
+            self.handle, p.size, p.ctypes.data, c.ctypes.data, None if f is None else f.ctypes.data,
+            None if t is None else t.ctypes.data, ids.ctypes.data, ctypes.byref(n))
+        if not (stop_when_full and code == native.GP_ERR_CAPACITY):
+            native.check(code)
+        return ids[:n.value]
+
+    def drain(self, cap: int = 65536) -> dict:
+        """Finished requests (released): ids, arrival and completion times,
+        hyperedges delivered, status."""
+        ids = np.zeros(cap, np.uint64)
+        ta = np.zeros(cap, np.uint64)
+        td = np.zeros(cap, np.uint64)
+        ne = np.zeros(cap, np.uint32)
+        st = np.zeros(cap, np.int32)
+        n = ctypes.c_uint32()
+        native.check(self.lib.gp_server_drain(self.handle, cap, ids.ctypes.data, ta.ctypes.data, td.ctypes.data,
+                                              ne.ctypes.data, st.ctypes.data, ctypes.byref(n)))
+        k = n.value
+        return dict(ids=ids[:k], t_arrival_ns=ta[:k], t_done_ns=td[:k], n_edges=ne[:k], status=st[:k])
+
     def step(self, level="L2", stream=None) -> int:
         n = ctypes.c_uint32()
         s = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
         native.check(self.lib.gp_server_step(self.handle, native.LEVELS[level], s, ctypes.byref(n)))
         return n.value
+
+    def last_timing(self) -> list[float]:
+        """Microseconds of the last step: host build, compile, select,
+        hand-out, then the compile's device stages (lowering, stage 1,
+        grouping, compaction)."""
+        a = (ctypes.c_float * 8)()
+        native.check(self.lib.gp_server_last_timing(self.handle, a))
+        return list(a)
 
     def completed(self, cap: int = 4096) -> list[int]:
         out = []
