@@ -15,18 +15,19 @@
 // candidate list holds every qubit whose planes may be non-zero (the active
 // qubits of the last layer plus the qubits the last layer's gates and
 // measurements touched); per layer L two barrier-separated phases run:
-//   A  each candidate whose planes are non-zero stays active; a half-warp
-//      evaluates the mask words of the noise rows touching it after the gates
-//      of L and before the gates of L+1 (the planes hold the state between
-//      the two), one Pauli component per lane.  A two-qubit row is listed
-//      under both of its qubits and evaluated from the first active one.
+//   A  a candidate whose planes are non-zero is active (marked in a per-qubit
+//      state byte); a half-warp evaluates the mask words of the noise rows
+//      touching it after the gates of L and before the gates of L+1 (the
+//      planes hold the state between the two), one Pauli component per lane.
+//      A two-qubit row is listed under both of its qubits and evaluated from
+//      the first active one.
 //   B  the gates of L on active qubits are undone backward: H swaps the
 //      planes, S: x ^= z, CX(c,t): x_c ^= x_t and z_t ^= z_c, CZ(a,b):
 //      x_a ^= z_b and x_b ^= z_a; measurements XOR in the column's detector
 //      bits; resets clear the planes after checking that the detectors
-//      commute with them.  A two-qubit gate whose partner was inactive makes
-//      the partner a candidate, and so does a measurement of the column on
-//      an inactive qubit.
+//      commute with them.  The next candidate list is built here: the active
+//      qubits, the inactive partners of their two-qubit gates, and inactive
+//      qubits the column measures in L.
 // A component's mask word is the XOR of the planes its Pauli names (Y = X xor
 // Z, two-qubit terms combine both qubits: Sec. 2.3.4).  Non-zero words become
 // 16-byte records {mechanism, column, word} that every warp writes straight to
@@ -54,14 +55,15 @@ constexpr int kSegCache = 256;      // layer segments cached for the producer
 constexpr int kMaxBufs = 4;         // window ring slots at most
 
 struct Smem {
-    unsigned long long *xs, *zs;
+    ulonglong2 *pl;                 // per qubit: {X plane, Z plane}
     unsigned long long *ent_w;      // entry words (merged per measurement)
     uint4 *segc;                    // layer segments [seg_lo, seg_lo + kSegCache)
     uint32_t *ent_m;                // entry measurement (sorted)
     uint32_t *ent_l;                // entry layer
     uint32_t *ent_q;                // entry qubit | x-basis << 31
     uint16_t *cand0, *cand1;        // candidate lists (ping-pong)
-    unsigned char *bits;            // per qubit: on the list being built
+    unsigned char *bits;            // per qubit: kActive (set in phase A), kAdded
+                                    // (put on the next list in phase B) or 0
     unsigned char *win;             // window buffers
 };
 
@@ -88,9 +90,8 @@ __host__ __device__ inline uint32_t window_index_bytes(uint32_t maxq) {
 __device__ __forceinline__ Smem carve(unsigned char *base, uint32_t maxq) {
     const uint32_t q8 = round8(maxq);
     Smem s;
-    s.xs = reinterpret_cast<unsigned long long *>(base);
-    s.zs = s.xs + q8;
-    s.ent_w = s.zs + q8;
+    s.pl = reinterpret_cast<ulonglong2 *>(base);
+    s.ent_w = reinterpret_cast<unsigned long long *>(s.pl + q8);
     s.segc = reinterpret_cast<uint4 *>(s.ent_w + kMaxEntries);
     s.ent_m = reinterpret_cast<uint32_t *>(s.segc + kSegCache);
     s.ent_l = s.ent_m + kMaxEntries;
@@ -103,6 +104,8 @@ __device__ __forceinline__ Smem carve(unsigned char *base, uint32_t maxq) {
 }
 
 __device__ __forceinline__ uint16_t *cand_list(const Smem &s, uint32_t i) { return i ? s.cand1 : s.cand0; }
+
+constexpr unsigned char kAdded = 1, kActive = 2;
 
 // XOR of the entry words recorded for measurement m (entries sorted by m)
 __device__ __forceinline__ unsigned long long meas_word(const Smem &s, uint32_t n_ent, uint32_t m) {
@@ -131,8 +134,7 @@ struct Shared {
     unsigned long long mbar[kMaxBufs];
     Window desc[kMaxBufs];
     uint32_t item, bail, nent, lmax, tmo;
-    uint32_t n_act[2];      // per candidate list: qubits kept in phase A
-    uint32_t n_new[2];      // ... and qubits added in phase B
+    uint32_t n_cand[2];     // length of each candidate list (built in phase B)
 };
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
@@ -150,6 +152,8 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
     constexpr uint32_t NCT = NCW * 32;             // consumer threads
     const Params &P = *B.params;
     const uint32_t level = P.level, rec_cap = P.rec_cap;
+    // Pauli components a level keeps (Table tab:correlation-level)
+    const uint32_t nc_dep1 = level == 0u ? 2u : 3u, nc_dep2 = level == 0u ? 6u : (level == 1u ? 10u : 15u);
     const uint32_t lane = threadIdx.x & 31u, l16 = lane & 15u, half = lane >> 4;
     const uint32_t warp = threadIdx.x >> 5;
     const bool producer = warp == NW - 1;
@@ -210,8 +214,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
             sh.bail = (*(volatile uint32_t *)&B.status->code) != 0u;
             sh.nent = 0;
             sh.lmax = 0;
-            sh.n_act[0] = sh.n_act[1] = 0;
-            sh.n_new[0] = sh.n_new[1] = 0;
+            sh.n_cand[0] = sh.n_cand[1] = 0;
         }
         __syncthreads();
         const uint32_t item = sh.item;
@@ -227,8 +230,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
         seg_lo = 0xFFFFFFFFu;             // the segment cache belongs to the last column
 
         for (uint32_t q = threadIdx.x; q < nq; q += NT) {
-            s.xs[q] = 0ull;
-            s.zs[q] = 0ull;
+            s.pl[q] = make_ulonglong2(0ull, 0ull);
             s.bits[q] = 0;
         }
         // (measurement, word) entries of this column (Eq. init-slp)
@@ -389,78 +391,85 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
             return sh.desc[slot];
         };
 
+        // mask word of component l16 of noise row r seen from candidate q (0
+        // for an empty slot, a component the level drops, or a two-qubit row
+        // whose first qubit is active: that one evaluates it)
+        auto row_word = [&](uint2 r, uint32_t q) -> unsigned long long {
+            const uint32_t kind = row_kind(r);
+            if (kind < K_XERR) return 0ull;
+            const uint32_t ra = row_a(r), rb = row_b(r);
+            const bool two = kind == K_DEP2;
+            const ulonglong2 pa = s.pl[ra];
+            const ulonglong2 pb = two ? s.pl[rb] : make_ulonglong2(0ull, 0ull);
+            if (two && q == rb && (pa.x | pa.y) != 0ull) return 0ull;
+            const uint32_t nc = two ? nc_dep2 : (kind == K_DEP1 ? nc_dep1 : 1u);
+            if (l16 >= nc) return 0ull;
+            const unsigned long long codes = two ? 0x0EBF7D639CA25184ull : (kind == K_DEP1 ? 0x321ull : (kind == K_XERR ? 1ull : 2ull));
+            const uint32_t code = (uint32_t)(codes >> (4u * l16)) & 0xFu;
+            return ((code & 1u) ? pa.x : 0ull) ^ ((code & 2u) ? pa.y : 0ull) ^ ((code & 4u) ? pb.x : 0ull) ^
+                   ((code & 8u) ? pb.y : 0ull);
+        };
+        // write the warp's non-zero words as records (warp-uniform call)
+        auto emit = [&](uint2 r, unsigned long long w) {
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, w != 0ull);
+            if (m == 0u) return;
+            const uint32_t cnt = (uint32_t)__popc(m);
+            if (!warp_room(cnt)) return;
+            if (w != 0ull) {
+                const uint32_t mech = mech_base + r.y + l16;
+                B.records[ck_pos + __popc(m & lt_mask)] = make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+                atomicAdd(&B.mech_cnt[mech], 1u);
+            }
+            ck_pos += cnt;
+        };
+
         // phase A for one candidate list (consumer warps): keep the non-zero
         // candidates (appended to list `out`) and emit the mask words of their
         // noise rows; with `after` false only the before-gate lists are read
         // (step -1).  The two half-warps of a warp take two candidates in
         // lockstep, so ballots span the whole warp.
-        auto phase_a = [&](const Window &v, const uint16_t *in, uint32_t n_in, uint32_t out, bool after,
-                           bool check_initial) {
-            uint16_t *outl = cand_list(s, out);
+        auto phase_a = [&](const Window &v, const uint16_t *in, uint32_t n_in, bool after, bool check_initial) {
             warp_prefetch();
             for (uint32_t base = 2u * warp; base < n_in; base += 2u * NCW) {
                 const uint32_t c = base + half;
                 const bool valid = c < n_in;
                 const uint32_t q = valid ? in[c] : 0u;
-                const unsigned long long xq = valid ? s.xs[q] : 0ull, zq = valid ? s.zs[q] : 0ull;
-                const bool act = (xq | zq) != 0ull;
-                if (valid && !act && l16 == 0u) s.bits[q] = 0;
-                const unsigned am = __ballot_sync(0xFFFFFFFFu, act && l16 == 0u);
-                if (am) {
-                    uint32_t abase = 0;
-                    if (lane == 0u) abase = atomicAdd(&sh.n_act[out], (uint32_t)__popc(am));
-                    abase = __shfl_sync(0xFFFFFFFFu, abase, 0);
-                    if (act && l16 == 0u) {
-                        outl[abase + __popc(am & lt_mask)] = (uint16_t)q;
-                        if (check_initial && zq != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, 0xFFFFFFFFu, gcol);
-                    }
+                // the planes and the list offsets load together (the offsets
+                // do not wait for the activity test)
+                const ulonglong2 pq = s.pl[q];
+                uint32_t a0 = 0, a1 = 0;
+                if (after) { a0 = v.aoff[q]; a1 = v.aoff[q + 1u]; }
+                const uint32_t b0 = v.boff[q], b1 = v.boff[q + 1u];
+                const bool act = valid && (pq.x | pq.y) != 0ull;
+                if (valid && l16 == 0u) {
+                    s.bits[q] = act ? kActive : (unsigned char)0;
+                    if (check_initial && act && pq.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, 0xFFFFFFFFu, gcol);
                 }
-                uint32_t a0 = 0, na = 0, b0 = 0, n = 0;
-                if (act) {
-                    if (after) { a0 = v.aoff[q]; na = v.aoff[q + 1u] - a0; }
-                    b0 = v.boff[q];
-                    n = na + (v.boff[q + 1u] - b0);
-                }
+                const uint32_t na = act ? a1 - a0 : 0u;
+                const uint32_t n = act ? na + (b1 - b0) : 0u;
                 const uint32_t nmax = max(n, __shfl_xor_sync(0xFFFFFFFFu, n, 16));
-                for (uint32_t i = 0; i < nmax; i++) {
-                    bool has = i < n;
-                    uint2 r = make_uint2(0u, 0u);
-                    if (has) r = v.lists[i < na ? a0 + i : v.n_after + b0 + (i - na)];
-                    const uint32_t kind = row_kind(r), ra = row_a(r), rb = row_b(r);
-                    // a two-qubit row is evaluated from its first qubit when
-                    // that one is active
-                    if (has && kind == K_DEP2 && q == rb && (s.xs[ra] | s.zs[ra]) != 0ull) has = false;
-                    unsigned long long w = 0ull;
-                    if (has && l16 < n_comp(kind, level)) {
-                        const uint32_t code = comp_planes(kind, l16);
-                        if (code & 1u) w ^= s.xs[ra];
-                        if (code & 2u) w ^= s.zs[ra];
-                        if (code & 4u) w ^= s.xs[rb];
-                        if (code & 8u) w ^= s.zs[rb];
-                    }
-                    const unsigned m = __ballot_sync(0xFFFFFFFFu, w != 0ull);
-                    if (m == 0u) continue;
-                    const uint32_t cnt = (uint32_t)__popc(m);
-                    if (!warp_room(cnt)) continue;
-                    if (w != 0ull) {
-                        const uint32_t mech = mech_base + r.y + l16;
-                        B.records[ck_pos + __popc(m & lt_mask)] =
-                            make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
-                        atomicAdd(&B.mech_cnt[mech], 1u);
-                    }
-                    ck_pos += cnt;
+                // two rows per iteration, their loads issued together
+                for (uint32_t i = 0; i < nmax; i += 2u) {
+                    uint2 r0 = make_uint2(0u, 0u), r1 = make_uint2(0u, 0u);
+                    if (i < n) r0 = v.lists[i < na ? a0 + i : v.n_after + b0 + (i - na)];
+                    if (i + 1u < n) r1 = v.lists[i + 1u < na ? a0 + i + 1u : v.n_after + b0 + (i + 1u - na)];
+                    const unsigned long long w0 = row_word(r0, q), w1 = row_word(r1, q);
+                    emit(r0, w0);
+                    emit(r1, w1);
                 }
             }
         };
-        // append the qubits of the lanes with `add` set to the list being
-        // built (one shared atomic per warp)
-        auto append_new = [&](uint16_t *list, uint32_t n_keep, uint32_t o, bool add, uint32_t q) {
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, add);
-            if (m == 0u) return;
+        // append up to two qubits per lane to the list being built (one
+        // shared atomic per warp)
+        auto append2 = [&](uint16_t *list, uint32_t o, bool add_a, uint32_t qa, bool add_b, uint32_t qb) {
+            const unsigned ma = __ballot_sync(0xFFFFFFFFu, add_a), mb = __ballot_sync(0xFFFFFFFFu, add_b);
+            const uint32_t na = (uint32_t)__popc(ma), tot = na + (uint32_t)__popc(mb);
+            if (tot == 0u) return;
             uint32_t nb = 0;
-            if (lane == 0u) nb = atomicAdd(&sh.n_new[o], (uint32_t)__popc(m));
+            if (lane == 0u) nb = atomicAdd(&sh.n_cand[o], tot);
             nb = __shfl_sync(0xFFFFFFFFu, nb, 0);
-            if (add) list[n_keep + nb + __popc(m & lt_mask)] = (uint16_t)q;
+            if (add_a) list[nb + __popc(ma & lt_mask)] = (uint16_t)qa;
+            if (add_b) list[nb + na + __popc(mb & lt_mask)] = (uint16_t)qb;
         };
 
         // ---- backward wave over the layers ---------------------------------
@@ -483,55 +492,81 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
             }
             const Window v = wait(L);
             // phase A
-            if (!producer && !sh.tmo) phase_a(v, cand_list(s, p), n_in, p ^ 1u, true, false);
+            const uint16_t *const in_list = cand_list(s, p);
+            if (!producer && !sh.tmo) phase_a(v, in_list, n_in, true, false);
             __syncthreads();
             if (sh.tmo) { timed_out = true; break; }
             // phase B: the gates of L undone
             const uint32_t o = p ^ 1u;
-            const uint32_t n_keep = sh.n_act[o];
-            uint16_t *const keep = cand_list(s, o);
-            if (threadIdx.x == 0) { sh.n_act[p] = 0; sh.n_new[p] = 0; }
+            uint16_t *const next = cand_list(s, o);
+            if (threadIdx.x == 0) sh.n_cand[p] = 0;
             if (!producer) {
-                for (uint32_t base = 0; base < n_keep; base += NCT) {
+                for (uint32_t base = 0; base < n_in; base += NCT) {
                     const uint32_t i = base + threadIdx.x;
-                    uint32_t partner = kNone;
-                    if (i < n_keep) {
-                        const uint32_t q = keep[i];
+                    uint32_t partner = kNone, q = 0;
+                    bool keep_q = false;
+                    if (i < n_in) q = in_list[i];
+                    if (i < n_in && s.bits[q] == kActive) {
+                        keep_q = true;
                         const uint32_t g = v.gate[q];
                         const uint32_t k = g >> 28, pay = g & 0x0FFFFFFFu;
                         switch (k) {
-                        case K_H: { const unsigned long long t = s.xs[q]; s.xs[q] = s.zs[q]; s.zs[q] = t; break; }
-                        case K_S: s.xs[q] ^= s.zs[q]; break;
-                        case GV_CX_C: s.xs[q] ^= s.xs[pay]; s.zs[pay] ^= s.zs[q]; partner = pay; break;
-                        case GV_CX_T:
-                            if (s.bits[pay]) break;               // undone from the active control
-                            s.xs[pay] ^= s.xs[q]; s.zs[q] ^= s.zs[pay]; partner = pay; break;
-                        case GV_CZ_B:
-                            if (s.bits[pay]) break;               // undone from the active first qubit
-                            // fall through
-                        case GV_CZ_A: {
-                            const unsigned long long za = s.zs[q], zb = s.zs[pay];
-                            s.xs[q] ^= zb;
-                            s.xs[pay] ^= za;
+                        case K_H: { const ulonglong2 t = s.pl[q]; s.pl[q] = make_ulonglong2(t.y, t.x); break; }
+                        case K_S: { ulonglong2 t = s.pl[q]; t.x ^= t.y; s.pl[q] = t; break; }
+                        case GV_CX_C: {
+                            ulonglong2 c_ = s.pl[q], t_ = s.pl[pay];
+                            c_.x ^= t_.x;
+                            t_.y ^= c_.y;
+                            s.pl[q] = c_;
+                            s.pl[pay] = t_;
                             partner = pay;
                             break;
                         }
-                        case K_R: case K_M: case K_MR:
-                            if (s.zs[q] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, (uint32_t)L, gcol);
-                            if (k != K_M) { s.xs[q] = 0ull; s.zs[q] = 0ull; }
-                            if (k != K_R) s.xs[q] ^= meas_word(s, n_ent, pay);
+                        case GV_CX_T: {
+                            if (s.bits[pay] == kActive) break;    // undone from the active control
+                            ulonglong2 c_ = s.pl[pay], t_ = s.pl[q];
+                            c_.x ^= t_.x;
+                            t_.y ^= c_.y;
+                            s.pl[pay] = c_;
+                            s.pl[q] = t_;
+                            partner = pay;
                             break;
-                        case K_RX: case K_MX: case K_MRX:
-                            if (s.xs[q] != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, (uint32_t)L, gcol);
-                            if (k != K_MX) { s.xs[q] = 0ull; s.zs[q] = 0ull; }
-                            if (k != K_RX) s.zs[q] ^= meas_word(s, n_ent, pay);
+                        }
+                        case GV_CZ_B:
+                            if (s.bits[pay] == kActive) break;    // undone from the active first qubit
+                            // fall through
+                        case GV_CZ_A: {
+                            ulonglong2 a_ = s.pl[q], b_ = s.pl[pay];
+                            const unsigned long long za = a_.y, zb = b_.y;
+                            a_.x ^= zb;
+                            b_.x ^= za;
+                            s.pl[q] = a_;
+                            s.pl[pay] = b_;
+                            partner = pay;
                             break;
+                        }
+                        case K_R: case K_M: case K_MR: {
+                            ulonglong2 t = s.pl[q];
+                            if (t.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, (uint32_t)L, gcol);
+                            if (k != K_M) t = make_ulonglong2(0ull, 0ull);
+                            if (k != K_R) t.x ^= meas_word(s, n_ent, pay);
+                            s.pl[q] = t;
+                            break;
+                        }
+                        case K_RX: case K_MX: case K_MRX: {
+                            ulonglong2 t = s.pl[q];
+                            if (t.x != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, b, (uint32_t)L, gcol);
+                            if (k != K_MX) t = make_ulonglong2(0ull, 0ull);
+                            if (k != K_RX) t.y ^= meas_word(s, n_ent, pay);
+                            s.pl[q] = t;
+                            break;
+                        }
                         default: break;
                         }
                     }
-                    const bool add = partner != kNone && !s.bits[partner];
-                    if (add) s.bits[partner] = 1;
-                    append_new(keep, n_keep, o, add, partner);
+                    const bool add = partner != kNone && s.bits[partner] == 0;
+                    if (add) s.bits[partner] = kAdded;
+                    append2(next, o, keep_q, q, add, partner);
                 }
             }
             // measurements of the column at L on inactive qubits
@@ -553,19 +588,19 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
                             const uint32_t qv = s.ent_q[i];
                             q = qv & 0x7FFFFFFFu;
                             // an active qubit had the word applied by its gate above
-                            if (w != 0ull && !s.bits[q]) {
-                                if (qv >> 31) s.zs[q] ^= w; else s.xs[q] ^= w;
-                                s.bits[q] = 1;
+                            if (w != 0ull && s.bits[q] == 0) {
+                                if (qv >> 31) s.pl[q].y ^= w; else s.pl[q].x ^= w;
+                                s.bits[q] = kAdded;
                                 add = true;
                             }
                         }
-                        append_new(keep, n_keep, o, add, q);
+                        append2(next, o, add, q, false, 0u);
                     }
                 }
             }
             cur = lo;
             __syncthreads();
-            n_in = sh.n_act[o] + sh.n_new[o];
+            n_in = sh.n_cand[o];
             p = o;
             if (L == 0) break;
             if (n_in == 0u && (uint32_t)(L - 1) < lmin) { stopped = true; break; }
@@ -576,7 +611,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
             // initial state
             L = -1;
             const Window v = wait(-1);
-            if (!producer && !sh.tmo) phase_a(v, cand_list(s, p), n_in, p ^ 1u, false, true);
+            if (!producer && !sh.tmo) phase_a(v, cand_list(s, p), n_in, false, true);
         }
         // windows published ahead of an early stop land before their slots
         // are reused
