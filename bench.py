@@ -231,18 +231,22 @@ def batch_section(args, world: int) -> dict:
 
 def serve_section(args) -> dict:
     """Continuous serving: ``--serve-patches`` patches, each issuing one
-    per-cycle request as a Poisson process of rate ``--serve-rate`` for
-    ``--serve-seconds``; patch mix rotated surface code d in {5, 7, ..., 25}
-    (uniform) and [[144,12,12]] bivariate bicycle memory at 3:1, p = 1e-3,
-    level L2.  Every patch registers its first and its steady-state syndrome
-    cycle once and repeats the latter.  One host thread submits the requests
-    that have arrived, steps the server (one batched launch over the windows
-    of all patches with pending cycles, up to ``--serve-k`` cycles each) and
-    drains the finished requests.  Latency = completion of the step that
-    delivered a request - its scheduled arrival (both on the steady clock)."""
+    per-cycle request as a Poisson process, for ``--serve-seconds`` at each
+    per-patch rate of ``--serve-rates``; patch mix rotated surface code d in
+    {5, 7, ..., 25} (uniform) and [[144,12,12]] bivariate bicycle memory at
+    3:1, p = 1e-3, level L2.  Every patch registers its first and its
+    steady-state syndrome cycle once and repeats the latter.  One host thread
+    submits the requests that have arrived, steps the server (one batched
+    launch over the windows of all patches with pending cycles, up to
+    ``--serve-k`` cycles each) and drains the finished requests.  Latency =
+    completion of the step that delivered a request - its scheduled arrival
+    (both on the steady clock).  A load the server cannot sustain shows as a
+    completed rate below the offered one and a latency that grows with the
+    run's length."""
     from paper_2604_16613_gb300 import circuits as C
     from paper_2604_16613_gb300.serve import Server
-    P, rate, T, K = args.serve_patches, args.serve_rate, args.serve_seconds, args.serve_k
+    P, T, K = args.serve_patches, args.serve_seconds, args.serve_k
+    rates = [float(r) for r in args.serve_rates.split(",") if r]
     ds = list(range(5, 27, 2))
     kinds = [("bb", 0) if i % 4 == 3 else ("surface", ds[(i - i // 4) % len(ds)]) for i in range(P)]
     tmpl = {}
@@ -268,57 +272,64 @@ def serve_section(args) -> dict:
     while srv.step():
         pass
     srv.drain()
-    # Poisson schedule
-    rng = np.random.default_rng(5)
-    ev_t, ev_p = [], []
-    for i in range(P):
-        t = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * T * 1.3) + 32))
-        t = t[t < T]
-        ev_t.append(t)
-        ev_p.append(np.full(t.size, i, np.int64))
-    ev_t, ev_p = np.concatenate(ev_t), np.concatenate(ev_p)
-    order = np.argsort(ev_t, kind="stable")
-    ev_t, ev_p = ev_t[order], ev_p[order]
-    n_ev = ev_t.size
-    start = time.monotonic_ns() + 2_000_000
-    abs_ns = (start + ev_t * 1e9).astype(np.uint64)
-    ev_patch, ev_cycle = pids[ev_p], mid[ev_p]
-    lat, edges, bad = [], 0, 0
-    i = outstanding = steps = 0
-    step_ns, step_req, step_parts = [], [], []
-    while i < n_ev or outstanding:
-        now = time.monotonic_ns()
-        j = int(np.searchsorted(abs_ns, now, side="right"))
-        if j > i:
-            got = srv.submit_registered_many(ev_patch[i:j], ev_cycle[i:j], None, abs_ns[i:j], stop_when_full=True)
-            outstanding += got.size
-            i += got.size
-        if outstanding:
-            t0 = time.monotonic_ns()
-            k = srv.step()
-            step_ns.append(time.monotonic_ns() - t0)
-            step_req.append(k)
-            step_parts.append(srv.last_timing())
-            steps += 1
-            d = srv.drain()
-            outstanding -= d["ids"].size
-            lat.append((d["t_done_ns"].astype(np.int64) - d["t_arrival_ns"].astype(np.int64)))
-            edges += int(d["n_edges"].sum())
-            bad += int((d["status"] != 0).sum())
-    elapsed = (time.monotonic_ns() - start) / 1e9
-    lat_us = np.concatenate(lat) / 1e3
+
+    def run(rate: float, seed: int) -> dict:
+        rng = np.random.default_rng(seed)
+        ev_t, ev_p = [], []
+        for i in range(P):
+            t = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * T * 1.3) + 32))
+            t = t[t < T]
+            ev_t.append(t)
+            ev_p.append(np.full(t.size, i, np.int64))
+        ev_t, ev_p = np.concatenate(ev_t), np.concatenate(ev_p)
+        order = np.argsort(ev_t, kind="stable")
+        ev_t, ev_p = ev_t[order], ev_p[order]
+        n_ev = ev_t.size
+        start = time.monotonic_ns() + 2_000_000
+        abs_ns = (start + ev_t * 1e9).astype(np.uint64)
+        ev_patch, ev_cycle = pids[ev_p], mid[ev_p]
+        lat, edges, bad = [], 0, 0
+        i = outstanding = steps = 0
+        step_ns, step_req, step_parts = [], [], []
+        while i < n_ev or outstanding:
+            now = time.monotonic_ns()
+            j = int(np.searchsorted(abs_ns, now, side="right"))
+            if j > i:
+                got = srv.submit_registered_many(ev_patch[i:j], ev_cycle[i:j], None, abs_ns[i:j],
+                                                 stop_when_full=True)
+                outstanding += got.size
+                i += got.size
+            if outstanding:
+                t0 = time.monotonic_ns()
+                k = srv.step()
+                step_ns.append(time.monotonic_ns() - t0)
+                step_req.append(k)
+                step_parts.append(srv.last_timing())
+                steps += 1
+                d = srv.drain()
+                outstanding -= d["ids"].size
+                lat.append((d["t_done_ns"].astype(np.int64) - d["t_arrival_ns"].astype(np.int64)))
+                edges += int(d["n_edges"].sum())
+                bad += int((d["status"] != 0).sum())
+        elapsed = (time.monotonic_ns() - start) / 1e9
+        lat_us = np.concatenate(lat) / 1e3
+        return {
+            "rate_per_patch_hz": rate, "offered_per_s": P * rate, "requests": int(n_ev), "failed": bad,
+            "completed_per_s": n_ev / elapsed, "hyperedges_per_s": edges / elapsed, "steps": steps,
+            "latency_us_p50": float(np.percentile(lat_us, 50)), "latency_us_p99": float(np.percentile(lat_us, 99)),
+            "latency_us_max": float(lat_us.max()),
+            "step_ms_mean": float(np.mean(step_ns) / 1e6), "requests_per_step_mean": float(np.mean(step_req)),
+            "step_us_mean": dict(zip(["build", "compile", "select", "hand_out", "lowering", "stage1", "group",
+                                      "compact"],
+                                     [float(x) for x in np.mean(np.array(step_parts), axis=0)])),
+        }
+
+    loads = [run(r, 5 + n) for n, r in enumerate(rates)]
     srv.close()
     return {
-        "workload": f"{P} patches (surface d=5..25 odd : BB [[144,12,12]] = 3:1), Poisson {rate:g} Hz per patch, "
-                    f"{T:g} s, p=1e-3, L2, H=1, up to {K} cycles per patch per step",
-        "requests": int(n_ev), "failed": bad, "steps": steps,
-        "offered_per_s": P * rate, "completed_per_s": n_ev / elapsed,
-        "hyperedges_per_s": edges / elapsed,
-        "latency_us_p50": float(np.percentile(lat_us, 50)), "latency_us_p99": float(np.percentile(lat_us, 99)),
-        "latency_us_max": float(lat_us.max()),
-        "step_ms_mean": float(np.mean(step_ns) / 1e6), "requests_per_step_mean": float(np.mean(step_req)),
-        "step_us_mean": dict(zip(["build", "compile", "select", "hand_out", "lowering", "stage1", "group", "compact"],
-                                 [float(x) for x in np.mean(np.array(step_parts), axis=0)])),
+        "workload": f"{P} patches (surface d=5..25 odd : BB [[144,12,12]] = 3:1), Poisson per-cycle requests, "
+                    f"{T:g} s per load, p=1e-3, L2, H=1, up to {K} cycles per patch per step",
+        "loads": loads,
     }
 
 
@@ -521,7 +532,8 @@ def main():
     ap.add_argument("--batch-reps", type=int, default=10)
     ap.add_argument("--serve-patches", type=int, default=64,
                     help="patches of the continuous-serving section (0 skips it)")
-    ap.add_argument("--serve-rate", type=float, default=1000.0, help="requests per second per patch")
+    ap.add_argument("--serve-rates", default="250,500,750,1000",
+                    help="per-patch request rates (Hz) of the serving loads, comma-separated")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-k", type=int, default=4, help="cycles of one patch merged into a step")
     args = ap.parse_args()

@@ -114,9 +114,12 @@ gp_status gp_server_submit(gp_server *srv, uint32_t patch, const gp_circuit *cyc
                            int final, uint64_t t_arrival_ns, uint64_t *request);
 
 /* Register a cycle a patch repeats (a steady-state syndrome round): it is
- * copied once into pinned host memory and submitted by id, with the same
- * checks as gp_server_submit at every submission.  *cycle_id receives its
- * id.  The registered cycles of a patch are freed when it closes. */
+ * copied once into device memory and submitted by id.  Its rows are checked
+ * here (the errors gp_server_submit reports for a cycle's own rows and
+ * sizes); each submission checks only what depends on the patch's history
+ * (record lookback and horizon, observables only in a final cycle, no cycle
+ * after the final one).  *cycle_id receives its id.  The registered cycles
+ * of a patch are freed when it closes. */
 gp_status gp_server_register_cycle(gp_server *srv, uint32_t patch, const gp_circuit *cycle, const float *noise,
                                    uint32_t *cycle_id);
 gp_status gp_server_submit_registered(gp_server *srv, uint32_t patch, uint32_t cycle_id, int final,

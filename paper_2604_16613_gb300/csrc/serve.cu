@@ -230,16 +230,22 @@ struct CycleInfo {
     const float *src_noise;
 };
 
-// a cycle registered once by its patch: pinned host copies (for the checks)
-// and device copies (the windows read it from there)
+// what a cycle's rows fix, whatever the patch saw before it: its counts and
+// how far its records look back past its own start
+struct CycleScan {
+    CycleInfo ci;               // counts (bases unset)
+    uint64_t reach = 0;         // measurements before the cycle the furthest record reaches
+    uint64_t reach_row = 0;     // the row holding that record
+    int64_t obs_row = -1;       // first OBSERVABLE_INCLUDE row, if any
+};
+
+// a cycle registered once by its patch: its scan and device copies of its
+// rows, records and noise (the windows read it from there)
 struct Registered {
-    uint4 *ops = nullptr;
-    uint32_t *recs = nullptr;
-    float *noise = nullptr;
     uint4 *d_ops = nullptr;
     uint32_t *d_recs = nullptr;
     float *d_noise = nullptr;
-    gp_circuit meta{};
+    CycleScan scan;             // its rows scanned at registration
 };
 
 // pinned host copy of one step's delivered hyperedges, shared by the
@@ -341,9 +347,6 @@ template <class T> T *carve_dev(unsigned char *base, uint64_t &off, uint64_t cou
 
 void free_registered(Patch &p) {
     for (Registered &r : p.registered) {
-        if (r.ops) cudaFreeHost(r.ops);
-        if (r.recs) cudaFreeHost(r.recs);
-        if (r.noise) cudaFreeHost(r.noise);
         if (r.d_ops) cudaFree(r.d_ops);
         if (r.d_recs) cudaFree(r.d_recs);
         if (r.d_noise) cudaFree(r.d_noise);
@@ -599,10 +602,8 @@ gp_status gp_server_close_patch(gp_server *s, uint32_t patch) {
 namespace {
 
 // checks of a cycle about to become patch p's next one; fills its sizes
-gp_status check_cycle(const gp_server *s, const Patch &p, const gp_circuit *cyc, const float *noise, bool final,
-                      CycleInfo &ci) {
+gp_status scan_cycle(const gp_server *s, const Patch &p, const gp_circuit *cyc, const float *noise, CycleScan &sc) {
     const gp_server_config &c = s->cfg;
-    if (p.final_submitted) return sfail(GP_ERR_INVALID, "patch already ended with a final cycle");
     if (cyc->n_ops > c.max_cycle_ops || cyc->n_recs > c.max_cycle_recs || cyc->n_locations > c.max_cycle_locations ||
         cyc->n_detectors > c.max_cycle_detectors)
         return sfail(GP_ERR_CAPACITY, "cycle larger than the server's per-cycle bounds");
@@ -611,15 +612,12 @@ gp_status check_cycle(const gp_server *s, const Patch &p, const gp_circuit *cyc,
     if ((cyc->n_ops && !cyc->ops) || (cyc->n_recs && !cyc->recs) || (cyc->n_locations && !noise))
         return sfail(GP_ERR_INVALID, "null cycle arrays");
     const uint4 *ops = reinterpret_cast<const uint4 *>(cyc->ops);
-    const uint32_t t = (uint32_t)p.cycles.size();
-    ci = CycleInfo{};
+    sc = CycleScan{};
+    CycleInfo &ci = sc.ci;
     ci.n_ops = (uint32_t)cyc->n_ops;
     ci.n_recs = (uint32_t)cyc->n_recs;
     ci.n_loc = cyc->n_locations;
-    ci.det_base = t ? p.cycles[t - 1].det_base + p.cycles[t - 1].n_det : 0;
-    ci.meas_base = t ? p.cycles[t - 1].meas_base + p.cycles[t - 1].n_meas : 0;
-    const uint64_t horizon_meas = t >= p.H ? p.cycles[t - p.H].meas_base : 0;
-    uint64_t meas = ci.meas_base;
+    uint64_t meas = 0;          // measurements of the cycle before the row
     uint32_t n_det = 0;
     for (uint64_t i = 0; i < cyc->n_ops; i++) {
         const uint4 op = ops[i];
@@ -630,22 +628,46 @@ gp_status check_cycle(const gp_server *s, const Patch &p, const gp_circuit *cyc,
             for (uint32_t l = 0; l < 3; l++) ci.mech[l] += n_comp_host(k, l);
             if (op.w >= cyc->n_locations) return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(i) + ": location out of range");
         } else if (k == K_DET || k == K_OBS) {
-            if (k == K_OBS && !final) return sfail(GP_ERR_INVALID, "observables are declared per patch; only a final cycle may define them");
+            if (k == K_OBS && sc.obs_row < 0) sc.obs_row = (int64_t)i;
             if (k == K_DET) n_det++;
             if ((uint64_t)op.y + op.z > cyc->n_recs) return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(i) + ": records out of range");
             for (uint32_t j = 0; j < op.z; j++) {
                 const uint32_t lb = cyc->recs[op.y + j];
-                if (lb == 0 || lb > meas) return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(i) + ": record lookback refers to no earlier measurement");
-                if (meas - lb < horizon_meas)
-                    return sfail(GP_ERR_HORIZON, "cycle row " + std::to_string(i) + ": record lookback reaches more than H cycles back");
+                if (lb == 0) return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(i) + ": record lookback refers to no earlier measurement");
+                if (lb > meas && lb - meas > sc.reach) {
+                    sc.reach = lb - meas;
+                    sc.reach_row = i;
+                }
             }
         }
     }
-    ci.n_meas = (uint32_t)(meas - ci.meas_base);
+    ci.n_meas = (uint32_t)meas;
     ci.n_det = n_det;
     if (n_det != cyc->n_detectors) return sfail(GP_ERR_INVALID, "cycle's n_detectors differs from its DETECTOR rows");
     if (ci.n_meas > c.max_cycle_measurements || ci.n_ticks + 1 > c.max_cycle_layers || ci.mech[2] > c.max_cycle_mechanisms)
         return sfail(GP_ERR_CAPACITY, "cycle larger than the server's per-cycle bounds");
+    return GP_OK;
+}
+
+// the checks that depend on the patch's history: a scanned cycle placed as the
+// patch's next one (its bases set)
+gp_status admit_cycle(const Patch &p, const CycleScan &sc, bool final, CycleInfo &ci) {
+    if (p.final_submitted) return sfail(GP_ERR_INVALID, "patch already ended with a final cycle");
+    if (sc.obs_row >= 0 && !final)
+        return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(sc.obs_row) +
+                                         ": observables are declared per patch; only a final cycle may define them");
+    const uint32_t t = (uint32_t)p.cycles.size();
+    ci = sc.ci;
+    ci.det_base = t ? p.cycles[t - 1].det_base + p.cycles[t - 1].n_det : 0;
+    ci.meas_base = t ? p.cycles[t - 1].meas_base + p.cycles[t - 1].n_meas : 0;
+    // a record of row i looks back lb measurements from meas_base + (the
+    // cycle's measurements before i); the furthest reaches `reach` before
+    // the cycle's start, which must lie within the last H cycles
+    const uint64_t horizon_meas = t >= p.H ? p.cycles[t - p.H].meas_base : 0;
+    if (sc.reach > ci.meas_base)
+        return sfail(GP_ERR_INVALID, "cycle row " + std::to_string(sc.reach_row) + ": record lookback refers to no earlier measurement");
+    if (ci.meas_base - sc.reach < horizon_meas)
+        return sfail(GP_ERR_HORIZON, "cycle row " + std::to_string(sc.reach_row) + ": record lookback reaches more than H cycles back");
     return GP_OK;
 }
 
@@ -680,7 +702,9 @@ gp_status gp_server_submit(gp_server *s, uint32_t patch, const gp_circuit *cyc, 
     if (patch >= c.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
     CycleInfo ci;
     {
-        const gp_status st = check_cycle(s, s->patches[patch], cyc, noise, final != 0, ci);
+        CycleScan sc;
+        gp_status st = scan_cycle(s, s->patches[patch], cyc, noise, sc);
+        if (st == GP_OK) st = admit_cycle(s->patches[patch], sc, final != 0, ci);
         if (st != GP_OK) return st;
     }
     if (s->free_stage.empty()) return sfail(GP_ERR_CAPACITY, "max_pending cycles are queued");
@@ -699,31 +723,18 @@ gp_status gp_server_register_cycle(gp_server *s, uint32_t patch, const gp_circui
     if (!s || !cyc || !cycle_id) return sfail(GP_ERR_INVALID, "null argument");
     const gp_server_config &c = s->cfg;
     if (patch >= c.max_patches || !s->patches[patch].open) return sfail(GP_ERR_INVALID, "no such open patch");
-    if (cyc->n_ops > c.max_cycle_ops || cyc->n_recs > c.max_cycle_recs || cyc->n_locations > c.max_cycle_locations)
-        return sfail(GP_ERR_CAPACITY, "cycle larger than the server's per-cycle bounds");
-    if ((cyc->n_ops && !cyc->ops) || (cyc->n_recs && !cyc->recs) || (cyc->n_locations && !noise))
-        return sfail(GP_ERR_INVALID, "null cycle arrays");
     Registered r;
-    r.meta = *cyc;
-    if (cudaMallocHost(&r.ops, sizeof(uint4) * std::max<uint64_t>(cyc->n_ops, 1)) != cudaSuccess ||
-        cudaMallocHost(&r.recs, sizeof(uint32_t) * std::max<uint64_t>(cyc->n_recs, 1)) != cudaSuccess ||
-        cudaMallocHost(&r.noise, sizeof(float) * std::max<uint32_t>(cyc->n_locations, 1)) != cudaSuccess) {
-        if (r.ops) cudaFreeHost(r.ops);
-        if (r.recs) cudaFreeHost(r.recs);
-        if (r.noise) cudaFreeHost(r.noise);
-        return sfail(GP_ERR_CUDA, "cudaMallocHost of a registered cycle failed");
+    {
+        // the rows are scanned once here; a submission only places the scan
+        const gp_status st = scan_cycle(s, s->patches[patch], cyc, noise, r.scan);
+        if (st != GP_OK) return st;
     }
-    if (cyc->n_ops) memcpy(r.ops, cyc->ops, cyc->n_ops * sizeof(uint4));
-    if (cyc->n_recs) memcpy(r.recs, cyc->recs, cyc->n_recs * sizeof(uint32_t));
-    if (cyc->n_locations) memcpy(r.noise, noise, cyc->n_locations * sizeof(float));
-    r.meta.ops = reinterpret_cast<const uint32_t *>(r.ops);
-    r.meta.recs = r.recs;
     if (cudaMalloc(&r.d_ops, sizeof(uint4) * std::max<uint64_t>(cyc->n_ops, 1)) != cudaSuccess ||
         cudaMalloc(&r.d_recs, sizeof(uint32_t) * std::max<uint64_t>(cyc->n_recs, 1)) != cudaSuccess ||
         cudaMalloc(&r.d_noise, sizeof(float) * std::max<uint32_t>(cyc->n_locations, 1)) != cudaSuccess ||
-        cudaMemcpy(r.d_ops, r.ops, sizeof(uint4) * cyc->n_ops, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(r.d_recs, r.recs, sizeof(uint32_t) * cyc->n_recs, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(r.d_noise, r.noise, sizeof(float) * cyc->n_locations, cudaMemcpyHostToDevice) != cudaSuccess) {
+        (cyc->n_ops && cudaMemcpy(r.d_ops, cyc->ops, sizeof(uint4) * cyc->n_ops, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (cyc->n_recs && cudaMemcpy(r.d_recs, cyc->recs, sizeof(uint32_t) * cyc->n_recs, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (cyc->n_locations && cudaMemcpy(r.d_noise, noise, sizeof(float) * cyc->n_locations, cudaMemcpyHostToDevice) != cudaSuccess)) {
         Patch tmp;
         tmp.registered.push_back(r);
         free_registered(tmp);
@@ -746,7 +757,7 @@ gp_status gp_server_submit_registered(gp_server *s, uint32_t patch, uint32_t cyc
     const Registered &r = p.registered[cycle_id];
     CycleInfo ci;
     {
-        const gp_status st = check_cycle(s, p, &r.meta, r.noise, final != 0, ci);
+        const gp_status st = admit_cycle(p, r.scan, final != 0, ci);
         if (st != GP_OK) return st;
     }
     *request = enqueue(s, patch, ci, final != 0, 0u, (int32_t)cycle_id, t_arrival_ns);
