@@ -273,7 +273,7 @@ gp_status enqueue_pipeline(gp_driver *d, cudaStream_t s, uint32_t *kernels) {
     const Stage1Shape shape1 = stage1_shape(bd.max_qubits, want, d->smem_limit);
     if (shape1.smem > d->smem_limit) return fail(GP_ERR_CAPACITY, "stage 1 does not fit in shared memory with these bounds");
     int occ = 1;
-    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage1_kernel_ptr(d->tuning.stage1_threads),
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage1_kernel_ptr(d->tuning.stage1_threads, shape1.split),
                                                           (int)d->tuning.stage1_threads, shape1.smem));
     if (occ < 1) return fail(GP_ERR_CAPACITY, "stage 1 does not fit on an SM with these bounds");
     const uint32_t bps = std::min<uint32_t>(want, (uint32_t)occ);
@@ -392,11 +392,12 @@ gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace, uint64_t 
     // per-layer index kernel
     d->smem_limit = stage1_dynamic_smem_limit(d->device);
     if (d->smem_limit == 0) return cleanup(fail(GP_ERR_CUDA, "querying the shared-memory limit failed"));
-    for (uint32_t t : {128u, 256u, 512u, 1024u}) {
-        if (cudaFuncSetAttribute(stage1_kernel_ptr(t), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)d->smem_limit) != cudaSuccess)
-            return cleanup(fail(GP_ERR_CUDA, "cudaFuncSetAttribute(stage1 shared memory) failed"));
-    }
+    for (uint32_t split : {0u, 1u})
+        for (uint32_t t : {128u, 256u, 512u, 1024u}) {
+            if (cudaFuncSetAttribute(stage1_kernel_ptr(t, split), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)d->smem_limit) != cudaSuccess)
+                return cleanup(fail(GP_ERR_CUDA, "cudaFuncSetAttribute(stage1 shared memory) failed"));
+        }
     if (lowering_setup(bounds->max_qubits) != cudaSuccess)
         return cleanup(fail(GP_ERR_CUDA, "cudaFuncSetAttribute(layer index shared memory) failed"));
     *out = d;

@@ -409,10 +409,12 @@ void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, u
                      uint32_t *launches);
 cudaError_t lowering_setup(uint32_t max_qubits);
 // shared-memory shape of the stage-1 walk: window buffers, list entries a
-// buffer holds, bytes of a buffer and of the whole block
+// buffer holds, bytes of a buffer and of the whole block, and which walk
+// (1: role-split, 0: block-wide)
 struct Stage1Shape {
     uint32_t nbuf, list_cap, wbytes;
     size_t smem;
+    uint32_t split;
 };
 // limit: dynamic shared memory one block may take (opt-in maximum less the
 // kernel's static shared memory)
@@ -420,7 +422,7 @@ Stage1Shape stage1_shape(uint32_t max_qubits, uint32_t blocks_per_sm, size_t lim
 size_t stage1_dynamic_smem_limit(int device);
 void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_qubits, const Stage1Shape &shape,
                    cudaStream_t s, uint32_t *launches);
-const void *stage1_kernel_ptr(uint32_t threads);
+const void *stage1_kernel_ptr(uint32_t threads, uint32_t split);
 void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
 void launch_init_table(TabSlot *t, size_t n, cudaStream_t s);

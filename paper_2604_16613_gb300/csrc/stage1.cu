@@ -119,6 +119,18 @@ __device__ __forceinline__ unsigned long long meas_word(const Smem &s, uint32_t 
     return w;
 }
 
+__device__ __forceinline__ unsigned long long meas_word_at(const uint32_t *ent_m, const unsigned long long *ent_w,
+                                                         uint32_t n_ent, uint32_t m) {
+    uint32_t lo = 0, hi = n_ent;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (ent_m[mid] < m) lo = mid + 1; else hi = mid;
+    }
+    unsigned long long w = 0ull;
+    for (uint32_t i = lo; i < n_ent && ent_m[i] == m; i++) w ^= ent_w[i];
+    return w;
+}
+
 // what one walk step reads (shared or global memory), published by the
 // producer with the window
 struct Window {
@@ -139,6 +151,106 @@ struct Shared {
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The (measurement, word) entries of one word column (Eq. init-slp): each
+// measurement a detector of the column (or the observable) reads, with the
+// column bit it sets, sorted by measurement, each run merged into its first
+// entry, and each entry's layer and qubit.  Every thread of the block calls
+// it, with nent_sh and lmax_sh zeroed.  Returns the entry count, or 0 when
+// the column has nothing to walk (no entries, every word cancelled, or over
+// capacity: reported); then lmax_sh - 1 is the latest layer holding a
+// non-zero word and ent_l[0] the earliest layer of an entry.
+template <int NT>
+__device__ uint32_t column_entries(const Buffers &B, const CircuitDev &C, uint32_t cidx, uint32_t local, bool is_obs,
+                                   uint32_t gcol, uint32_t *ent_m, unsigned long long *ent_w, uint32_t *ent_l,
+                                   uint32_t *ent_q, uint32_t &nent_sh, uint32_t &lmax_sh) {
+    // (measurement, word) entries of this column (Eq. init-slp)
+    if (!is_obs) {
+        const uint32_t j0 = local * 64u, j1 = min(j0 + 64u, C.n_det);
+        for (uint32_t j = j0 + threadIdx.x; j < j1; j += NT) {
+            const uint32_t row = B.det_row[C.det_base + j];
+            const uint4 op = C.ops[row];
+            const uint32_t mb = B.aux[C.op_base + row];
+            for (uint32_t i = 0; i < op.z; i++) {
+                const uint32_t e = atomicAdd(&nent_sh, 1u);
+                if (e < (uint32_t)kMaxEntries) {
+                    ent_m[e] = mb - C.recs[op.y + i];
+                    ent_w[e] = 1ull << (j & 63u);
+                }
+            }
+        }
+    } else {
+        const uint32_t n_rows = B.obs_count[cidx];
+        for (uint32_t i0 = threadIdx.x; i0 < n_rows; i0 += NT) {
+            const uint32_t row = B.obs_rows[C.op_base + i0];
+            const uint4 op = C.ops[row];
+            const uint32_t mb = B.aux[C.op_base + row];
+            for (uint32_t i = 0; i < op.z; i++) {
+                const uint32_t e = atomicAdd(&nent_sh, 1u);
+                if (e < (uint32_t)kMaxEntries) {
+                    ent_m[e] = mb - C.recs[op.y + i];
+                    ent_w[e] = 1ull << op.w;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t n_ent = nent_sh;
+    if (n_ent > (uint32_t)kMaxEntries) {
+        if (threadIdx.x == 0) report(B.status, GP_ERR_CAPACITY, 5u, gcol, n_ent);
+        return 0u;
+    }
+    if (n_ent == 0u) return 0u;
+    // bitonic sort of the entries by measurement index
+    uint32_t npow = 1;
+    while (npow < n_ent) npow <<= 1;
+    for (uint32_t i = n_ent + threadIdx.x; i < npow; i += NT) { ent_m[i] = 0xFFFFFFFFu; ent_w[i] = 0ull; }
+    __syncthreads();
+    for (uint32_t k2 = 2; k2 <= npow; k2 <<= 1) {
+        for (uint32_t j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+            for (uint32_t i = threadIdx.x; i < npow; i += NT) {
+                const uint32_t ixj = i ^ j2;
+                if (ixj > i) {
+                    const bool asc = (i & k2) == 0u;
+                    const uint32_t mi = ent_m[i], mj = ent_m[ixj];
+                    if ((mi > mj) == asc) {
+                        ent_m[i] = mj; ent_m[ixj] = mi;
+                        const unsigned long long wi = ent_w[i];
+                        ent_w[i] = ent_w[ixj]; ent_w[ixj] = wi;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // merge the entries of one measurement: the first of a run holds the
+    // XOR of the run, the rest hold zero (the layer array holds the merged
+    // words meanwhile)
+    unsigned long long *merged = reinterpret_cast<unsigned long long *>(ent_l);
+    static_assert(kMaxEntries % 2 == 0, "ent_l and ent_q hold one 64-bit word per entry");
+    for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
+        unsigned long long w = 0ull;
+        if (i == 0u || ent_m[i] != ent_m[i - 1u]) {
+            for (uint32_t j = i; j < n_ent && ent_m[j] == ent_m[i]; j++) w ^= ent_w[j];
+        }
+        merged[i] = w;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
+        const unsigned long long w = merged[i];
+        ent_w[i] = w;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
+        const uint2 lq = B.meas_lq[C.meas_base + ent_m[i]];
+        ent_l[i] = lq.x;
+        ent_q[i] = lq.y;
+        if (ent_w[i] != 0ull) atomicMax(&lmax_sh, lq.x + 1u);
+    }
+    __syncthreads();
+    if (lmax_sh == 0u) return 0u;   // every word cancelled
+    return n_ent;
 }
 
 template <int NT>
@@ -233,92 +345,9 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
             s.pl[q] = make_ulonglong2(0ull, 0ull);
             s.bits[q] = 0;
         }
-        // (measurement, word) entries of this column (Eq. init-slp)
-        if (!is_obs) {
-            const uint32_t j0 = local * 64u, j1 = min(j0 + 64u, C.n_det);
-            for (uint32_t j = j0 + threadIdx.x; j < j1; j += NT) {
-                const uint32_t row = B.det_row[C.det_base + j];
-                const uint4 op = C.ops[row];
-                const uint32_t mb = B.aux[C.op_base + row];
-                for (uint32_t i = 0; i < op.z; i++) {
-                    const uint32_t e = atomicAdd(&sh.nent, 1u);
-                    if (e < (uint32_t)kMaxEntries) {
-                        s.ent_m[e] = mb - C.recs[op.y + i];
-                        s.ent_w[e] = 1ull << (j & 63u);
-                    }
-                }
-            }
-        } else {
-            const uint32_t n_rows = B.obs_count[b];
-            for (uint32_t i0 = threadIdx.x; i0 < n_rows; i0 += NT) {
-                const uint32_t row = B.obs_rows[C.op_base + i0];
-                const uint4 op = C.ops[row];
-                const uint32_t mb = B.aux[C.op_base + row];
-                for (uint32_t i = 0; i < op.z; i++) {
-                    const uint32_t e = atomicAdd(&sh.nent, 1u);
-                    if (e < (uint32_t)kMaxEntries) {
-                        s.ent_m[e] = mb - C.recs[op.y + i];
-                        s.ent_w[e] = 1ull << op.w;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        const uint32_t n_ent = sh.nent;
-        if (n_ent > (uint32_t)kMaxEntries) {
-            if (threadIdx.x == 0) report(B.status, GP_ERR_CAPACITY, 5u, gcol, n_ent);
-            __syncthreads();
-            continue;
-        }
+        const uint32_t n_ent = column_entries<NT>(B, C, b, local, is_obs, gcol, s.ent_m, s.ent_w, s.ent_l, s.ent_q,
+                                                  sh.nent, sh.lmax);
         if (n_ent == 0u) { __syncthreads(); continue; }
-        // bitonic sort of the entries by measurement index
-        uint32_t npow = 1;
-        while (npow < n_ent) npow <<= 1;
-        for (uint32_t i = n_ent + threadIdx.x; i < npow; i += NT) { s.ent_m[i] = 0xFFFFFFFFu; s.ent_w[i] = 0ull; }
-        __syncthreads();
-        for (uint32_t k2 = 2; k2 <= npow; k2 <<= 1) {
-            for (uint32_t j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
-                for (uint32_t i = threadIdx.x; i < npow; i += NT) {
-                    const uint32_t ixj = i ^ j2;
-                    if (ixj > i) {
-                        const bool asc = (i & k2) == 0u;
-                        const uint32_t mi = s.ent_m[i], mj = s.ent_m[ixj];
-                        if ((mi > mj) == asc) {
-                            s.ent_m[i] = mj; s.ent_m[ixj] = mi;
-                            const unsigned long long wi = s.ent_w[i];
-                            s.ent_w[i] = s.ent_w[ixj]; s.ent_w[ixj] = wi;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        // merge the entries of one measurement: the first of a run holds the
-        // XOR of the run, the rest hold zero (the layer array holds the merged
-        // words meanwhile)
-        unsigned long long *merged = reinterpret_cast<unsigned long long *>(s.ent_l);
-        static_assert(kMaxEntries % 2 == 0, "ent_l and ent_q hold one 64-bit word per entry");
-        for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
-            unsigned long long w = 0ull;
-            if (i == 0u || s.ent_m[i] != s.ent_m[i - 1u]) {
-                for (uint32_t j = i; j < n_ent && s.ent_m[j] == s.ent_m[i]; j++) w ^= s.ent_w[j];
-            }
-            merged[i] = w;
-        }
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
-            const unsigned long long w = merged[i];
-            s.ent_w[i] = w;
-        }
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
-            const uint2 lq = B.meas_lq[C.meas_base + s.ent_m[i]];
-            s.ent_l[i] = lq.x;
-            s.ent_q[i] = lq.y;
-            if (s.ent_w[i] != 0ull) atomicMax(&sh.lmax, lq.x + 1u);
-        }
-        __syncthreads();
-        if (sh.lmax == 0u) { __syncthreads(); continue; }   // every word cancelled
         const uint32_t lmax = sh.lmax - 1u;
         const uint32_t lmin = s.ent_l[0];
 
@@ -624,6 +653,585 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Role-split walk.  The walk of a column is a chain over its layers; the
+// noise rows of a layer only read the planes of that layer.  So one warp (the
+// walker) advances the planes layer by layer with warp-level syncs only, and
+// publishes for each step a snapshot of its active qubits' planes; the other
+// warps (emitters) evaluate the noise rows of a step from that snapshot while
+// the walker is already on the next one; the last warp stages the layer
+// windows.  The snapshot tables are double-buffered by step parity and
+// tagged with the step that wrote an entry (a qubit whose tag differs is not
+// active in that step), so they are never cleared.  mbarriers order the
+// roles: window full (producer -> walker, emitters), window free (walker,
+// emitters -> producer), table full (walker -> emitters), table free
+// (emitters -> walker); every wait is bounded.
+// ---------------------------------------------------------------------------
+struct SplitSmem {
+    ulonglong2 *pl;                 // walker: per qubit {X plane, Z plane}
+    ulonglong2 *tab0, *tab1;        // snapshot planes per step parity
+    uint4 *segc;                    // producer: layer segments
+    unsigned long long *ent_w;      // entry words
+    uint32_t *tag0, *tag1;          // step that wrote a snapshot entry
+    uint32_t *ent_m, *ent_l, *ent_q;
+    uint16_t *act0, *act1;          // active qubits of a step
+    uint16_t *add;                  // qubits the walker adds to the next step's candidates
+    unsigned char *bits;            // walker: kActive / kAdded / 0 per qubit
+    unsigned char *win;             // window buffers
+};
+
+__host__ __device__ inline size_t split_base_bytes(uint32_t maxq) {
+    const size_t q8 = round8(maxq);
+    size_t b = 16 * q8 * 3                          // pl, tab[2]
+               + 16 * (size_t)kSegCache             // segc
+               + 8 * (size_t)kMaxEntries            // ent_w
+               + 4 * q8 * 2                         // tag[2]
+               + 12 * (size_t)kMaxEntries           // ent_m, ent_l, ent_q
+               + 2 * q8 * 3                         // act[2], add
+               + q8;                                // bits
+    return (b + 127) & ~(size_t)127;
+}
+
+__device__ __forceinline__ SplitSmem split_carve(unsigned char *base, uint32_t maxq) {
+    const uint32_t q8 = round8(maxq);
+    SplitSmem s;
+    s.pl = reinterpret_cast<ulonglong2 *>(base);
+    s.tab0 = s.pl + q8;
+    s.tab1 = s.tab0 + q8;
+    s.segc = reinterpret_cast<uint4 *>(s.tab1 + q8);
+    s.ent_w = reinterpret_cast<unsigned long long *>(s.segc + kSegCache);
+    s.tag0 = reinterpret_cast<uint32_t *>(s.ent_w + kMaxEntries);
+    s.tag1 = s.tag0 + q8;
+    s.ent_m = s.tag1 + q8;
+    s.ent_l = s.ent_m + kMaxEntries;
+    s.ent_q = s.ent_l + kMaxEntries;
+    s.act0 = reinterpret_cast<uint16_t *>(s.ent_q + kMaxEntries);
+    s.act1 = s.act0 + q8;
+    s.add = s.act1 + q8;
+    s.bits = reinterpret_cast<unsigned char *>(s.add + q8);
+    s.win = base + split_base_bytes(maxq);
+    return s;
+}
+// the parity-b copies (selects, not an indexed array: no stack frame)
+__device__ __forceinline__ ulonglong2 *tab_of(const SplitSmem &s, uint32_t b) { return b ? s.tab1 : s.tab0; }
+__device__ __forceinline__ uint32_t *tag_of(const SplitSmem &s, uint32_t b) { return b ? s.tag1 : s.tag0; }
+__device__ __forceinline__ uint16_t *act_of(const SplitSmem &s, uint32_t b) { return b ? s.act1 : s.act0; }
+
+// what the walker publishes with a step's snapshot
+struct StepDesc {
+    int layer;          // L (-1: the before-gate noise of layer 0)
+    uint32_t n_act;     // active qubits (act list of the step's parity)
+    uint32_t slot;      // window slot of L
+    uint32_t end;       // 1: no step; the column is done
+};
+
+struct SplitShared {
+    unsigned long long win_full[kMaxBufs], win_free[kMaxBufs];
+    unsigned long long tab_full[2], tab_free[2];
+    Window desc[kMaxBufs];
+    StepDesc step[2];
+    uint32_t item, bail, nent, lmax;
+    uint32_t tmo;           // a wait gave up (every role leaves)
+    uint32_t walk_done;     // the walker left the column (the producer stops)
+    int stop_layer;         // last layer the walker stepped through
+    int posted_lo;          // lowest window the producer posted
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t maxq, uint32_t nbuf,
+                                                             uint32_t list_cap, uint32_t wbytes, uint32_t wchunk) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const SplitSmem s = split_carve(smem_raw, maxq);
+    __shared__ SplitShared sh;
+    constexpr uint32_t NW = NT / 32;
+    constexpr uint32_t NE = NW - 2;                 // emitter warps (1 .. NW-2)
+    static_assert(NW >= 3, "walker, emitters and producer");
+    const Params &P = *B.params;
+    const uint32_t level = P.level, rec_cap = P.rec_cap;
+    const uint32_t nc_dep1 = level == 0u ? 2u : 3u, nc_dep2 = level == 0u ? 6u : (level == 1u ? 10u : 15u);
+    const uint32_t lane = threadIdx.x & 31u, l16 = lane & 15u, half = lane >> 4;
+    const uint32_t warp = threadIdx.x >> 5;
+    const bool walker = warp == 0u, producer = warp == NW - 1u;
+    const uint32_t ew = warp - 1u;                  // emitter index
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t windex = window_index_bytes(maxq);
+    const uint32_t nring = nbuf >= 2u ? nbuf : 2u;
+    volatile uint32_t *const tmo_v = &sh.tmo;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kMaxBufs; i++) {
+            mbar_init(&sh.win_full[i], 1);
+            mbar_init(&sh.win_free[i], NE + 1u);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&sh.tab_full[i], 1);
+            mbar_init(&sh.tab_free[i], NE);
+        }
+        fence_mbar_init();
+        sh.tmo = 0;
+    }
+    for (uint32_t q = threadIdx.x; q < round8(maxq); q += NT) s.tag0[q] = s.tag1[q] = kNone;
+    __syncthreads();
+
+    // per-thread barrier phases (bit i: slot or buffer i)
+    uint32_t full_par = 0;                  // walker, emitters: window full
+    uint32_t free_par = 0, free_pend = 0;   // producer: window free; slots awaiting a release
+    uint32_t post_par = 0, posted_any = 0;  // producer: parity of the posts per slot
+    uint32_t tfull_par = 0;                 // emitters: table full
+    uint32_t tfree_par = 0, tfree_pend = 0; // walker: table free; buffers awaiting a release
+    uint32_t st = 0;                        // steps taken by this block (snapshot tags)
+    uint32_t ck_pos = 0, ck_end = 0, ck_next = 0;
+    bool has_next = false;
+    uint32_t seg_lo = 0xFFFFFFFFu;
+
+    // bounded wait; gives up early once another role has given up
+    auto wait_bar = [&](unsigned long long *bar, uint32_t parity) -> bool {
+        for (uint32_t it = 0; it < (1u << 22); it++) {
+            if (mbar_try_wait(bar, parity)) return true;
+            if ((it & 31u) == 31u && *tmo_v) return false;
+        }
+        *tmo_v = 1u;
+        return false;
+    };
+    // the same, by every lane of a warp with one outcome for all (the loops
+    // around it use warp-wide votes)
+    auto wait_warp = [&](unsigned long long *bar, uint32_t parity) -> bool {
+        return __all_sync(0xFFFFFFFFu, wait_bar(bar, parity));
+    };
+    auto warp_room = [&](uint32_t need) -> bool {
+        if (ck_end - ck_pos >= need) return true;
+        uint32_t nb = 0;
+        if (has_next) {
+            nb = __shfl_sync(0xFFFFFFFFu, ck_next, 0);
+        } else {
+            if (lane == 0u) nb = atomicAdd(&B.status->rec_count, wchunk);
+            nb = __shfl_sync(0xFFFFFFFFu, nb, 0);
+        }
+        has_next = false;
+        if (nb + wchunk > rec_cap || nb + wchunk < nb) {
+            if (lane == 0u) report(B.status, GP_ERR_CAPACITY, 8u, nb, rec_cap);
+            ck_pos = ck_end = 0;
+            return false;
+        }
+        ck_pos = nb;
+        ck_end = nb + wchunk;
+        return true;
+    };
+    auto warp_prefetch = [&]() {
+        if (!has_next && ck_end != 0u && ck_end - ck_pos < wchunk / 2u) {
+            if (lane == 0u) ck_next = atomicAdd(&B.status->rec_count, wchunk);
+            has_next = true;
+        }
+    };
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            sh.item = atomicAdd(&B.status->queue_head, 1u);
+            sh.bail = (*(volatile uint32_t *)&B.status->code) != 0u;
+            sh.nent = 0;
+            sh.lmax = 0;
+            sh.walk_done = 0;
+            sh.stop_layer = 0;
+            sh.posted_lo = 0;
+        }
+        __syncthreads();
+        const uint32_t item = sh.item;
+        if (item >= P.n_items || sh.bail || sh.tmo) break;
+        const uint32_t gcol = B.items[item];
+        const uint32_t cidx = B.col_circ[gcol];
+        const CircuitDev &C = B.circ[cidx];
+        const uint32_t local = gcol - C.col_base;
+        const bool is_obs = (C.n_obs > 0u) && (local == C.n_cols - 1u);
+        const uint32_t col_tag = gcol | (is_obs ? kObsColFlag : 0u);
+        const uint32_t nq = C.n_qubits;
+        const uint32_t mech_base = C.mech_base;
+        seg_lo = 0xFFFFFFFFu;
+        for (uint32_t q = threadIdx.x; q < nq; q += NT) {
+            s.pl[q] = make_ulonglong2(0ull, 0ull);
+            s.bits[q] = 0;
+        }
+        const uint32_t n_ent = column_entries<NT>(B, C, cidx, local, is_obs, gcol, s.ent_m, s.ent_w, s.ent_l,
+                                                  s.ent_q, sh.nent, sh.lmax);
+        if (n_ent == 0u) { __syncthreads(); continue; }
+        const uint32_t lmax = sh.lmax - 1u;
+        const uint32_t lmin = s.ent_l[0];
+        const LayerGeo geo = layer_geo(nq);
+        const unsigned char *qbase = B.qidx + (size_t)C.qidx_off * 16u;
+        const uint2 *lbase = B.lists + 2ull * C.op_base;
+        const uint4 *seg_g = B.layer_seg + C.layer_base;
+        auto slot_of = [&](int L) -> uint32_t { return (uint32_t)(L + 1) % nring; };
+
+        if (walker) {
+            // ---- walker: candidates of a step = the active qubits of the
+            // last step, then the qubits the last step added
+            uint32_t n_prev = 0, n_add = 0, cur = n_ent;
+            int L = (int)lmax;
+            bool ok = true;
+            for (;;) {
+                const uint32_t slot = slot_of(L), b = st & 1u;
+                if (!wait_warp(&sh.win_full[slot], (full_par >> slot) & 1u)) { ok = false; break; }
+                full_par ^= 1u << slot;
+                const Window v = sh.desc[slot];
+                if ((tfree_pend >> b) & 1u) {
+                    if (!wait_warp(&sh.tab_free[b], (tfree_par >> b) & 1u)) { ok = false; break; }
+                    tfree_par ^= 1u << b;
+                }
+                tfree_pend |= 1u << b;
+                // pass 1: activity and snapshot
+                const uint16_t *prev = act_of(s, b ^ 1u);
+                ulonglong2 *const tb = tab_of(s, b);
+                uint32_t *const tg = tag_of(s, b);
+                uint16_t *const ab = act_of(s, b);
+                const uint32_t n_cand = n_prev + n_add;
+                uint32_t n_act = 0;
+                for (uint32_t base = 0; base < n_cand; base += 64u) {
+                    const uint32_t i0 = base + lane, i1 = i0 + 32u;
+                    uint32_t q0 = 0, q1 = 0;
+                    if (i0 < n_cand) q0 = i0 < n_prev ? prev[i0] : s.add[i0 - n_prev];
+                    if (i1 < n_cand) q1 = i1 < n_prev ? prev[i1] : s.add[i1 - n_prev];
+                    const ulonglong2 p0 = s.pl[q0], p1 = s.pl[q1];
+                    const bool a0 = i0 < n_cand && (p0.x | p0.y) != 0ull;
+                    const bool a1 = i1 < n_cand && (p1.x | p1.y) != 0ull;
+                    if (i0 < n_cand) s.bits[q0] = a0 ? kActive : (unsigned char)0;
+                    if (i1 < n_cand) s.bits[q1] = a1 ? kActive : (unsigned char)0;
+                    if (a0) { tb[q0] = p0; tg[q0] = st; }
+                    if (a1) { tb[q1] = p1; tg[q1] = st; }
+                    if (L < 0 && ((a0 && p0.y != 0ull) || (a1 && p1.y != 0ull)))
+                        report(B.status, GP_ERR_NONDETERMINISTIC, cidx, 0xFFFFFFFFu, gcol);
+                    const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0), m1 = __ballot_sync(0xFFFFFFFFu, a1);
+                    if (a0) ab[n_act + __popc(m0 & lt_mask)] = (uint16_t)q0;
+                    n_act += __popc(m0);
+                    if (a1) ab[n_act + __popc(m1 & lt_mask)] = (uint16_t)q1;
+                    n_act += __popc(m1);
+                }
+                if (lane == 0u) sh.step[b] = StepDesc{L, n_act, slot, 0u};
+                __syncwarp();
+                if (lane == 0u) mbar_arrive(&sh.tab_full[b]);
+                // pass 2: the gates of L undone on the active qubits; inactive
+                // partners of their two-qubit gates go on the next candidates
+                uint32_t n_new = 0;
+                if (L >= 0) {
+                    for (uint32_t base = 0; base < n_act; base += 32u) {
+                        const uint32_t i = base + lane;
+                        uint32_t partner = kNone;
+                        if (i < n_act) {
+                            const uint32_t q = ab[i];
+                            const uint32_t g = v.gate[q];
+                            const uint32_t k = g >> 28, pay = g & 0x0FFFFFFFu;
+                            switch (k) {
+                            case K_H: { const ulonglong2 t = s.pl[q]; s.pl[q] = make_ulonglong2(t.y, t.x); break; }
+                            case K_S: { ulonglong2 t = s.pl[q]; t.x ^= t.y; s.pl[q] = t; break; }
+                            case GV_CX_C: {
+                                ulonglong2 c_ = s.pl[q], t_ = s.pl[pay];
+                                c_.x ^= t_.x;
+                                t_.y ^= c_.y;
+                                s.pl[q] = c_;
+                                s.pl[pay] = t_;
+                                partner = pay;
+                                break;
+                            }
+                            case GV_CX_T: {
+                                if (s.bits[pay] == kActive) break;    // undone from the active control
+                                ulonglong2 c_ = s.pl[pay], t_ = s.pl[q];
+                                c_.x ^= t_.x;
+                                t_.y ^= c_.y;
+                                s.pl[pay] = c_;
+                                s.pl[q] = t_;
+                                partner = pay;
+                                break;
+                            }
+                            case GV_CZ_B:
+                                if (s.bits[pay] == kActive) break;    // undone from the active first qubit
+                                // fall through
+                            case GV_CZ_A: {
+                                ulonglong2 a_ = s.pl[q], b_ = s.pl[pay];
+                                const unsigned long long za = a_.y, zb = b_.y;
+                                a_.x ^= zb;
+                                b_.x ^= za;
+                                s.pl[q] = a_;
+                                s.pl[pay] = b_;
+                                partner = pay;
+                                break;
+                            }
+                            case K_R: case K_M: case K_MR: {
+                                ulonglong2 t = s.pl[q];
+                                if (t.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)L, gcol);
+                                if (k != K_M) t = make_ulonglong2(0ull, 0ull);
+                                if (k != K_R) t.x ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
+                                s.pl[q] = t;
+                                break;
+                            }
+                            case K_RX: case K_MX: case K_MRX: {
+                                ulonglong2 t = s.pl[q];
+                                if (t.x != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)L, gcol);
+                                if (k != K_MX) t = make_ulonglong2(0ull, 0ull);
+                                if (k != K_RX) t.y ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
+                                s.pl[q] = t;
+                                break;
+                            }
+                            default: break;
+                            }
+                        }
+                        const bool add = partner != kNone && s.bits[partner] == 0;
+                        if (add) s.bits[partner] = kAdded;
+                        const unsigned m = __ballot_sync(0xFFFFFFFFu, add);
+                        if (add) s.add[n_new + __popc(m & lt_mask)] = (uint16_t)partner;
+                        n_new += __popc(m);
+                    }
+                    // measurements of the column at L on inactive qubits
+                    if (cur > 0u && s.ent_l[cur - 1u] == (uint32_t)L) {
+                        uint32_t l0 = 0, h0 = cur;
+                        while (l0 < h0) {
+                            const uint32_t mid = (l0 + h0) >> 1;
+                            if (s.ent_l[mid] < (uint32_t)L) l0 = mid + 1; else h0 = mid;
+                        }
+                        for (uint32_t base = l0; base < cur; base += 32u) {
+                            const uint32_t i = base + lane;
+                            bool add = false;
+                            uint32_t q = 0;
+                            if (i < cur) {
+                                const unsigned long long w = s.ent_w[i];
+                                const uint32_t qv = s.ent_q[i];
+                                q = qv & 0x7FFFFFFFu;
+                                // an active qubit had the word applied by its gate above
+                                if (w != 0ull && s.bits[q] == 0) {
+                                    if (qv >> 31) s.pl[q].y ^= w; else s.pl[q].x ^= w;
+                                    s.bits[q] = kAdded;
+                                    add = true;
+                                }
+                            }
+                            const unsigned m = __ballot_sync(0xFFFFFFFFu, add);
+                            if (add) s.add[n_new + __popc(m & lt_mask)] = (uint16_t)q;
+                            n_new += __popc(m);
+                        }
+                        cur = l0;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0u) mbar_arrive(&sh.win_free[slot]);
+                st++;
+                n_prev = n_act;
+                n_add = n_new;
+                if (L < 0) break;
+                if (L == 0) { L = -1; continue; }
+                if (n_prev + n_add == 0u && (uint32_t)(L - 1) < lmin) break;
+                L--;
+            }
+            if (ok) {
+                // the end-of-column step: the emitters leave on it
+                const uint32_t b = st & 1u;
+                if ((tfree_pend >> b) & 1u) {
+                    if (!wait_warp(&sh.tab_free[b], (tfree_par >> b) & 1u)) ok = false;
+                    else tfree_par ^= 1u << b;
+                }
+                if (ok) {
+                    tfree_pend |= 1u << b;
+                    if (lane == 0u) {
+                        sh.step[b] = StepDesc{0, 0u, 0u, 1u};
+                        sh.stop_layer = L;
+                    }
+                    __syncwarp();
+                    if (lane == 0u) mbar_arrive(&sh.tab_full[b]);
+                    st++;
+                }
+            }
+            if (lane == 0u) *(volatile uint32_t *)&sh.walk_done = 1u;
+        } else if (!producer) {
+            // ---- emitters: the noise rows of each published step
+            for (;;) {
+                const uint32_t b = st & 1u;
+                if (!wait_warp(&sh.tab_full[b], (tfull_par >> b) & 1u)) break;
+                tfull_par ^= 1u << b;
+                const StepDesc sd = sh.step[b];
+                if (sd.end) {
+                    __syncwarp();
+                    if (lane == 0u) mbar_arrive(&sh.tab_free[b]);
+                    st++;
+                    break;
+                }
+                const uint32_t slot = sd.slot;
+                if (!wait_warp(&sh.win_full[slot], (full_par >> slot) & 1u)) break;
+                full_par ^= 1u << slot;
+                const Window v = sh.desc[slot];
+                const ulonglong2 *const tb = tab_of(s, b);
+                const uint32_t *const tg = tag_of(s, b);
+                const uint16_t *const ab = act_of(s, b);
+                const uint32_t n_act = sd.n_act;
+                const bool after = sd.layer >= 0;
+                const uint32_t stamp = st;
+                // planes of qubit x in this step (0 unless x is active)
+                auto planes = [&](uint32_t x) -> ulonglong2 {
+                    const uint32_t t = tg[x];
+                    const ulonglong2 p = tb[x];
+                    return t == stamp ? p : make_ulonglong2(0ull, 0ull);
+                };
+                auto row_word = [&](uint2 r, uint32_t q) -> unsigned long long {
+                    const uint32_t kind = row_kind(r);
+                    if (kind < K_XERR) return 0ull;
+                    const uint32_t ra = row_a(r), rb = row_b(r);
+                    const bool two = kind == K_DEP2;
+                    const ulonglong2 pa = planes(ra);
+                    const ulonglong2 pb = two ? planes(rb) : make_ulonglong2(0ull, 0ull);
+                    if (two && q == rb && (pa.x | pa.y) != 0ull) return 0ull;
+                    const uint32_t nc = two ? nc_dep2 : (kind == K_DEP1 ? nc_dep1 : 1u);
+                    if (l16 >= nc) return 0ull;
+                    const unsigned long long codes =
+                        two ? 0x0EBF7D639CA25184ull : (kind == K_DEP1 ? 0x321ull : (kind == K_XERR ? 1ull : 2ull));
+                    const uint32_t code = (uint32_t)(codes >> (4u * l16)) & 0xFu;
+                    return ((code & 1u) ? pa.x : 0ull) ^ ((code & 2u) ? pa.y : 0ull) ^ ((code & 4u) ? pb.x : 0ull) ^
+                           ((code & 8u) ? pb.y : 0ull);
+                };
+                auto emit = [&](uint2 r, unsigned long long w) {
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, w != 0ull);
+                    if (m == 0u) return;
+                    const uint32_t cnt = (uint32_t)__popc(m);
+                    if (!warp_room(cnt)) return;
+                    if (w != 0ull) {
+                        const uint32_t mech = mech_base + r.y + l16;
+                        B.records[ck_pos + __popc(m & lt_mask)] =
+                            make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+                        atomicAdd(&B.mech_cnt[mech], 1u);
+                    }
+                    ck_pos += cnt;
+                };
+                warp_prefetch();
+                for (uint32_t base = 2u * ew; base < n_act; base += 2u * NE) {
+                    const uint32_t c = base + half;
+                    const bool valid = c < n_act;
+                    const uint32_t q = valid ? ab[c] : 0u;
+                    uint32_t a0 = 0, a1 = 0;
+                    if (after) { a0 = v.aoff[q]; a1 = v.aoff[q + 1u]; }
+                    const uint32_t b0 = v.boff[q], b1 = v.boff[q + 1u];
+                    const uint32_t na = valid ? a1 - a0 : 0u;
+                    const uint32_t n = valid ? na + (b1 - b0) : 0u;
+                    const uint32_t nmax = max(n, __shfl_xor_sync(0xFFFFFFFFu, n, 16));
+                    for (uint32_t i = 0; i < nmax; i += 2u) {
+                        uint2 r0 = make_uint2(0u, 0u), r1 = make_uint2(0u, 0u);
+                        if (i < n) r0 = v.lists[i < na ? a0 + i : v.n_after + b0 + (i - na)];
+                        if (i + 1u < n) r1 = v.lists[i + 1u < na ? a0 + i + 1u : v.n_after + b0 + (i + 1u - na)];
+                        const unsigned long long w0 = row_word(r0, q), w1 = row_word(r1, q);
+                        emit(r0, w0);
+                        emit(r1, w1);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0u) {
+                    mbar_arrive(&sh.tab_free[b]);
+                    mbar_arrive(&sh.win_free[slot]);
+                }
+                st++;
+            }
+        } else {
+            // ---- producer: windows lmax, lmax - 1, ..., -1 until the walker
+            // leaves the column, each into a slot its last window released
+            auto post = [&](int L) {
+                const uint32_t need = L > 0 ? (uint32_t)L : 0u;
+                if (seg_lo == 0xFFFFFFFFu || need < seg_lo || (uint32_t)L + 1u >= seg_lo + (uint32_t)kSegCache) {
+                    seg_lo = (uint32_t)L + 2u > (uint32_t)kSegCache ? (uint32_t)L + 2u - (uint32_t)kSegCache : 0u;
+                    const uint32_t n = min((uint32_t)kSegCache, C.n_layers + 1u - seg_lo);
+                    __syncwarp();
+                    for (uint32_t i = lane; i < n; i += 32u) s.segc[i] = seg_g[seg_lo + i];
+                    __syncwarp();
+                }
+                if (lane != 0u) return;
+                const uint4 s1 = s.segc[L + 1 - (int)seg_lo];
+                const uint32_t n_after = L >= 0 ? s.segc[L - (int)seg_lo].y : 0u;
+                const uint32_t list_start = 2u * s1.x - n_after;
+                const uint32_t list_n = n_after + s1.z;
+                const uint32_t slot = slot_of(L);
+                Window &d = sh.desc[slot];
+                d.n_after = n_after;
+                if (nbuf >= 2u && list_n + 1u <= list_cap) {
+                    unsigned char *dst = s.win + (size_t)slot * wbytes;
+                    const unsigned char *qsrc = L >= 0 ? qbase + (size_t)L * geo.bytes + 2u * geo.qb : qbase;
+                    const uint32_t qbytes = L >= 0 ? 4u * geo.nq4 + 4u * geo.qb : 2u * geo.qb;
+                    const uint32_t delta = list_start & 1u;
+                    const uint32_t lbytes = list_n ? ((list_n + delta) * 8u + 15u) & ~15u : 0u;
+                    d.lists = reinterpret_cast<const uint2 *>(dst + windex) + delta;
+                    if (L >= 0) {
+                        d.gate = reinterpret_cast<const uint32_t *>(dst);
+                        d.aoff = reinterpret_cast<const uint16_t *>(dst + 4u * geo.nq4);
+                        d.boff = d.aoff + geo.qb;
+                    } else {
+                        d.gate = nullptr;
+                        d.aoff = nullptr;
+                        d.boff = reinterpret_cast<const uint16_t *>(dst);
+                    }
+                    mbar_expect_tx(&sh.win_full[slot], qbytes + lbytes);
+                    bulk_load(dst, qsrc, qbytes, &sh.win_full[slot]);
+                    if (lbytes) bulk_load(dst + windex, lbase + list_start - delta, lbytes, &sh.win_full[slot]);
+                } else {
+                    d.lists = lbase + list_start;
+                    if (L >= 0) {
+                        const unsigned char *p = qbase + (size_t)L * geo.bytes + 2u * geo.qb;
+                        d.gate = reinterpret_cast<const uint32_t *>(p);
+                        d.aoff = reinterpret_cast<const uint16_t *>(p + 4u * geo.nq4);
+                        d.boff = d.aoff + geo.qb;
+                    } else {
+                        d.gate = nullptr;
+                        d.aoff = nullptr;
+                        d.boff = reinterpret_cast<const uint16_t *>(qbase);
+                    }
+                    mbar_arrive(&sh.win_full[slot]);
+                }
+            };
+            volatile uint32_t *const done_v = &sh.walk_done;
+            int Lp = (int)lmax;
+            while (Lp >= -1) {
+                const uint32_t slot = slot_of(Lp);
+                if ((free_pend >> slot) & 1u) {
+                    uint32_t got = 0;
+                    if (lane == 0u) {
+                        uint32_t it = 0;
+                        for (; it < (1u << 22); it++) {
+                            if (mbar_try_wait(&sh.win_free[slot], (free_par >> slot) & 1u)) { got = 1u; break; }
+                            if ((it & 15u) == 15u && (*done_v || *tmo_v)) break;
+                        }
+                        if (it == (1u << 22)) *tmo_v = 1u;
+                    }
+                    if (!__shfl_sync(0xFFFFFFFFu, got, 0)) break;
+                    free_par ^= 1u << slot;
+                    free_pend &= ~(1u << slot);
+                }
+                const uint32_t stop = lane == 0u ? (*done_v | *tmo_v) : 0u;
+                if (__shfl_sync(0xFFFFFFFFu, stop, 0)) break;
+                post(Lp);
+                free_pend |= 1u << slot;
+                post_par ^= 1u << slot;
+                posted_any |= 1u << slot;
+                Lp--;
+            }
+            if (lane == 0u) sh.posted_lo = Lp + 1;
+        }
+        __syncthreads();
+        if (!sh.tmo) {
+            // windows posted below the walk's last layer were never used:
+            // their copies land (consumers absorb the phase), and no release
+            // comes for them
+            const int stop_layer = sh.stop_layer, posted_lo = sh.posted_lo;
+            for (int k2 = stop_layer - 1; k2 >= posted_lo; k2--) {
+                const uint32_t slot = slot_of(k2);
+                if (producer) {
+                    free_pend &= ~(1u << slot);
+                } else {
+                    if (!wait_bar(&sh.win_full[slot], (full_par >> slot) & 1u)) break;
+                    full_par ^= 1u << slot;
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.tmo) {
+            if (threadIdx.x == 0) report(B.status, GP_ERR_TIMEOUT, 1u, gcol, 0u);
+            break;
+        }
+    }
+    // copies still in flight (after a timeout) land before the block exits
+    if (producer && lane == 0u) {
+        for (uint32_t i = 0; i < nring; i++)
+            if ((posted_any >> i) & 1u) mbar_wait_bounded(&sh.win_full[i], ((post_par >> i) & 1u) ^ 1u);
+    }
+}
+
 }  // namespace
 
 size_t stage1_dynamic_smem_limit(int device) {
@@ -631,40 +1239,55 @@ size_t stage1_dynamic_smem_limit(int device) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
     cudaFuncAttributes fa{};
     size_t stat = 0;
-    for (uint32_t t : {128u, 256u, 512u, 1024u}) {
-        if (cudaFuncGetAttributes(&fa, stage1_kernel_ptr(t)) != cudaSuccess) return 0;
-        stat = std::max(stat, fa.sharedSizeBytes);
-    }
+    for (uint32_t split : {0u, 1u})
+        for (uint32_t t : {128u, 256u, 512u, 1024u}) {
+            if (cudaFuncGetAttributes(&fa, stage1_kernel_ptr(t, split)) != cudaSuccess) return 0;
+            stat = std::max(stat, fa.sharedSizeBytes);
+        }
     return (size_t)optin > stat ? (size_t)optin - stat : 0;
 }
 
 Stage1Shape stage1_shape(uint32_t maxq, uint32_t blocks_per_sm, size_t limit) {
     Stage1Shape sh{};
-    const size_t base = smem_base_bytes(maxq);
     // k blocks per SM share the SM's shared memory (1 KB of it reserved per block)
     const size_t per_sm = limit + 1024;
     const size_t budget = blocks_per_sm > 1 ? std::min(limit, per_sm / blocks_per_sm - 1024) : limit;
     const uint32_t wi = window_index_bytes(maxq);
-    for (uint32_t nbuf = 3; nbuf >= 2; nbuf--) {
-        if (budget < base + (size_t)nbuf * (wi + 512 * 8)) continue;
-        size_t cap = (budget - base) / nbuf;
-        cap = (cap - wi) / 8;
-        cap = std::min<size_t>(cap, 4096) & ~(size_t)15;
-        sh.nbuf = nbuf;
-        sh.list_cap = (uint32_t)cap;
-        sh.wbytes = wi + (uint32_t)cap * 8;
-        sh.smem = base + (size_t)nbuf * sh.wbytes;
-        return sh;
+    // the role-split walk when its tables and at least two windows fit, else
+    // the block-wide walk
+    for (int split = 1; split >= 0; split--) {
+        const size_t base = split ? split_base_bytes(maxq) : smem_base_bytes(maxq);
+        for (uint32_t nbuf = split ? 4u : 3u; nbuf >= 2; nbuf--) {
+            if (budget < base + (size_t)nbuf * (wi + 512 * 8)) continue;
+            size_t cap = (budget - base) / nbuf;
+            cap = (cap - wi) / 8;
+            cap = std::min<size_t>(cap, 4096) & ~(size_t)15;
+            sh.nbuf = nbuf;
+            sh.list_cap = (uint32_t)cap;
+            sh.wbytes = wi + (uint32_t)cap * 8;
+            sh.smem = base + (size_t)nbuf * sh.wbytes;
+            sh.split = (uint32_t)split;
+            return sh;
+        }
     }
     // no room for window buffers: every window is read from global memory
     sh.nbuf = 0;
     sh.list_cap = 0;
     sh.wbytes = 0;
-    sh.smem = base;
+    sh.smem = smem_base_bytes(maxq);
+    sh.split = 0;
     return sh;
 }
 
-const void *stage1_kernel_ptr(uint32_t threads) {
+const void *stage1_kernel_ptr(uint32_t threads, uint32_t split) {
+    if (split) {
+        switch (threads) {
+        case 128: return (const void *)stage1_split_kernel<128>;
+        case 256: return (const void *)stage1_split_kernel<256>;
+        case 1024: return (const void *)stage1_split_kernel<1024>;
+        default: return (const void *)stage1_split_kernel<512>;
+        }
+    }
     switch (threads) {
     case 128: return (const void *)stage1_kernel<128>;
     case 256: return (const void *)stage1_kernel<256>;
@@ -680,11 +1303,20 @@ void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t m
     const uint64_t warps = (uint64_t)grid * (threads / 32u - 1u);
     uint32_t wchunk = (uint32_t)std::min<uint64_t>(256, kPoolSlack / std::max<uint64_t>(warps, 1)) & ~31u;
     if (wchunk < 32u) wchunk = 32u;
-    switch (threads) {
-    case 128: stage1_kernel<128><<<grid, 128, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
-    case 256: stage1_kernel<256><<<grid, 256, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
-    case 1024: stage1_kernel<1024><<<grid, 1024, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
-    default: stage1_kernel<512><<<grid, 512, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+    if (sh.split) {
+        switch (threads) {
+        case 128: stage1_split_kernel<128><<<grid, 128, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 256: stage1_split_kernel<256><<<grid, 256, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 1024: stage1_split_kernel<1024><<<grid, 1024, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        default: stage1_split_kernel<512><<<grid, 512, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        }
+    } else {
+        switch (threads) {
+        case 128: stage1_kernel<128><<<grid, 128, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 256: stage1_kernel<256><<<grid, 256, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 1024: stage1_kernel<1024><<<grid, 1024, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        default: stage1_kernel<512><<<grid, 512, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        }
     }
     *launches += 1;
 }

@@ -11,7 +11,7 @@ if not torch.cuda.is_available():
 import oracle
 from paper_2604_16613_gb300 import circuits as C
 from paper_2604_16613_gb300.autotune import autotune
-from paper_2604_16613_gb300.dem import DemFunction, DeviceCircuit, Driver
+from paper_2604_16613_gb300.dem import Bounds, DemFunction, DeviceCircuit, Driver
 
 from parity import compare_edges, oracle_edges
 
@@ -120,3 +120,24 @@ def test_autotune_does_not_change_results():
         other = drv.compile(dcs, noise).to_host()
         for k in base:
             assert np.array_equal(base[k], other[k]), (shape, k)
+
+
+def test_block_wide_walk_equals_role_split_walk():
+    """Stage 1 has two walks: the role-split one (a walker warp and emitter
+    warps, used when its per-qubit tables fit in shared memory) and the
+    block-wide one (used above that, here forced by bounds for 4096 qubits).
+    Both give the same compile bit for bit, at every launch shape."""
+    circs = [C.rotated_surface_code_memory(7, 7, C.NoiseModel.uniform(1e-3)),
+             C.concatenated_adaptive_branch(4, 5, seed=7, noise=C.NoiseModel.uniform(1e-3)),
+             C.bb_memory(3, C.NoiseModel.uniform(1e-3), seed=3)]
+    noise = torch.tensor(f32(np.concatenate([c.default_noise for c in circs])), device="cuda")
+    dcs = [DeviceCircuit(c) for c in circs]
+    split = Driver.for_circuits(circs).compile(dcs, noise).to_host()
+    bd = Bounds.for_circuits(circs)
+    bd.max_qubits = 4096
+    wide = Driver(bd)
+    for shape in [(512, 1, 256, 16), (256, 2, 256, 16), (128, 1, 256, 16)]:
+        wide.set_tuning(*shape)
+        got = wide.compile(dcs, noise).to_host()
+        for k in split:
+            assert np.array_equal(split[k], got[k]), (shape, k)
