@@ -663,9 +663,10 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
 // windows.  The snapshot tables are double-buffered by step parity and
 // tagged with the step that wrote an entry (a qubit whose tag differs is not
 // active in that step), so they are never cleared.  mbarriers order the
-// roles: window full (producer -> walker, emitters), window free (walker,
-// emitters -> producer), table full (walker -> emitters), table free
-// (emitters -> walker); every wait is bounded.
+// roles: window full (producer -> walker), window free (walker, emitters ->
+// producer), table full (walker -> emitters: it also carries the window,
+// which the walker saw land before publishing), table free (emitters ->
+// walker); every wait is bounded.
 // ---------------------------------------------------------------------------
 struct SplitSmem {
     ulonglong2 *pl;                 // walker: per qubit {X plane, Z plane}
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
     __syncthreads();
 
     // per-thread barrier phases (bit i: slot or buffer i)
-    uint32_t full_par = 0;                  // walker, emitters: window full
+    uint32_t full_par = 0;                  // walker: window full
     uint32_t free_par = 0, free_pend = 0;   // producer: window free; slots awaiting a release
     uint32_t post_par = 0, posted_any = 0;  // producer: parity of the posts per slot
     uint32_t tfull_par = 0;                 // emitters: table full
@@ -796,6 +797,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
     // the same, by every lane of a warp with one outcome for all (the loops
     // around it use warp-wide votes)
     auto wait_warp = [&](unsigned long long *bar, uint32_t parity) -> bool {
+        if (__all_sync(0xFFFFFFFFu, mbar_try_wait(bar, parity))) return true;     // usually done already
         return __all_sync(0xFFFFFFFFu, wait_bar(bar, parity));
     };
     auto warp_room = [&](uint32_t need) -> bool {
@@ -867,8 +869,47 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
             uint32_t n_prev = 0, n_add = 0, cur = n_ent;
             int L = (int)lmax;
             bool ok = true;
+            uint32_t slot = slot_of(L);
+            // the gates of L undone for one candidate (registers from the
+            // activity pass): the owner of a two-qubit gate (its active
+            // qubit, or its control / first qubit when both are active)
+            // updates both planes; returns the partner it touched
+            auto undo = [&](uint32_t q, ulonglong2 P, uint32_t g, bool act) -> uint32_t {
+                if (!act) return kNone;
+                const uint32_t k = g >> 28, pay = g & 0x0FFFFFFFu;
+                if (k >= GV_CX_C) {
+                    const bool pact = s.bits[pay] == kActive;
+                    if (pact && (k == GV_CX_T || k == GV_CZ_B)) return kNone;
+                    const ulonglong2 Q = s.pl[pay];
+                    const bool cxc = k == GV_CX_C, cxt = k == GV_CX_T, cz = !cxc && !cxt;
+                    // CX(c,t): x_c ^= x_t, z_t ^= z_c; CZ(a,b): x_a ^= z_b, x_b ^= z_a
+                    const unsigned long long ox = P.x ^ (cxc ? Q.x : 0ull) ^ (cz ? Q.y : 0ull);
+                    const unsigned long long oz = P.y ^ (cxt ? Q.y : 0ull);
+                    const unsigned long long px = Q.x ^ (cxt ? P.x : 0ull) ^ (cz ? P.y : 0ull);
+                    const unsigned long long pz = Q.y ^ (cxc ? P.y : 0ull);
+                    s.pl[q] = make_ulonglong2(ox, oz);
+                    s.pl[pay] = make_ulonglong2(px, pz);
+                    return pay;
+                }
+                if (k == K_H) { s.pl[q] = make_ulonglong2(P.y, P.x); return kNone; }
+                if (k == K_S) { s.pl[q] = make_ulonglong2(P.x ^ P.y, P.y); return kNone; }
+                if (k == GV_NONE) return kNone;
+                // measurements and resets
+                ulonglong2 t = P;
+                if (k <= K_MR) {
+                    if (t.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)L, gcol);
+                    if (k != K_M) t = make_ulonglong2(0ull, 0ull);
+                    if (k != K_R) t.x ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
+                } else {
+                    if (t.x != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)L, gcol);
+                    if (k != K_MX) t = make_ulonglong2(0ull, 0ull);
+                    if (k != K_RX) t.y ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
+                }
+                s.pl[q] = t;
+                return kNone;
+            };
             for (;;) {
-                const uint32_t slot = slot_of(L), b = st & 1u;
+                const uint32_t b = st & 1u;
                 if (!wait_warp(&sh.win_full[slot], (full_par >> slot) & 1u)) { ok = false; break; }
                 full_par ^= 1u << slot;
                 const Window v = sh.desc[slot];
@@ -877,21 +918,24 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     tfree_par ^= 1u << b;
                 }
                 tfree_pend |= 1u << b;
-                // pass 1: activity and snapshot
                 const uint16_t *prev = act_of(s, b ^ 1u);
                 ulonglong2 *const tb = tab_of(s, b);
                 uint32_t *const tg = tag_of(s, b);
                 uint16_t *const ab = act_of(s, b);
                 const uint32_t n_cand = n_prev + n_add;
-                uint32_t n_act = 0;
-                for (uint32_t base = 0; base < n_cand; base += 64u) {
-                    const uint32_t i0 = base + lane, i1 = i0 + 32u;
-                    uint32_t q0 = 0, q1 = 0;
+                uint32_t n_act = 0, n_new = 0;
+                // activity and snapshot of candidates c0, c1 (one lane's pair)
+                auto activity = [&](uint32_t i0, uint32_t i1, uint32_t &q0, uint32_t &q1, ulonglong2 &p0, ulonglong2 &p1,
+                                    uint32_t &g0, uint32_t &g1, bool &a0, bool &a1) {
+                    q0 = q1 = 0;
                     if (i0 < n_cand) q0 = i0 < n_prev ? prev[i0] : s.add[i0 - n_prev];
                     if (i1 < n_cand) q1 = i1 < n_prev ? prev[i1] : s.add[i1 - n_prev];
-                    const ulonglong2 p0 = s.pl[q0], p1 = s.pl[q1];
-                    const bool a0 = i0 < n_cand && (p0.x | p0.y) != 0ull;
-                    const bool a1 = i1 < n_cand && (p1.x | p1.y) != 0ull;
+                    p0 = s.pl[q0];
+                    p1 = s.pl[q1];
+                    g0 = L >= 0 ? v.gate[q0] : 0u;
+                    g1 = L >= 0 ? v.gate[q1] : 0u;
+                    a0 = i0 < n_cand && (p0.x | p0.y) != 0ull;
+                    a1 = i1 < n_cand && (p1.x | p1.y) != 0ull;
                     if (i0 < n_cand) s.bits[q0] = a0 ? kActive : (unsigned char)0;
                     if (i1 < n_cand) s.bits[q1] = a1 ? kActive : (unsigned char)0;
                     if (a0) { tb[q0] = p0; tg[q0] = st; }
@@ -903,82 +947,64 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     n_act += __popc(m0);
                     if (a1) ab[n_act + __popc(m1 & lt_mask)] = (uint16_t)q1;
                     n_act += __popc(m1);
-                }
-                if (lane == 0u) sh.step[b] = StepDesc{L, n_act, slot, 0u};
-                __syncwarp();
-                if (lane == 0u) mbar_arrive(&sh.tab_full[b]);
-                // pass 2: the gates of L undone on the active qubits; inactive
-                // partners of their two-qubit gates go on the next candidates
-                uint32_t n_new = 0;
-                if (L >= 0) {
-                    for (uint32_t base = 0; base < n_act; base += 32u) {
-                        const uint32_t i = base + lane;
-                        uint32_t partner = kNone;
-                        if (i < n_act) {
-                            const uint32_t q = ab[i];
-                            const uint32_t g = v.gate[q];
-                            const uint32_t k = g >> 28, pay = g & 0x0FFFFFFFu;
-                            switch (k) {
-                            case K_H: { const ulonglong2 t = s.pl[q]; s.pl[q] = make_ulonglong2(t.y, t.x); break; }
-                            case K_S: { ulonglong2 t = s.pl[q]; t.x ^= t.y; s.pl[q] = t; break; }
-                            case GV_CX_C: {
-                                ulonglong2 c_ = s.pl[q], t_ = s.pl[pay];
-                                c_.x ^= t_.x;
-                                t_.y ^= c_.y;
-                                s.pl[q] = c_;
-                                s.pl[pay] = t_;
-                                partner = pay;
-                                break;
-                            }
-                            case GV_CX_T: {
-                                if (s.bits[pay] == kActive) break;    // undone from the active control
-                                ulonglong2 c_ = s.pl[pay], t_ = s.pl[q];
-                                c_.x ^= t_.x;
-                                t_.y ^= c_.y;
-                                s.pl[pay] = c_;
-                                s.pl[q] = t_;
-                                partner = pay;
-                                break;
-                            }
-                            case GV_CZ_B:
-                                if (s.bits[pay] == kActive) break;    // undone from the active first qubit
-                                // fall through
-                            case GV_CZ_A: {
-                                ulonglong2 a_ = s.pl[q], b_ = s.pl[pay];
-                                const unsigned long long za = a_.y, zb = b_.y;
-                                a_.x ^= zb;
-                                b_.x ^= za;
-                                s.pl[q] = a_;
-                                s.pl[pay] = b_;
-                                partner = pay;
-                                break;
-                            }
-                            case K_R: case K_M: case K_MR: {
-                                ulonglong2 t = s.pl[q];
-                                if (t.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)L, gcol);
-                                if (k != K_M) t = make_ulonglong2(0ull, 0ull);
-                                if (k != K_R) t.x ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
-                                s.pl[q] = t;
-                                break;
-                            }
-                            case K_RX: case K_MX: case K_MRX: {
-                                ulonglong2 t = s.pl[q];
-                                if (t.x != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)L, gcol);
-                                if (k != K_MX) t = make_ulonglong2(0ull, 0ull);
-                                if (k != K_RX) t.y ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
-                                s.pl[q] = t;
-                                break;
-                            }
-                            default: break;
-                            }
-                        }
-                        const bool add = partner != kNone && s.bits[partner] == 0;
-                        if (add) s.bits[partner] = kAdded;
-                        const unsigned m = __ballot_sync(0xFFFFFFFFu, add);
-                        if (add) s.add[n_new + __popc(m & lt_mask)] = (uint16_t)partner;
-                        n_new += __popc(m);
+                };
+                auto append = [&](uint32_t partner) {
+                    const bool add = partner != kNone && s.bits[partner] == 0;
+                    if (add) s.bits[partner] = kAdded;
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, add);
+                    if (add) s.add[n_new + __popc(m & lt_mask)] = (uint16_t)partner;
+                    n_new += __popc(m);
+                };
+                auto publish = [&]() {
+                    if (lane == 0u) sh.step[b] = StepDesc{L, n_act, slot, 0u};
+                    __syncwarp();
+                    if (lane == 0u) mbar_arrive(&sh.tab_full[b]);
+                };
+                if (n_cand <= 32u) {
+                    // the step's candidates stay in registers (one per lane)
+                    uint32_t q0 = 0;
+                    if (lane < n_cand) q0 = lane < n_prev ? prev[lane] : s.add[lane - n_prev];
+                    const ulonglong2 p0 = s.pl[q0];
+                    const uint32_t g0 = L >= 0 ? v.gate[q0] : 0u;
+                    const bool a0 = lane < n_cand && (p0.x | p0.y) != 0ull;
+                    if (lane < n_cand) s.bits[q0] = a0 ? kActive : (unsigned char)0;
+                    if (a0) { tb[q0] = p0; tg[q0] = st; }
+                    if (L < 0 && a0 && p0.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, 0xFFFFFFFFu, gcol);
+                    const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0);
+                    if (a0) ab[__popc(m0 & lt_mask)] = (uint16_t)q0;
+                    n_act = __popc(m0);
+                    publish();
+                    if (L >= 0) append(undo(q0, p0, g0, a0));
+                } else if (n_cand <= 64u) {
+                    // two per lane
+                    uint32_t q0, q1, g0, g1;
+                    ulonglong2 p0, p1;
+                    bool a0, a1;
+                    activity(lane, lane + 32u, q0, q1, p0, p1, g0, g1, a0, a1);
+                    publish();
+                    if (L >= 0) {
+                        append(undo(q0, p0, g0, a0));
+                        append(undo(q1, p1, g1, a1));
                     }
-                    // measurements of the column at L on inactive qubits
+                } else {
+                    for (uint32_t base = 0; base < n_cand; base += 64u) {
+                        uint32_t q0, q1, g0, g1;
+                        ulonglong2 p0, p1;
+                        bool a0, a1;
+                        activity(base + lane, base + lane + 32u, q0, q1, p0, p1, g0, g1, a0, a1);
+                    }
+                    publish();
+                    if (L >= 0) {
+                        for (uint32_t base = 0; base < n_act; base += 32u) {
+                            const uint32_t i = base + lane;
+                            const uint32_t q = i < n_act ? ab[i] : 0u;
+                            const ulonglong2 P = s.pl[q];
+                            append(undo(q, P, i < n_act ? v.gate[q] : 0u, i < n_act));
+                        }
+                    }
+                }
+                if (L >= 0) {
+                // measurements of the column at L on inactive qubits
                     if (cur > 0u && s.ent_l[cur - 1u] == (uint32_t)L) {
                         uint32_t l0 = 0, h0 = cur;
                         while (l0 < h0) {
@@ -1010,6 +1036,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                 __syncwarp();
                 if (lane == 0u) mbar_arrive(&sh.win_free[slot]);
                 st++;
+                slot = slot == 0u ? nring - 1u : slot - 1u;   // window L - 1
                 n_prev = n_act;
                 n_add = n_new;
                 if (L < 0) break;
@@ -1049,9 +1076,10 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     st++;
                     break;
                 }
+                // the walker waited for the window before it published the
+                // step, so the window's contents are visible here through the
+                // step's release and acquire
                 const uint32_t slot = sd.slot;
-                if (!wait_warp(&sh.win_full[slot], (full_par >> slot) & 1u)) break;
-                full_par ^= 1u << slot;
                 const Window v = sh.desc[slot];
                 const ulonglong2 *const tb = tab_of(s, b);
                 const uint32_t *const tg = tag_of(s, b);
@@ -1213,7 +1241,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                 const uint32_t slot = slot_of(k2);
                 if (producer) {
                     free_pend &= ~(1u << slot);
-                } else {
+                } else if (walker) {
                     if (!wait_bar(&sh.win_full[slot], (full_par >> slot) & 1u)) break;
                     full_par ^= 1u << slot;
                 }
