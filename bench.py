@@ -445,7 +445,7 @@ def run_ours(args):
     hbm_peak, peak_kind = peaks()
     achieved = alg[dom] / (stage_mean[dom] * 1e-6) / 1e9
     b_alg_pipeline = b_in + n_mech * 32 + 2 * 12 * words + n_edges * 16 + 4 * host["det_idx"].size
-    kernel_name = {"stage1": "stage1_kernel", "group": "group_kernel", "lowering": "tile_lower_kernel",
+    kernel_name = {"stage1": "stage1_split_kernel", "group": "group_kernel", "lowering": "tile_lower_kernel",
                    "compact": "compact_write_kernel"}[dom]
     traffic = measured_traffic(kernel_name)
 
