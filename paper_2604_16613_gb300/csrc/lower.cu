@@ -3,7 +3,7 @@
 // backward wave runs).
 //
 // Four launches, no device-wide waits:
-//   tile_count   per tile of 4096 rows: counts of TICKs, measurements,
+//   tile_count   per tile of 1024 rows: counts of TICKs, measurements,
 //                detectors and mechanisms (components at the chosen level)
 //   tile_scan    one block: per-circuit scan of the tile counts, circuit
 //                totals and batch offsets, capacity checks
@@ -39,6 +39,9 @@ __device__ __forceinline__ uint4 row_counts(uint4 op, uint32_t level) {
 __device__ __forceinline__ uint4 add4(uint4 a, uint4 b) {
     return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
+__device__ __forceinline__ uint4 sub4(uint4 a, uint4 b) {
+    return make_uint4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
 
 __global__ void __launch_bounds__(kLowerThreads) tile_count_kernel(Buffers B) {
     const Params &P = *B.params;
@@ -68,24 +71,44 @@ __global__ void __launch_bounds__(kLowerThreads) tile_count_kernel(Buffers B) {
     }
 }
 
-// One block.  Thread b scans the tiles of circuit b (tiles of a circuit are
-// contiguous); then block scans give the batch offsets.
+// One block.  An exclusive scan of the tile sums over the whole batch gives
+// each tile's offset (tiles of a circuit are contiguous, so a tile's offset
+// within its circuit is its offset less that of the circuit's first tile);
+// then block scans over the circuits give the batch offsets.
 __global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
     const Params &P = *B.params;
     __shared__ uint32_t warp_tmp[kLowerThreads / 32];
     __shared__ uint32_t carry_layer, carry_meas, carry_mech;
     __shared__ unsigned long long carry_qidx;
-    if (threadIdx.x == 0) { carry_layer = 0; carry_meas = 0; carry_mech = 0; carry_qidx = 0; }
+    __shared__ uint4 carry4;
+    if (threadIdx.x == 0) {
+        carry_layer = 0; carry_meas = 0; carry_mech = 0; carry_qidx = 0;
+        carry4 = make_uint4(0, 0, 0, 0);
+    }
     __syncthreads();
+    for (uint32_t base = 0; base < P.n_tiles; base += kLowerThreads) {
+        const uint32_t t = base + threadIdx.x;
+        const uint4 v = t < P.n_tiles ? B.tile_sums[t] : make_uint4(0, 0, 0, 0);
+        uint4 ex, tot4;
+        ex.x = block_exclusive_scan<kLowerThreads>(v.x, warp_tmp, tot4.x);
+        ex.y = block_exclusive_scan<kLowerThreads>(v.y, warp_tmp, tot4.y);
+        ex.z = block_exclusive_scan<kLowerThreads>(v.z, warp_tmp, tot4.z);
+        ex.w = block_exclusive_scan<kLowerThreads>(v.w, warp_tmp, tot4.w);
+        const uint4 c = carry4;
+        if (t < P.n_tiles) B.tile_off[t] = add4(ex, c);
+        __syncthreads();
+        if (threadIdx.x == 0) carry4 = add4(c, tot4);
+        __syncthreads();
+    }
     for (uint32_t base = 0; base < P.n_circuits; base += kLowerThreads) {
         const uint32_t b = base + threadIdx.x;
         uint32_t layers = 0, meas = 0, mech = 0, qblocks = 0;
         if (b < P.n_circuits) {
             CircuitDev &C = B.circ[b];
             uint4 run = make_uint4(0, 0, 0, 0);
-            for (uint32_t t = C.tile_first; t < C.tile_first + C.n_tiles; t++) {
-                B.tile_off[t] = run;
-                run = add4(run, B.tile_sums[t]);
+            if (C.n_tiles) {
+                const uint32_t f = C.tile_first, l = f + C.n_tiles - 1u;
+                run = sub4(add4(B.tile_off[l], B.tile_sums[l]), B.tile_off[f]);
             }
             if (run.z != C.n_det) report(B.status, GP_ERR_INVALID, 1u, b, run.z);
             C.n_layers = run.x + 1;
@@ -168,7 +191,7 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
     for (uint32_t r = r0; r < r1; r++) mine = add4(mine, row_counts(C.ops[r], P.level));
     __shared__ uint32_t warp_tmp[kLowerThreads / 32];
     uint32_t tot;
-    const uint4 toff = B.tile_off[t];
+    const uint4 toff = sub4(B.tile_off[t], B.tile_off[C.tile_first]);
     uint4 run;
     run.x = block_exclusive_scan<kLowerThreads>(mine.x, warp_tmp, tot) + toff.x;
     run.y = block_exclusive_scan<kLowerThreads>(mine.y, warp_tmp, tot) + toff.y;
