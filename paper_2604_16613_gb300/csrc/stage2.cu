@@ -46,8 +46,14 @@ __device__ __forceinline__ uint2 block_scan2(uint2 v, uint32_t *tmp, uint2 &tota
 
 // ---- hierarchical exclusive scan of uint2 values ---------------------------
 // level 1: per block of 2048 values, the sum
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint2 *in, const uint32_t *n_ptr,
-                                                                   uint2 *bsum, const Status *st) {
+// (in == nullptr: the values are the word counts `cnt`, second channel 0)
+__device__ __forceinline__ uint2 scan_in(const uint2 *in, const uint32_t *cnt, uint32_t i) {
+    return in ? in[i] : make_uint2(cnt[i], 0u);
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint2 *in, const uint32_t *cnt,
+                                                                   const uint32_t *n_ptr, uint2 *bsum,
+                                                                   const Status *st) {
     if (st->code != 0u) return;
     const uint32_t n = *n_ptr;
     const uint32_t b0 = blockIdx.x * kScanBlock;
@@ -55,7 +61,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint2 *
     uint2 acc = make_uint2(0, 0);
     for (int k = 0; k < kScanPer; k++) {
         const uint32_t i = b0 + threadIdx.x * kScanPer + k;
-        if (i < n) acc = add2(acc, in[i]);
+        if (i < n) acc = add2(acc, scan_in(in, cnt, i));
     }
     __shared__ uint32_t tmp[kScanThreads / 32];
     uint2 tot;
@@ -130,9 +136,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_down2_kernel(const uint32_t
 }
 
 // level 1 down: exclusive prefix of every value; out[n] = total
-__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in, const uint32_t *n_ptr,
-                                                                 const uint2 *bsum, const uint2 *total,
-                                                                 uint2 *out, const Status *st) {
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in, const uint32_t *cnt,
+                                                                 const uint32_t *n_ptr, const uint2 *bsum,
+                                                                 const uint2 *total, uint2 *out, const Status *st) {
     if (st->code != 0u) return;
     const uint32_t n = *n_ptr;
     const uint32_t b0 = blockIdx.x * kScanBlock;
@@ -142,7 +148,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in
     uint2 acc = make_uint2(0, 0);
     for (int k = 0; k < kScanPer; k++) {
         const uint32_t i = b0 + threadIdx.x * kScanPer + k;
-        v[k] = i < n ? in[i] : make_uint2(0, 0);
+        v[k] = i < n ? scan_in(in, cnt, i) : make_uint2(0, 0);
         acc = add2(acc, v[k]);
     }
     __shared__ uint32_t tmp[kScanThreads / 32];
@@ -157,14 +163,6 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in
 
 
 // ---- per-mechanism words ----------------------------------------------------
-// word counts as scan input
-__global__ void counts_kernel(Buffers B) {
-    if (B.status->code != 0u) return;
-    const uint32_t N = B.status->n_mech;
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x)
-        B.scan_val[m] = make_uint2(B.mech_cnt[m], 0u);
-}
-
 __global__ void scatter_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const Params &P = *B.params;
@@ -412,27 +410,33 @@ __global__ void init_table_kernel(TabSlot *t, size_t n) {
 }  // namespace
 
 // exclusive scan of n (read on the device) uint2 values: out[i] = sum of
-// in[0..i), out[n] = the total; three levels of 2048-element blocks
-void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
-                 cudaStream_t s, uint32_t *launches) {
+// in[0..i), out[n] = the total; three levels of 2048-element blocks.  With
+// in == nullptr the values are (cnt[i], 0).
+void launch_scan_counts(const Buffers &B, const uint2 *in, const uint32_t *cnt, const uint32_t *n_ptr, uint2 *out,
+                        uint32_t max_n, cudaStream_t s, uint32_t *launches) {
     const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
     const uint32_t g2 = (g1 + kScanBlock - 1) / kScanBlock;
     const uint32_t grid1 = g1 ? g1 : 1u, grid2 = g2 ? g2 : 1u;
-    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.status);
+    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, B.status);
     scan_reduce2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
     scan_top_kernel<<<1, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum2, B.scan_total, B.status);
     scan_down2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
-    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.scan_total, out, B.status);
+    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, B.scan_total, out, B.status);
     *launches += 5;
+}
+
+void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
+                 cudaStream_t s, uint32_t *launches) {
+    launch_scan_counts(B, in, nullptr, n_ptr, out, max_n, s, launches);
 }
 
 void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
                   uint32_t *launches) {
-    counts_kernel<<<grid, threads, 0, s>>>(b);
-    launch_scan(b, b.scan_val, &b.status->n_mech, b.mech_off, max_mech, s, launches);
+    // offsets of the per-mechanism word ranges: scan of the word counts
+    launch_scan_counts(b, nullptr, b.mech_cnt, &b.status->n_mech, b.mech_off, max_mech, s, launches);
     scatter_kernel<<<grid, threads, 0, s>>>(b);
     group_kernel<<<grid, threads, 0, s>>>(b);
-    *launches += 3;
+    *launches += 2;
 }
 
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
