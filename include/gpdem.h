@@ -167,8 +167,11 @@ void gp_driver_destroy(gp_driver *drv);
  * circuits: host array of n_circuits descriptors; their ops/recs pointers are
  * device addresses if inputs_on_device, else host addresses.  noise: the
  * concatenation of every circuit's noise vector (sum of n_locations floats),
- * device or host likewise.  On GP_OK *out describes the result.  The call
- * returns after the work has finished on `stream` (it reads back a small
+ * device or host likewise.  Host arrays are read by the device itself when
+ * it addresses pageable host memory coherently (a Grace-Blackwell node) and
+ * every array is 4-byte aligned; otherwise they are copied through the
+ * driver's pinned staging buffers.  On GP_OK *out describes the result.  The
+ * call returns after the work has finished on `stream` (it reads back a small
  * status block).  Errors: GP_ERR_INVALID (malformed rows, noise outside a
  * channel's range), GP_ERR_NONDETERMINISTIC, GP_ERR_CAPACITY, GP_ERR_CUDA. */
 gp_status gp_compile_batch(gp_driver *drv, const gp_circuit *circuits,

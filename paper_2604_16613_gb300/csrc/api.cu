@@ -8,6 +8,7 @@
 // kernels on the caller's stream and reads back a small status block.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -172,6 +173,10 @@ struct gp_driver {
     uint4 *h_ops = nullptr;
     uint32_t *h_recs = nullptr;
     float *h_noise = nullptr;
+    // host inputs: gathered by the device straight from the caller's arrays
+    // when it can address pageable host memory coherently, else staged
+    bool coherent_host = false;
+    CopyJob *h_jobs = nullptr;      // pinned: 3 jobs per circuit
     // last result
     bool have_result = false;
     gp_dem_view view{};
@@ -378,8 +383,20 @@ gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace, uint64_t 
         cudaMallocHost(&d->h_circ_edges, sizeof(uint32_t) * bounds->max_circuits) != cudaSuccess ||
         cudaMallocHost(&d->h_ops, sizeof(uint4) * bounds->max_ops) != cudaSuccess ||
         cudaMallocHost(&d->h_recs, sizeof(uint32_t) * std::max<uint64_t>(bounds->max_recs, 1)) != cudaSuccess ||
-        cudaMallocHost(&d->h_noise, sizeof(float) * std::max<uint32_t>(bounds->max_locations, 1)) != cudaSuccess)
+        cudaMallocHost(&d->h_noise, sizeof(float) * std::max<uint32_t>(bounds->max_locations, 1)) != cudaSuccess ||
+        cudaMallocHost(&d->h_jobs, sizeof(CopyJob) * 3ull * bounds->max_circuits) != cudaSuccess)
         return cleanup(fail(GP_ERR_CUDA, "cudaMallocHost staging failed"));
+    {
+        int pageable = 0, host_tables = 0;
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, d->device) == cudaSuccess &&
+            cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, d->device) ==
+                cudaSuccess)
+            d->coherent_host = pageable == 1 && host_tables == 1;
+        // GPDEM_STAGE_HOST_INPUTS=1 keeps the staged copies (both paths are
+        // tested against each other)
+        const char *env = getenv("GPDEM_STAGE_HOST_INPUTS");
+        if (env && env[0] == '1') d->coherent_host = false;
+    }
     for (int i = 0; i < 5; i++)
         if (cudaEventCreate(&d->ev[i]) != cudaSuccess) return cleanup(fail(GP_ERR_CUDA, "cudaEventCreate failed"));
     if (cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -413,6 +430,7 @@ void gp_driver_destroy(gp_driver *d) {
     if (d->h_ops) cudaFreeHost(d->h_ops);
     if (d->h_recs) cudaFreeHost(d->h_recs);
     if (d->h_noise) cudaFreeHost(d->h_noise);
+    if (d->h_jobs) cudaFreeHost(d->h_jobs);
     for (int i = 0; i < 5; i++)
         if (d->ev[i]) cudaEventDestroy(d->ev[i]);
     if (d->exec) cudaGraphExecDestroy(d->exec);
@@ -456,6 +474,15 @@ gp_status gp_result_view(const gp_driver *d, gp_dem_view *out) {
     if (!d->have_result) return fail(GP_ERR_INVALID, "no successful compile on this driver");
     *out = d->view;
     return GP_OK;
+}
+
+// the device gathers host arrays with 4-byte (or 16-byte) loads, so every
+// source must be 4-byte aligned; other callers go through the staged copies
+static bool host_words_aligned(const gp_circuit *circuits, uint32_t n, const float *noise) {
+    uintptr_t bits = reinterpret_cast<uintptr_t>(noise);
+    for (uint32_t b = 0; b < n; b++)
+        bits |= reinterpret_cast<uintptr_t>(circuits[b].ops) | reinterpret_cast<uintptr_t>(circuits[b].recs);
+    return (bits & 3u) == 0u;
 }
 
 gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_circuits, const float *noise,
@@ -544,6 +571,28 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
                 return fail(GP_ERR_INVALID, "device ops must be 16-byte aligned");
         }
         P->noise = noise;
+    } else if (d->coherent_host && host_words_aligned(circuits, n_circuits, noise)) {
+        // the device reads the caller's arrays itself (no host copy)
+        if (loc_total && !noise) return fail(GP_ERR_INVALID, "null noise");
+        uint32_t nj = 0;
+        uint64_t max_bytes = 0, r0 = 0;
+        auto job = [&](const void *src, void *dst, uint64_t bytes) {
+            if (!bytes) return;
+            d->h_jobs[nj++] = CopyJob{src, dst, bytes};
+            max_bytes = std::max(max_bytes, bytes);
+        };
+        for (uint32_t b = 0; b < n_circuits; b++) {
+            const gp_circuit &c = circuits[b];
+            hc[b].ops = d->B.ops_arena + hc[b].op_base;
+            hc[b].recs = d->B.recs_arena + r0;
+            job(c.ops, d->B.ops_arena + hc[b].op_base, c.n_ops * sizeof(uint4));
+            job(c.recs, d->B.recs_arena + r0, c.n_recs * sizeof(uint32_t));
+            r0 += c.n_recs;
+        }
+        job(noise, d->B.noise_arena, loc_total * sizeof(float));
+        launch_gather_host(d->h_jobs, nj, max_bytes, (uint32_t)d->n_sms, s);
+        GP_CUDA(cudaGetLastError());
+        P->noise = d->B.noise_arena;
     } else {
         for (uint32_t b = 0; b < n_circuits; b++) {
             const gp_circuit &c = circuits[b];

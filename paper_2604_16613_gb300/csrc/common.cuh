@@ -405,6 +405,13 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 
 // kernel entry points (implemented in lower.cu, stage1.cu, stage2.cu)
 namespace gpdem {
+// one host -> device copy done by the device (all byte counts multiples of 4)
+struct CopyJob {
+    const void *src;
+    void *dst;
+    uint64_t bytes;
+};
+void launch_gather_host(const CopyJob *jobs, uint32_t n_jobs, uint64_t max_bytes, uint32_t n_sms, cudaStream_t s);
 void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, cudaStream_t s,
                      uint32_t *launches);
 cudaError_t lowering_setup(uint32_t max_qubits);

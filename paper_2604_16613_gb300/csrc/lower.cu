@@ -18,6 +18,8 @@
 //                qubit, and per qubit the lists of packed noise rows that
 //                touch it after and before the gates (CSR, a two-qubit row
 //                listed under both of its qubits)
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gpdem {
@@ -392,7 +394,41 @@ __global__ void __launch_bounds__(kPackThreads) layer_index_kernel(Buffers B) {
     }
 }
 
+// Host arrays gathered into device arenas by the GPU itself, through the
+// coherent host memory of a Grace-Blackwell node (pageable memory is
+// addressable from the device there): block (x, j) copies its share of job
+// j, 16 bytes per thread when both ends are 16-byte aligned, else 4.
+__global__ void __launch_bounds__(256) gather_host_kernel(const CopyJob *jobs, uint32_t n_jobs) {
+    const uint32_t j = blockIdx.y;
+    if (j >= n_jobs) return;
+    const CopyJob job = jobs[j];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool wide = ((reinterpret_cast<uintptr_t>(job.src) | reinterpret_cast<uintptr_t>(job.dst)) & 15u) == 0u;
+    uint64_t done = 0;
+    if (wide) {
+        const uint64_t n16 = job.bytes / 16u;
+        const uint4 *src = static_cast<const uint4 *>(job.src);
+        uint4 *dst = static_cast<uint4 *>(job.dst);
+        for (uint64_t i = tid; i < n16; i += stride) dst[i] = src[i];
+        done = n16 * 16u;
+    }
+    const uint64_t n4 = (job.bytes - done) / 4u;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(static_cast<const unsigned char *>(job.src) + done);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(job.dst) + done);
+    for (uint64_t i = tid; i < n4; i += stride) dst[i] = src[i];
+}
+
 }  // namespace
+
+void launch_gather_host(const CopyJob *jobs, uint32_t n_jobs, uint64_t max_bytes, uint32_t n_sms, cudaStream_t s) {
+    if (!n_jobs) return;
+    // enough blocks that the largest job is spread over the whole GPU
+    const uint64_t per_block = 256ull * 16u * 4u;
+    uint32_t gx = (uint32_t)std::min<uint64_t>((max_bytes + per_block - 1) / per_block, 4ull * n_sms);
+    if (gx == 0) gx = 1;
+    gather_host_kernel<<<dim3(gx, n_jobs), 256, 0, s>>>(jobs, n_jobs);
+}
 
 void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, cudaStream_t s,
                      uint32_t *launches) {

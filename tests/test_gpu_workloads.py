@@ -141,3 +141,23 @@ def test_block_wide_walk_equals_role_split_walk():
         got = wide.compile(dcs, noise).to_host()
         for k in split:
             assert np.array_equal(split[k], got[k]), (shape, k)
+
+
+def test_host_inputs_gathered_equal_staged(monkeypatch):
+    """Host arrays reach the device either gathered by the device itself
+    (coherent host memory) or through pinned staging copies; both give the
+    same compile bit for bit, for one circuit and for a batch."""
+    circs = [C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3)),
+             C.concatenated_adaptive_branch(4, 4, seed=3, noise=C.NoiseModel.uniform(1e-3))]
+    noises = [f32(c.default_noise) for c in circs]
+    gathered = Driver.for_circuits(circs)
+    monkeypatch.setenv("GPDEM_STAGE_HOST_INPUTS", "1")
+    staged = Driver.for_circuits(circs)
+    for c, nz in zip(circs, noises):
+        a, b = gathered.compile(c, nz).to_host(), staged.compile(c, nz).to_host()
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    a = gathered.compile(circs, np.concatenate(noises)).to_host()
+    b = staged.compile(circs, np.concatenate(noises)).to_host()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
