@@ -192,14 +192,19 @@ __device__ __forceinline__ uint32_t load_sorted(const Buffers &B, uint32_t m, ui
     return cnt;
 }
 
+// mask of mechanism rep equal to the sorted words col/w (exact): every word
+// of rep found at its column among them, counts equal
 __device__ __forceinline__ bool same_mask(const Buffers &B, uint32_t rep, uint32_t cnt, const uint32_t *col,
                                           const unsigned long long *w) {
-    if (B.mech_off[rep + 1].x - B.mech_off[rep].x != cnt) return false;
-    uint32_t c2[kMaxMaskWords];
-    unsigned long long w2[kMaxMaskWords];
-    load_sorted(B, rep, c2, w2);
-    for (uint32_t i = 0; i < cnt; i++)
-        if (c2[i] != col[i] || w2[i] != w[i]) return false;
+    const uint32_t r0 = B.mech_off[rep].x;
+    if (B.mech_off[rep + 1].x - r0 != cnt) return false;
+    for (uint32_t j = 0; j < cnt; j++) {
+        const uint32_t c = B.slot_col[r0 + j];
+        const unsigned long long x = B.slot_word[r0 + j];
+        uint32_t i = 0;
+        while (i < cnt && col[i] != c) i++;
+        if (i == cnt || w[i] != x) return false;
+    }
     return true;
 }
 
@@ -311,14 +316,21 @@ __global__ void compact_write_kernel(Buffers B) {
             const unsigned long long info = B.mech_info[m];
             b = (uint32_t)(info >> 48);
             const uint32_t col_base = B.circ[b].col_base;
-            uint32_t col[kMaxMaskWords];
-            unsigned long long w[kMaxMaskWords];
-            const uint32_t cnt = load_sorted(B, m, col, w);
+            const uint32_t o0 = B.mech_off[m].x, cnt = B.mech_off[m + 1].x - o0;
             unsigned long long obs = 0ull;
-            for (uint32_t j = 0; j < cnt; j++) {
-                if (col[j] & kObsColFlag) { obs ^= w[j]; continue; }
-                unsigned long long x = w[j];
-                const uint32_t base_id = (col[j] - col_base) * 64u;
+            // words in ascending column order (selection over the range), so
+            // the detector ids come out ascending
+            uint32_t prev = 0u;
+            for (uint32_t k = 0; k < cnt; k++) {
+                uint32_t cmin = 0xFFFFFFFFu, jmin = 0u;
+                for (uint32_t j = 0; j < cnt; j++) {
+                    const uint32_t c = B.slot_col[o0 + j];
+                    if ((k == 0u || c > prev) && c < cmin) { cmin = c; jmin = j; }
+                }
+                prev = cmin;
+                unsigned long long x = B.slot_word[o0 + jmin];
+                if (cmin & kObsColFlag) { obs ^= x; continue; }
+                const uint32_t base_id = (cmin - col_base) * 64u;
                 while (x) {
                     const int bit = __ffsll((long long)x) - 1;
                     B.det_idx[d++] = base_id + (uint32_t)bit;
