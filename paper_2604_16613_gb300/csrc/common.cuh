@@ -12,8 +12,8 @@ namespace gpdem {
 // ---------------------------------------------------------------------------
 // limits and constants
 // ---------------------------------------------------------------------------
-constexpr int kRowTile = 1024;          // circuit rows per lowering tile
-constexpr int kLowerThreads = 256;      // 4 rows per thread
+constexpr int kRowTile = 512;           // circuit rows per lowering tile
+constexpr int kLowerThreads = 256;      // 2 rows per thread
 constexpr int kMaxEntries = 1024;       // (measurement, word) pairs per column
 constexpr int kMaxMaskWords = 16;       // hard cap of mask words per mechanism
 constexpr int kMechPerBlockScan = 1024; // mechanisms per compaction block

@@ -3,7 +3,7 @@
 // backward wave runs).
 //
 // Four launches, no device-wide waits:
-//   tile_count   per tile of 1024 rows: counts of TICKs, measurements,
+//   tile_count   per tile of 512 rows: counts of TICKs, measurements,
 //                detectors and mechanisms (components at the chosen level)
 //   tile_scan    one block: per-circuit scan of the tile counts, circuit
 //                totals and batch offsets, capacity checks
