@@ -41,6 +41,23 @@ def make_workload(d: int = 25):
     return circ, noise
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's);
+    x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank compiles its own replica)."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -418,12 +435,8 @@ def run_ours(args):
         stage_us.append(drv.last_timing())
     barrier()
     clocks = sampler.stop()
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n_mech * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(step_ms)), dist, "cuda")
+    value = job_rate(n_mech * args.steps, world, total_ms / 1e3)
     per_cycle = np.array(step_ms) * 1e3 / 25
 
     # per-stage device times (CUDA events on the compile's stream)
@@ -475,12 +488,8 @@ def run_ours(args):
         pinned["logodds"].copy_(dm.logodds, non_blocking=True)
         torch.cuda.synchronize()
         walls.append(time.perf_counter() - t_a)
-    e2e_time = float(sum(walls))
-    if dist is not None:
-        t = torch.tensor([e2e_time], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_time = float(t.item())
-    e2e_value = world * n_mech * e2e_steps / e2e_time
+    e2e_time = max_over_ranks(float(sum(walls)), dist, "cuda")
+    e2e_value = job_rate(n_mech * e2e_steps, world, e2e_time)
 
     result = None
     if rank == 0:
