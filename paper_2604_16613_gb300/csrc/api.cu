@@ -134,8 +134,6 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     {
         const uint64_t nb = ((uint64_t)bd.max_mechanisms + 2047) / 2048;
         B.scan_bsum = c.take<uint2>(nb + 1);
-        B.scan_bsum2 = c.take<uint2>((nb + 2047) / 2048 + 1);
-        B.scan_total = c.take<uint2>(1);
     }
     B.det_off = c.take<uint32_t>((uint64_t)bd.max_mechanisms + 1);
     B.det_idx = c.take<uint32_t>(L.max_det_entries);

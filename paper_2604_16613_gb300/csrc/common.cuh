@@ -126,7 +126,7 @@ struct Buffers {
     TabSlot *table;             // grouping hash table
     uint2 *scan_val;            // per mechanism: scan input
     uint2 *comp_off;            // per mechanism: (edge, detector id) offsets, n + 1
-    uint2 *scan_bsum, *scan_bsum2, *scan_total;   // scan levels
+    uint2 *scan_bsum;           // scans: per-block sums
     uint32_t *det_off;          // n_edges + 1
     uint32_t *det_idx;
     unsigned long long *obs_mask;

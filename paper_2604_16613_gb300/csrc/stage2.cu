@@ -20,9 +20,9 @@
 //              cleared for the next compile
 //   backward   dP/dp_i = (1 - 2P) / 2 * dt_i/dp and dw/dP = -1 / (P (1 - P)),
 //              summed per noise location in fixed point
-// The scans are three-level reduce-then-scan passes (2048 elements per
-// block) with every grid fixed by the driver's bounds, so the whole sequence
-// can be captured once and replayed.
+// The scans are two-pass reduce-then-scan passes (2048 elements per block)
+// with every grid fixed by the driver's bounds, so the whole sequence can be
+// captured once and replayed.
 #include "common.cuh"
 
 namespace gpdem {
@@ -69,81 +69,29 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint2 *
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// level 2: sums of chunks of 2048 block sums
-__global__ void __launch_bounds__(kScanThreads) scan_reduce2_kernel(const uint32_t *n_ptr, const uint2 *bsum,
-                                                                    uint2 *bsum2, const Status *st) {
-    if (st->code != 0u) return;
-    const uint32_t nb = (*n_ptr + kScanBlock - 1) / kScanBlock;
-    const uint32_t c0 = blockIdx.x * kScanBlock;
-    if (c0 >= nb) return;
-    uint2 acc = make_uint2(0, 0);
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = c0 + threadIdx.x * kScanPer + k;
-        if (i < nb) acc = add2(acc, bsum[i]);
-    }
-    __shared__ uint32_t tmp[kScanThreads / 32];
-    uint2 tot;
-    block_scan2(acc, tmp, tot);
-    if (threadIdx.x == 0) bsum2[blockIdx.x] = tot;
-}
-
-// level 3: one block scans the chunk sums (at most 2048 of them) in place
-// and stores the grand total
-__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(const uint32_t *n_ptr, uint2 *bsum2,
-                                                                uint2 *total_out, const Status *st) {
-    if (st->code != 0u) return;
-    const uint32_t nb2 = ((*n_ptr + kScanBlock - 1) / kScanBlock + kScanBlock - 1) / kScanBlock;
-    uint2 v[kScanPer];
-    uint2 acc = make_uint2(0, 0);
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = threadIdx.x * kScanPer + k;
-        v[k] = i < nb2 ? bsum2[i] : make_uint2(0, 0);
-        acc = add2(acc, v[k]);
-    }
-    __shared__ uint32_t tmp[kScanThreads / 32];
-    uint2 tot;
-    uint2 run = block_scan2(acc, tmp, tot);
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = threadIdx.x * kScanPer + k;
-        if (i < nb2) bsum2[i] = run;
-        run = add2(run, v[k]);
-    }
-    if (threadIdx.x == 0) *total_out = tot;
-}
-
-// level 2 down: exclusive offsets of the block sums
-__global__ void __launch_bounds__(kScanThreads) scan_down2_kernel(const uint32_t *n_ptr, uint2 *bsum,
-                                                                  const uint2 *bsum2, const Status *st) {
-    if (st->code != 0u) return;
-    const uint32_t nb = (*n_ptr + kScanBlock - 1) / kScanBlock;
-    const uint32_t c0 = blockIdx.x * kScanBlock;
-    if (c0 >= nb) return;
-    uint2 v[kScanPer];
-    uint2 acc = make_uint2(0, 0);
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = c0 + threadIdx.x * kScanPer + k;
-        v[k] = i < nb ? bsum[i] : make_uint2(0, 0);
-        acc = add2(acc, v[k]);
-    }
-    __shared__ uint32_t tmp[kScanThreads / 32];
-    uint2 tot;
-    uint2 run = add2(block_scan2(acc, tmp, tot), bsum2[blockIdx.x]);
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = c0 + threadIdx.x * kScanPer + k;
-        if (i < nb) bsum[i] = run;
-        run = add2(run, v[k]);
-    }
-}
-
-// level 1 down: exclusive prefix of every value; out[n] = total
+// level 2: exclusive prefix of every value.  Each block adds up the sums of
+// the blocks before it itself (a few hundred values), so no separate pass
+// scans the block sums; block 0 also writes out[n] = the total.
 __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in, const uint32_t *cnt,
                                                                  const uint32_t *n_ptr, const uint2 *bsum,
-                                                                 const uint2 *total, uint2 *out, const Status *st) {
+                                                                 uint2 *out, const Status *st) {
     if (st->code != 0u) return;
     const uint32_t n = *n_ptr;
     const uint32_t b0 = blockIdx.x * kScanBlock;
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
+    const uint32_t nb = (n + kScanBlock - 1) / kScanBlock;
+    __shared__ uint32_t tmp[kScanThreads / 32];
+    if (blockIdx.x == 0) {
+        uint2 all = make_uint2(0, 0);
+        for (uint32_t i = threadIdx.x; i < nb; i += kScanThreads) all = add2(all, bsum[i]);
+        uint2 tot;
+        block_scan2(all, tmp, tot);
+        if (threadIdx.x == 0) out[n] = tot;
+    }
     if (b0 >= n) return;
+    uint2 before = make_uint2(0, 0);
+    for (uint32_t i = threadIdx.x; i < blockIdx.x; i += kScanThreads) before = add2(before, bsum[i]);
+    uint2 prefix;
+    block_scan2(before, tmp, prefix);
     uint2 v[kScanPer];
     uint2 acc = make_uint2(0, 0);
     for (int k = 0; k < kScanPer; k++) {
@@ -151,9 +99,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in
         v[k] = i < n ? scan_in(in, cnt, i) : make_uint2(0, 0);
         acc = add2(acc, v[k]);
     }
-    __shared__ uint32_t tmp[kScanThreads / 32];
     uint2 tot;
-    uint2 run = add2(block_scan2(acc, tmp, tot), bsum[blockIdx.x]);
+    uint2 run = add2(block_scan2(acc, tmp, tot), prefix);
     for (int k = 0; k < kScanPer; k++) {
         const uint32_t i = b0 + threadIdx.x * kScanPer + k;
         if (i < n) out[i] = run;
@@ -354,26 +301,26 @@ __global__ void compact_write_kernel(Buffers B) {
     }
 }
 
-__global__ void finalize_mech_kernel(Buffers B) {
+// per-mechanism class ids and counters reset (i < N), used table slots
+// cleared (i < E): disjoint fields, one pass
+__global__ void finalize_kernel(Buffers B) {
     if (B.status->code != 0u) return;
-    const uint32_t N = B.status->n_mech;
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
-        const uint32_t slot = B.slot_of[m];
-        B.mech_class[m] = (slot == kNone) ? -1 : (int32_t)B.table[slot].cls;
-        B.mech_cnt[m] = 0u;
-        B.mech_fill[m] = 0u;
-    }
-}
-
-__global__ void finalize_table_kernel(Buffers B) {
-    if (B.status->code != 0u) return;
-    const uint32_t E = B.status->n_edges;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        TabSlot &ts = B.table[B.class_slot[e]];
-        ts.entry = kEmpty;
-        ts.min = kNone;
-        ts.acc_lo = 0ull;
-        ts.acc_hi = 0ull;
+    const uint32_t N = B.status->n_mech, E = B.status->n_edges;
+    const uint32_t M = max(N, E);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+        if (i < N) {
+            const uint32_t slot = B.slot_of[i];
+            B.mech_class[i] = (slot == kNone) ? -1 : (int32_t)B.table[slot].cls;
+            B.mech_cnt[i] = 0u;
+            B.mech_fill[i] = 0u;
+        }
+        if (i < E) {
+            TabSlot &ts = B.table[B.class_slot[i]];
+            ts.entry = kEmpty;
+            ts.min = kNone;
+            ts.acc_lo = 0ull;
+            ts.acc_hi = 0ull;
+        }
     }
 }
 
@@ -422,19 +369,15 @@ __global__ void init_table_kernel(TabSlot *t, size_t n) {
 }  // namespace
 
 // exclusive scan of n (read on the device) uint2 values: out[i] = sum of
-// in[0..i), out[n] = the total; three levels of 2048-element blocks.  With
+// in[0..i), out[n] = the total; blocks of 2048 values, two passes.  With
 // in == nullptr the values are (cnt[i], 0).
 void launch_scan_counts(const Buffers &B, const uint2 *in, const uint32_t *cnt, const uint32_t *n_ptr, uint2 *out,
                         uint32_t max_n, cudaStream_t s, uint32_t *launches) {
     const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
-    const uint32_t g2 = (g1 + kScanBlock - 1) / kScanBlock;
-    const uint32_t grid1 = g1 ? g1 : 1u, grid2 = g2 ? g2 : 1u;
+    const uint32_t grid1 = g1 ? g1 : 1u;
     scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, B.status);
-    scan_reduce2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
-    scan_top_kernel<<<1, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum2, B.scan_total, B.status);
-    scan_down2_kernel<<<grid2, kScanThreads, 0, s>>>(n_ptr, B.scan_bsum, B.scan_bsum2, B.status);
-    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, B.scan_total, out, B.status);
-    *launches += 5;
+    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, out, B.status);
+    *launches += 2;
 }
 
 void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
@@ -456,9 +399,8 @@ void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t 
     leaders_kernel<<<grid, threads, 0, s>>>(b);
     launch_scan(b, b.scan_val, &b.status->n_mech, b.comp_off, max_mech, s, launches);
     compact_write_kernel<<<grid, threads, 0, s>>>(b);
-    finalize_mech_kernel<<<grid, threads, 0, s>>>(b);
-    finalize_table_kernel<<<grid, threads, 0, s>>>(b);
-    *launches += 4;
+    finalize_kernel<<<grid, threads, 0, s>>>(b);
+    *launches += 3;
 }
 
 void launch_backward(const Buffers &b, const float *g_prob, const float *g_logodds, float *g_noise,
