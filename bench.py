@@ -144,8 +144,9 @@ def measured_traffic(kernel: str) -> float | None:
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
         fields = {}
         for line in open(path):
-            if ":" in line and line.strip().startswith(("dram_bytes_per_launch", "source_hash")):
-                k, v = line.strip().strip("`- ").split(":", 1)
+            item = line.strip().lstrip("-* ").strip("`")
+            if ":" in item and item.startswith(("dram_bytes_per_launch", "source_hash")):
+                k, v = item.split(":", 1)
                 fields[k.strip().strip("`")] = v.strip().strip("`")
         if fields.get("source_hash") == kernel_source_hash() and "dram_bytes_per_launch" in fields:
             return float(fields["dram_bytes_per_launch"])

@@ -104,3 +104,21 @@ def test_missing_library_fails_loudly(tmp_path):
             native.load(str(tmp_path / "absent.so"))
         finally:
             native._lib = native._lib_backup
+
+
+
+def test_bench_reads_profile_traffic(tmp_path, monkeypatch):
+    """bench.py takes roofline.traffic from a committed profile summary only
+    when the summary's source hash matches the current kernel sources."""
+    import bench
+    current = bench.kernel_source_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "demo_kernel_case.md").write_text(
+        f"# x\n\n- dram_bytes_per_launch: 1234\n- source_hash: {current}\n")
+    (prof / "stale_kernel_case.md").write_text("- dram_bytes_per_launch: 99\n- source_hash: 0000000000000000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: current)
+    assert bench.measured_traffic("demo_kernel") == 1234.0
+    assert bench.measured_traffic("stale_kernel") is None
+    assert bench.measured_traffic("absent_kernel") is None
