@@ -464,12 +464,12 @@ def run_ours(args):
     traffic = measured_traffic(kernel_name)
 
     # end to end through the C ABI with host buffers: H2D of the circuit and
-    # noise, compile, D2H of the hyperedges into pinned host memory
+    # noise, compile, the hyperedges into pinned host memory (gp_result_to_host)
     e2e_steps = max(10, min(args.steps, 200))
     pinned = {
         "det_offsets": torch.empty(n_edges + 1, dtype=torch.int32, pin_memory=True),
         "det_idx": torch.empty(int(host["det_idx"].size), dtype=torch.int32, pin_memory=True),
-        "obs": torch.empty(n_edges, dtype=torch.int64, pin_memory=True),
+        "obs_mask": torch.empty(n_edges, dtype=torch.int64, pin_memory=True),
         "prob": torch.empty(n_edges, dtype=torch.float32, pin_memory=True),
         "logodds": torch.empty(n_edges, dtype=torch.float32, pin_memory=True),
     }
@@ -482,11 +482,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t_a = time.perf_counter()
         dm = drv.compile(circ, noise)
-        pinned["det_offsets"].copy_(dm.det_offsets, non_blocking=True)
-        pinned["det_idx"].copy_(dm.det_idx, non_blocking=True)
-        pinned["obs"].copy_(dm.obs_mask, non_blocking=True)
-        pinned["prob"].copy_(dm.prob, non_blocking=True)
-        pinned["logodds"].copy_(dm.logodds, non_blocking=True)
+        dm.copy_to_host(pinned)
         torch.cuda.synchronize()
         walls.append(time.perf_counter() - t_a)
     e2e_time = max_over_ranks(float(sum(walls)), dist, "cuda")

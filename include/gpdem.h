@@ -198,6 +198,16 @@ gp_status gp_backward(gp_driver *drv, const float *g_prob,
 /* View of the last successful compile. */
 gp_status gp_result_view(const gp_driver *drv, gp_dem_view *out);
 
+/* Host copy of the last successful compile's hyperedges into caller-owned
+ * host arrays (any may be NULL to skip it): det_offsets[n_edges + 1],
+ * det_idx[n_det_entries], obs_mask[n_edges], prob[n_edges],
+ * logodds[n_edges].  On a device that addresses host memory coherently, and
+ * with every array 4-byte aligned, one device pass writes them all; else
+ * one asynchronous copy per array.  Returns after the copies have finished
+ * on `stream`.  Errors: GP_ERR_INVALID (no result), GP_ERR_CUDA. */
+gp_status gp_result_to_host(gp_driver *drv, uint32_t *det_offsets, uint32_t *det_idx,
+                            uint64_t *obs_mask, float *prob, float *logodds, void *stream);
+
 /* Tunable launch parameters (picked by the package's autotuner). */
 typedef struct {
     uint32_t stage1_threads;      /* 128, 256, 512 or 1024                    */

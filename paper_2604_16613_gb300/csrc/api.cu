@@ -174,7 +174,7 @@ struct gp_driver {
     // host inputs: gathered by the device straight from the caller's arrays
     // when it can address pageable host memory coherently, else staged
     bool coherent_host = false;
-    CopyJob *h_jobs = nullptr;      // pinned: 3 jobs per circuit
+    CopyJob *h_jobs = nullptr;      // pinned: 3 jobs per circuit (at least 8)
     // last result
     bool have_result = false;
     gp_dem_view view{};
@@ -382,7 +382,7 @@ gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace, uint64_t 
         cudaMallocHost(&d->h_ops, sizeof(uint4) * bounds->max_ops) != cudaSuccess ||
         cudaMallocHost(&d->h_recs, sizeof(uint32_t) * std::max<uint64_t>(bounds->max_recs, 1)) != cudaSuccess ||
         cudaMallocHost(&d->h_noise, sizeof(float) * std::max<uint32_t>(bounds->max_locations, 1)) != cudaSuccess ||
-        cudaMallocHost(&d->h_jobs, sizeof(CopyJob) * 3ull * bounds->max_circuits) != cudaSuccess)
+        cudaMallocHost(&d->h_jobs, sizeof(CopyJob) * std::max<uint64_t>(3ull * bounds->max_circuits, 8)) != cudaSuccess)
         return cleanup(fail(GP_ERR_CUDA, "cudaMallocHost staging failed"));
     {
         int pageable = 0, host_tables = 0;
@@ -471,6 +471,41 @@ gp_status gp_result_view(const gp_driver *d, gp_dem_view *out) {
     if (!d || !out) return fail(GP_ERR_INVALID, "null argument");
     if (!d->have_result) return fail(GP_ERR_INVALID, "no successful compile on this driver");
     *out = d->view;
+    return GP_OK;
+}
+
+gp_status gp_result_to_host(gp_driver *d, uint32_t *det_offsets, uint32_t *det_idx, uint64_t *obs_mask, float *prob,
+                            float *logodds, void *stream) {
+    if (!d) return fail(GP_ERR_INVALID, "null argument");
+    if (!d->have_result) return fail(GP_ERR_INVALID, "no successful compile on this driver");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const gp_dem_view &v = d->view;
+    struct Part { void *dst; const void *src; uint64_t bytes; };
+    const Part parts[5] = {
+        {det_offsets, v.det_offsets, 4ull * (v.n_edges + 1ull)},
+        {det_idx, v.det_idx, 4ull * v.n_det_entries},
+        {obs_mask, v.obs_mask, 8ull * v.n_edges},
+        {prob, v.prob, 4ull * v.n_edges},
+        {logodds, v.logodds, 4ull * v.n_edges},
+    };
+    uintptr_t bits = 0;
+    for (const Part &p : parts) bits |= reinterpret_cast<uintptr_t>(p.dst);
+    if (d->coherent_host && (bits & 3u) == 0u) {
+        // one device pass writes every array into host memory
+        uint32_t nj = 0;
+        uint64_t max_bytes = 0;
+        for (const Part &p : parts) {
+            if (!p.dst || !p.bytes) continue;
+            d->h_jobs[nj++] = CopyJob{p.src, p.dst, p.bytes};
+            max_bytes = std::max(max_bytes, p.bytes);
+        }
+        launch_gather_host(d->h_jobs, nj, max_bytes, (uint32_t)d->n_sms, s);
+        GP_CUDA(cudaGetLastError());
+    } else {
+        for (const Part &p : parts)
+            if (p.dst && p.bytes) GP_CUDA(cudaMemcpyAsync(p.dst, p.src, p.bytes, cudaMemcpyDeviceToHost, s));
+    }
+    GP_CUDA(cudaStreamSynchronize(s));
     return GP_OK;
 }
 

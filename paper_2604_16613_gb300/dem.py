@@ -148,6 +148,33 @@ class Dem:
                     prob=self.prob.cpu().numpy(), logodds=self.logodds.cpu().numpy(),
                     edge_offsets=self.edge_offsets.copy())
 
+    def copy_to_host(self, out: dict, stream=None) -> dict:
+        """Copy the hyperedges into caller-owned host arrays (numpy arrays or
+        CPU tensors, pinned or not): any of det_offsets (int32/uint32,
+        n_edges + 1), det_idx (int32/uint32, n_det_entries), obs_mask
+        (int64/uint64, n_edges), prob and logodds (float32, n_edges).
+        Returns ``out``."""
+        self._check()
+        want = {"det_offsets": (self.n_edges + 1, 4), "det_idx": (self.n_det_entries, 4),
+                "obs_mask": (self.n_edges, 8), "prob": (self.n_edges, 4), "logodds": (self.n_edges, 4)}
+        ptrs = []
+        for name, (n, size) in want.items():
+            a = out.get(name)
+            if a is None:
+                ptrs.append(None)
+                continue
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or not a.is_contiguous() or a.element_size() != size or a.numel() < n:
+                    raise ValueError(f"{name}: a contiguous CPU tensor of >= {n} {size}-byte elements")
+                ptrs.append(a.data_ptr())
+            else:
+                if not a.flags["C_CONTIGUOUS"] or a.itemsize != size or a.size < n:
+                    raise ValueError(f"{name}: a contiguous array of >= {n} {size}-byte elements")
+                ptrs.append(a.ctypes.data)
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        native.check(self.driver.lib.gp_result_to_host(self.driver.handle, *[ctypes.c_void_p(p) for p in ptrs], s))
+        return out
+
     def edges(self, circuit: int = 0, host: dict | None = None) -> dict:
         """{(detector tuple, observable mask): (P, w)} for one circuit."""
         h = host or self.to_host()

@@ -21,7 +21,7 @@ LEVELS = {"L0": 0, "L1": 1, "L2": 2, 0: 0, 1: 1, 2: 2}
 # every symbol include/gpdem.h declares
 EXPORTED = [
     "gp_workspace_size", "gp_driver_create", "gp_driver_destroy", "gp_compile_batch", "gp_compile",
-    "gp_backward", "gp_result_view", "gp_set_tuning", "gp_get_tuning", "gp_enable_timing",
+    "gp_backward", "gp_result_view", "gp_result_to_host", "gp_set_tuning", "gp_get_tuning", "gp_enable_timing",
     "gp_last_timing", "gp_last_launch_count", "gp_last_error", "gp_pmerge_noalloc",
     "gp_server_create", "gp_server_destroy", "gp_server_open_patch", "gp_server_close_patch",
     "gp_server_submit", "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release",
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
         lib.gp_compile.argtypes = [vp, ctypes.POINTER(GpCircuit), vp, i32, i32, vp, ctypes.POINTER(GpDemView)]
         lib.gp_backward.argtypes = [vp, vp, vp, vp, vp]
         lib.gp_result_view.argtypes = [vp, ctypes.POINTER(GpDemView)]
+        lib.gp_result_to_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.gp_set_tuning.argtypes = [vp, ctypes.POINTER(GpTuning)]
         lib.gp_get_tuning.argtypes = [vp, ctypes.POINTER(GpTuning)]
         lib.gp_enable_timing.argtypes = [vp, i32]
@@ -145,8 +146,8 @@ def load(path: str = LIB_PATH):
         lib.gp_last_error.argtypes = []
         lib.gp_last_error.restype = ctypes.c_char_p
         for name in ("gp_workspace_size", "gp_driver_create", "gp_compile_batch", "gp_compile",
-                     "gp_backward", "gp_result_view", "gp_set_tuning", "gp_get_tuning",
-                     "gp_enable_timing", "gp_last_timing"):
+                     "gp_backward", "gp_result_view", "gp_result_to_host", "gp_set_tuning",
+                     "gp_get_tuning", "gp_enable_timing", "gp_last_timing"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib

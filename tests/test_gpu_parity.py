@@ -243,3 +243,27 @@ def test_gradient_matches_oracle(d):
     err = np.abs(g_gpu - g_ref)
     bad = err > 1e-4 * np.abs(g_ref) + floor
     assert not bad.any(), f"{bad.sum()} locations off; worst {err.max():.3g}"
+
+
+@pytest.mark.parametrize("staged", [False, True])
+def test_result_to_host_matches_to_host(staged, monkeypatch):
+    """gp_result_to_host (one device pass into host memory, or per-array
+    copies) delivers the same arrays as reading the device tensors."""
+    if staged:
+        monkeypatch.setenv("GPDEM_STAGE_HOST_INPUTS", "1")
+    circ = C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))
+    drv = Driver.for_circuits([circ])
+    dem = drv.compile(circ, f32(circ.default_noise))
+    ref = dem.to_host()
+    out = {"det_offsets": np.zeros(dem.n_edges + 1, np.int32), "det_idx": np.zeros(dem.n_det_entries, np.int32),
+           "obs_mask": np.zeros(dem.n_edges, np.uint64), "prob": np.zeros(dem.n_edges, np.float32),
+           "logodds": torch.zeros(dem.n_edges, dtype=torch.float32, pin_memory=True)}
+    dem.copy_to_host(out)
+    assert np.array_equal(out["det_offsets"], ref["det_offsets"])
+    assert np.array_equal(out["det_idx"], ref["det_idx"])
+    assert np.array_equal(out["obs_mask"], ref["obs_mask"])
+    assert np.array_equal(out["prob"], ref["prob"])
+    assert np.array_equal(out["logodds"].numpy(), ref["logodds"])
+    part = {"prob": np.zeros(dem.n_edges, np.float32)}
+    dem.copy_to_host(part)
+    assert np.array_equal(part["prob"], ref["prob"])
