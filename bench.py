@@ -247,6 +247,45 @@ def batch_section(args, world: int) -> dict:
     }
 
 
+def levels_section(args) -> list:
+    """The correlation level as a benchmark axis: the d = 25 workload compiled
+    at L0, L1 and L2, with every detector and with the Z-check detectors only
+    (the detector set paired with L0 in a Z-basis experiment).  Device time
+    per compile (CUDA events, L2 flushed, median of ``--levels-steps``)."""
+    import torch
+    from paper_2604_16613_gb300 import circuits as C
+    from paper_2604_16613_gb300.dem import DeviceCircuit, Driver
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for zonly in (False, True):
+        circ = C.rotated_surface_code_memory(25, 25, C.NoiseModel.uniform(1e-3), z_detectors_only=zonly)
+        noise = torch.tensor(C.log_uniform_noise(circ.n_locations, seed=2).astype(np.float32), device="cuda")
+        drv = Driver.for_circuits([circ])
+        dc = DeviceCircuit(circ)
+        for level in ("L0", "L1", "L2"):
+            for _ in range(3):
+                dem = drv.compile(dc, noise, level)
+            n_mech = int((dem.mech_class >= 0).sum().item())
+            ms = []
+            for _ in range(args.levels_steps):
+                flush.fill_(1)
+                e0.record(stream)
+                drv.compile(dc, noise, level)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = float(np.median(ms))
+            rows.append({"level": level, "detectors": "Z checks only" if zonly else "all",
+                         "n_detectors": circ.n_detectors, "mechanisms": n_mech, "hyperedges": dem.n_edges,
+                         "ms_per_compile_p50": t, "mechanisms_per_s": n_mech / (t * 1e-3)})
+        del drv
+    del flush
+    torch.cuda.empty_cache()
+    return rows
+
+
 def serve_section(args) -> dict:
     """Continuous serving: ``--serve-patches`` patches, each issuing one
     per-cycle request as a Poisson process, for ``--serve-seconds`` at each
@@ -513,6 +552,8 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(circ, noise)
+        if args.levels_steps > 0:
+            result["levels"] = levels_section(args)
         if args.batch_branches > 0:
             del drv
             torch.cuda.empty_cache()
@@ -536,6 +577,8 @@ def main():
     ap.add_argument("--batch-branches", type=int, default=256,
                     help="adaptive branches for the batched-vs-plain section (0 skips it)")
     ap.add_argument("--batch-reps", type=int, default=10)
+    ap.add_argument("--levels-steps", type=int, default=50,
+                    help="timed compiles per correlation level in the levels section (0 skips it)")
     ap.add_argument("--serve-patches", type=int, default=64,
                     help="patches of the continuous-serving section (0 skips it)")
     ap.add_argument("--serve-rates", default="250,500,750,1000",

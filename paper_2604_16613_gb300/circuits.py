@@ -601,7 +601,7 @@ def rotated_surface_layout(d: int) -> SurfaceLayout:
 
 
 def rotated_surface_code_memory(d: int, rounds: int | None = None,
-                                noise: NoiseModel | None = None) -> Circuit:
+                                noise: NoiseModel | None = None, z_detectors_only: bool = False) -> Circuit:
     """Z-basis memory experiment on the rotated surface code (Sec. 4).
 
     Per round, TICK layers: reset ancillas (data too in round 1), H on X
@@ -611,7 +611,10 @@ def rotated_surface_code_memory(d: int, rounds: int | None = None,
     DEPOLARIZE2 after CX.  Round 1 has Z-check detectors only; later rounds
     compare each check with its previous outcome; the final data measurement
     closes every Z check and defines observable 0 = Z_L.
-    Detector count: d (d^2 - 1).
+    Detector count: d (d^2 - 1).  With ``z_detectors_only`` the X checks are
+    still measured but declare no detectors, (d^2 - 1)/2 (rounds + 1) in all:
+    the detector set the configurable-correlation-level section pairs with
+    level L0 in a Z-basis experiment.
     """
     rounds = d if rounds is None else rounds
     lay = rotated_surface_layout(d)
@@ -647,6 +650,8 @@ def rotated_surface_code_memory(d: int, rounds: int | None = None,
         L.close(tick=False)
         if prev is None:
             c.detectors([[rec[n_x + i]] for i in range(len(lay.z_checks))])
+        elif z_detectors_only:
+            c.detectors([[rec[n_x + i], prev[n_x + i]] for i in range(len(lay.z_checks))])
         else:
             c.detectors([[m, pm] for m, pm in zip(rec, prev)])
         prev = rec

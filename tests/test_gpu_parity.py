@@ -267,3 +267,24 @@ def test_result_to_host_matches_to_host(staged, monkeypatch):
     part = {"prob": np.zeros(dem.n_edges, np.float32)}
     dem.copy_to_host(part)
     assert np.array_equal(part["prob"], ref["prob"])
+
+
+@pytest.mark.parametrize("level", ["L0", "L1", "L2"])
+def test_z_check_detectors_only_parity(level):
+    """The Z-basis memory experiment with its X-check detectors left out (the
+    detector set paired with L0) against the oracle, at every level."""
+    circ = C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3), z_detectors_only=True)
+    nz = f32(C.log_uniform_noise(circ.n_locations, seed=11))
+    got = Driver.for_circuits([circ]).compile(circ, nz, level).edges()
+    compare_edges(got, oracle_edges(circ, nz, level).edges(), f"z-only {level}")
+
+
+def test_dem_text_round_trip_gpu():
+    """A compiled model written as text and read back is the same model (the
+    FP32 probabilities survive exactly)."""
+    from paper_2604_16613_gb300.demtext import read_dem, write_dem
+    circ = C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))
+    got = Driver.for_circuits([circ]).compile(circ, f32(circ.default_noise)).edges()
+    back, n_det, n_obs = read_dem(write_dem(got, circ.n_detectors, circ.n_observables))
+    assert (n_det, n_obs) == (circ.n_detectors, circ.n_observables)
+    assert back == {k: p for k, (p, _) in got.items()}

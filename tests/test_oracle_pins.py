@@ -495,3 +495,44 @@ def test_surface_circuit_distance(d):
     circ = C.rotated_surface_code_memory(d, d, C.NoiseModel.uniform(1e-3))
     dem = oracle.analyze_circuit(circ, level=0)
     assert _graphlike_distance(dem) == d
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_z_only_detectors_equal_restricted_full_model(d):
+    """Dropping the X-check detectors of a Z-basis memory experiment (the
+    configurable-correlation-level section pairs level L0 with such a
+    detector set) must give the full model restricted to the Z-check
+    detectors: each class's mask loses
+    its X detectors, classes whose restricted masks coincide merge with
+    P = 1/2 (1 - prod (1 - 2 P_c)) (Eq. pmerge), and classes left with an
+    empty mask disappear.  Built here from the full model, independently of
+    the oracle's own grouping."""
+    noise = C.NoiseModel.uniform(1e-3)
+    full = C.rotated_surface_code_memory(d, d, noise)
+    zonly = C.rotated_surface_code_memory(d, d, noise, z_detectors_only=True)
+    n_z = (d * d - 1) // 2
+    n_x = n_z
+    assert zonly.n_detectors == n_z * (d + 1)
+    assert full.n_detectors == d * (d * d - 1)
+    # detector numbering: round 1 has Z checks only; later rounds list the X
+    # checks, then the Z checks; the final data measurement closes Z checks
+    remap, k, z = {}, 0, 0
+    blocks = [(0, n_z)] + [(n_x, n_z)] * (d - 1) + [(0, n_z)]
+    for nx, nz in blocks:
+        k += nx
+        for _ in range(nz):
+            remap[k] = z
+            k += 1
+            z += 1
+    assert k == full.n_detectors and z == zonly.n_detectors
+    expected: dict = {}
+    for (dets, obs), (p, _) in oracle.analyze_circuit(full).edges().items():
+        key = (tuple(remap[x] for x in dets if x in remap), obs)
+        if not key[0] and not key[1]:
+            continue
+        expected[key] = expected.get(key, 1.0) * (1.0 - 2.0 * p)
+    expected = {k: 0.5 * (1.0 - v) for k, v in expected.items()}
+    got = {k: p for k, (p, _) in oracle.analyze_circuit(zonly).edges().items()}
+    assert set(got) == set(expected)
+    for k, p in expected.items():
+        assert got[k] == pytest.approx(p, rel=1e-12), k
