@@ -286,6 +286,37 @@ def levels_section(args) -> list:
     return rows
 
 
+def calibration_section(args) -> dict:
+    """Noise recalibration with the adjoint (forward compile, adjoint kernel,
+    closed-form detector statistics): rotated surface code d=5, 5 rounds,
+    detection events from the Pauli-frame sampler with known per-channel
+    parameters, fitted from a uniform start; wall time of the whole fit
+    (setup of the pair statistics and every loss evaluation: one compile and
+    one adjoint each)."""
+    import torch
+    from paper_2604_16613_gb300 import circuits as C
+    from paper_2604_16613_gb300.calibrate import fit_groups, location_kinds
+    from paper_2604_16613_gb300.dem import Driver
+    from paper_2604_16613_gb300.sampler import sample
+    circ = C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))
+    kinds = location_kinds(circ)
+    groups = np.select([kinds == C.DEPOLARIZE2, kinds == C.DEPOLARIZE1], [0, 1], 2)
+    true = np.array([3e-3, 1e-3, 2e-3])
+    shots = 1 << 17
+    det, _ = sample(circ, true[groups], shots, seed=3)
+    drv = Driver.for_circuits([circ])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fitted, history = fit_groups(drv, circ, groups, det, p0=[1e-3] * 3, steps=args.calib_steps)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"workload": f"rotated surface code d=5, 5 rounds, {shots} sampled shots, 3 channel groups",
+            "evaluations": len(history), "fit_wall_s": el,
+            "true": true.tolist(), "fitted": [float(x) for x in fitted],
+            "max_rel_error": float(np.max(np.abs(fitted / true - 1.0))),
+            "loss_first_best": [history[0], min(history)]}
+
+
 def serve_section(args) -> dict:
     """Continuous serving: ``--serve-patches`` patches, each issuing one
     per-cycle request as a Poisson process, for ``--serve-seconds`` at each
@@ -554,6 +585,8 @@ def run_ours(args):
             result["cpu_baseline"] = cpu_baseline(circ, noise)
         if args.levels_steps > 0:
             result["levels"] = levels_section(args)
+        if args.calib_steps > 0:
+            result["calibration"] = calibration_section(args)
         if args.batch_branches > 0:
             del drv
             torch.cuda.empty_cache()
@@ -577,6 +610,8 @@ def main():
     ap.add_argument("--batch-branches", type=int, default=256,
                     help="adaptive branches for the batched-vs-plain section (0 skips it)")
     ap.add_argument("--batch-reps", type=int, default=10)
+    ap.add_argument("--calib-steps", type=int, default=100,
+                    help="loss evaluations of the noise-recalibration fit (0 skips it)")
     ap.add_argument("--levels-steps", type=int, default=50,
                     help="timed compiles per correlation level in the levels section (0 skips it)")
     ap.add_argument("--serve-patches", type=int, default=64,
