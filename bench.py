@@ -179,6 +179,35 @@ def cpu_baseline(circ, noise, budget_s: float = 12.0, max_runs: int = 40) -> dic
                       f"{platform.machine()} host)"}
 
 
+def _oracle_branch(args):
+    """One branch through the CPU oracle (a worker of the all-core pool)."""
+    import oracle
+    ops, recs, n_qubits, noise = args
+    return oracle.analyze(ops, recs, n_qubits, noise, "L2").n_mechanisms
+
+
+def cpu_batch_baseline(branches, budget_s: float = 10.0) -> dict:
+    """The oracle as it stands over the batch's branches on every host core
+    (one branch per worker process, started with spawn), on the branches that
+    fit about ``budget_s`` of wall time."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    work = [(b.ops, b.recs, b.n_qubits, np.asarray(b.default_noise, np.float64)) for b in branches]
+    t0 = time.perf_counter()
+    done = n_mech = 0
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for k in range(0, len(work), cores):
+            n_mech += sum(pool.map(_oracle_branch, work[k:k + cores]))
+            done = min(k + cores, len(work))
+            if time.perf_counter() - t0 >= budget_s:
+                break
+    el = time.perf_counter() - t0
+    return {"value": n_mech / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {len(work)} branches in {el:.1f} s (pool start included), one per process"}
+
+
 def batch_section(args, world: int) -> dict:
     """Adaptive [[4,2,2]]-concatenated surface code, outer distance 10: 256
     realised branches of 10-30 cycles (block firing 5 % per cycle, refresh
@@ -232,6 +261,7 @@ def batch_section(args, world: int) -> dict:
         plain_ms.append(ms)
         plain_pc.append(ms * 1e3 / cyc[i])
     plain_pc = np.array(plain_pc)
+    cpu = cpu_batch_baseline(branches) if not args.no_cpu_baseline else None
     return {
         "workload": "adaptive [[4,2,2]]-concatenated surface code d=10, %d branches of 10-30 cycles, p=1e-3, L2" % n,
         "mechanisms": n_mech, "cycles": total_cycles, "qubits_per_branch": lay.n_qubits,
@@ -240,6 +270,7 @@ def batch_section(args, world: int) -> dict:
                     "per_cycle_us_p99": float(np.percentile(batched_pc, 99)),
                     "mechanisms_per_s": n_mech / (np.median(reps) / 1e3),
                     "tuning": {k: v for k, v in tune.items() if k != "ms"}},
+        "cpu_all_cores": cpu,
         "plain": {"ms_per_branch_p50": float(np.median(plain_ms)),
                   "per_cycle_us_p50": float(np.percentile(plain_pc, 50)),
                   "per_cycle_us_p99": float(np.percentile(plain_pc, 99)),
