@@ -261,7 +261,7 @@ def batch_section(args, world: int) -> dict:
         plain_ms.append(ms)
         plain_pc.append(ms * 1e3 / cyc[i])
     plain_pc = np.array(plain_pc)
-    cpu = cpu_batch_baseline(branches) if not args.no_cpu_baseline else None
+    cpu = cpu_batch_baseline(branches) if not args.no_cpu_baseline and world == 1 else None
     return {
         "workload": "adaptive [[4,2,2]]-concatenated surface code d=10, %d branches of 10-30 cycles, p=1e-3, L2" % n,
         "mechanisms": n_mech, "cycles": total_cycles, "qubits_per_branch": lay.n_qubits,
@@ -615,7 +615,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:      # the oracle's baseline: N = 1 only
             result["cpu_baseline"] = cpu_baseline(circ, noise)
         if args.levels_steps > 0:
             result["levels"] = levels_section(args)
