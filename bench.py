@@ -508,7 +508,6 @@ def run_ours(args):
     nz = torch.tensor(noise, device="cuda")
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    drv.enable_timing(True)
 
     for _ in range(max(args.warmup, 3)):
         dem = drv.compile(dc, nz)
@@ -527,7 +526,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     barrier()
     sampler.start()
-    step_ms, stage_us = [], []
+    step_ms = []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
@@ -537,9 +536,17 @@ def run_ours(args):
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
-        stage_us.append(drv.last_timing())
     barrier()
     clocks = sampler.stop()
+    # per-stage device times from a separate, untimed pass: the library's
+    # stage events are instrumentation and stay out of the timed steps
+    drv.enable_timing(True)
+    stage_us = []
+    for _ in range(max(50, min(args.steps, 200))):
+        flush.fill_(1)
+        drv.compile(dc, nz)
+        stage_us.append(drv.last_timing())
+    drv.enable_timing(False)
     total_ms = max_over_ranks(float(sum(step_ms)), dist, "cuda")
     value = job_rate(n_mech * args.steps, world, total_ms / 1e3)
     per_cycle = np.array(step_ms) * 1e3 / 25

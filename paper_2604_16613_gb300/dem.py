@@ -128,13 +128,30 @@ class Dem:
         self.n_det_entries = view.n_det_entries
         self.n_mechanisms = view.n_mechanisms
         self.edge_offsets = np.array([view.edge_offsets[i] for i in range(view.n_circuits + 1)], np.int64)
-        self.det_offsets = _view(view.det_offsets, self.n_edges + 1, torch.int32, driver)
-        self.det_idx = _view(view.det_idx, self.n_det_entries, torch.int32, driver)
-        self.obs_mask = _view(view.obs_mask, self.n_edges, torch.int64, driver)
-        self.prob = _view(view.prob, self.n_edges, torch.float32, driver)
-        self.logodds = _view(view.logodds, self.n_edges, torch.float32, driver)
-        self.edge_circuit = _view(view.edge_circuit, self.n_edges, torch.int32, driver)
-        self.mech_class = _view(view.mech_class, self.n_mechanisms, torch.int32, driver)
+        # device pointers; the tensors over them are made on first access
+        self._ptr = {"det_offsets": (view.det_offsets, self.n_edges + 1, torch.int32),
+                     "det_idx": (view.det_idx, self.n_det_entries, torch.int32),
+                     "obs_mask": (view.obs_mask, self.n_edges, torch.int64),
+                     "prob": (view.prob, self.n_edges, torch.float32),
+                     "logodds": (view.logodds, self.n_edges, torch.float32),
+                     "edge_circuit": (view.edge_circuit, self.n_edges, torch.int32),
+                     "mech_class": (view.mech_class, self.n_mechanisms, torch.int32)}
+        self._tensors: dict = {}
+
+    def _tensor(self, name: str) -> torch.Tensor:
+        t = self._tensors.get(name)
+        if t is None:
+            ptr, n, dtype = self._ptr[name]
+            t = self._tensors[name] = _view(ptr, n, dtype, self.driver)
+        return t
+
+    det_offsets = property(lambda self: self._tensor("det_offsets"))
+    det_idx = property(lambda self: self._tensor("det_idx"))
+    obs_mask = property(lambda self: self._tensor("obs_mask"))
+    prob = property(lambda self: self._tensor("prob"))
+    logodds = property(lambda self: self._tensor("logodds"))
+    edge_circuit = property(lambda self: self._tensor("edge_circuit"))
+    mech_class = property(lambda self: self._tensor("mech_class"))
 
     def _check(self):
         if self.driver.generation != self.generation:
