@@ -21,6 +21,7 @@ constexpr uint64_t kPoolSlack = 1ull << 22;  // record-pool slack for unused chu
 constexpr int kPackThreads = 256;       // layer packing block size
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint32_t kTailItem = 0x80000000u;     // work item: the tail half of a long walk
 constexpr uint32_t kObsColFlag = 0x80000000u;   // set on the column id of an
                                                 // observable word in a mask
 
@@ -246,6 +247,10 @@ __device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t coun
 }
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// arrive on behalf of `count` participants
+__device__ __forceinline__ void mbar_arrive_count(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -52,6 +52,7 @@ namespace gpdem {
 namespace {
 
 constexpr int kSegCache = 256;      // layer segments cached for the producer
+constexpr uint32_t kSplitMinLayers = 64;   // observable walks at least this long are split
 constexpr int kMaxBufs = 4;         // window ring slots at most
 
 struct Smem {
@@ -839,7 +840,9 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         __syncthreads();
         const uint32_t item = sh.item;
         if (item >= P.n_items || sh.bail || sh.tmo) break;
-        const uint32_t gcol = B.items[item];
+        const uint32_t item_word = B.items[item];
+        const bool tail = (item_word & kTailItem) != 0u;
+        const uint32_t gcol = item_word & ~kTailItem;
         const uint32_t cidx = B.col_circ[gcol];
         const CircuitDev &C = B.circ[cidx];
         const uint32_t local = gcol - C.col_base;
@@ -857,6 +860,14 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         if (n_ent == 0u) { __syncthreads(); continue; }
         const uint32_t lmax = sh.lmax - 1u;
         const uint32_t lmin = s.ent_l[0];
+        // a long observable walk is shared by two blocks (two work items):
+        // the head emits the steps lmax .. mid; the tail fast-forwards through
+        // them (gates undone, nothing emitted or published) and emits the
+        // steps mid - 1 .. -1.  Fast-forwarding costs about 0.6 of an emitting
+        // step, so mid near 2/7 of lmax balances the two.
+        const bool split_col = is_obs && lmax >= kSplitMinLayers;
+        const int mid = split_col ? max(1, (int)(2u * lmax / 7u)) : -2;
+        if (tail && !split_col) { __syncthreads(); continue; }
         const LayerGeo geo = layer_geo(nq);
         const unsigned char *qbase = B.qidx + (size_t)C.qidx_off * 16u;
         const uint2 *lbase = B.lists + 2ull * C.op_base;
@@ -870,6 +881,14 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
             int L = (int)lmax;
             bool ok = true;
             uint32_t slot = slot_of(L);
+            // fast-forward steps (tail, L >= mid) keep their active lists in
+            // the two act buffers alternately, arranged so that the last one
+            // lands where the first emitting step reads its predecessor's
+            uint32_t ff_buf = 0u;
+            if (tail) {
+                const uint32_t n_ff = lmax - (uint32_t)mid + 1u;
+                ff_buf = ((st & 1u) ^ 1u) ^ ((n_ff - 1u) & 1u);
+            }
             // the gates of L undone for one candidate (registers from the
             // activity pass): the owner of a two-qubit gate (its active
             // qubit, or its control / first qubit when both are active)
@@ -909,19 +928,23 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                 return kNone;
             };
             for (;;) {
+                const bool ff = tail && L >= mid;
+                const bool snap = !ff;            // a snapshot is published for the emitters
                 const uint32_t b = st & 1u;
                 if (!wait_warp(&sh.win_full[slot], (full_par >> slot) & 1u)) { ok = false; break; }
                 full_par ^= 1u << slot;
                 const Window v = sh.desc[slot];
-                if ((tfree_pend >> b) & 1u) {
-                    if (!wait_warp(&sh.tab_free[b], (tfree_par >> b) & 1u)) { ok = false; break; }
-                    tfree_par ^= 1u << b;
+                if (snap) {
+                    if ((tfree_pend >> b) & 1u) {
+                        if (!wait_warp(&sh.tab_free[b], (tfree_par >> b) & 1u)) { ok = false; break; }
+                        tfree_par ^= 1u << b;
+                    }
+                    tfree_pend |= 1u << b;
                 }
-                tfree_pend |= 1u << b;
-                const uint16_t *prev = act_of(s, b ^ 1u);
+                const uint16_t *prev = ff ? act_of(s, ff_buf ^ 1u) : act_of(s, b ^ 1u);
                 ulonglong2 *const tb = tab_of(s, b);
                 uint32_t *const tg = tag_of(s, b);
-                uint16_t *const ab = act_of(s, b);
+                uint16_t *const ab = ff ? act_of(s, ff_buf) : act_of(s, b);
                 const uint32_t n_cand = n_prev + n_add;
                 uint32_t n_act = 0, n_new = 0;
                 // activity and snapshot of candidates c0, c1 (one lane's pair)
@@ -938,8 +961,8 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     a1 = i1 < n_cand && (p1.x | p1.y) != 0ull;
                     if (i0 < n_cand) s.bits[q0] = a0 ? kActive : (unsigned char)0;
                     if (i1 < n_cand) s.bits[q1] = a1 ? kActive : (unsigned char)0;
-                    if (a0) { tb[q0] = p0; tg[q0] = st; }
-                    if (a1) { tb[q1] = p1; tg[q1] = st; }
+                    if (a0 && snap) { tb[q0] = p0; tg[q0] = st; }
+                    if (a1 && snap) { tb[q1] = p1; tg[q1] = st; }
                     if (L < 0 && ((a0 && p0.y != 0ull) || (a1 && p1.y != 0ull)))
                         report(B.status, GP_ERR_NONDETERMINISTIC, cidx, 0xFFFFFFFFu, gcol);
                     const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0), m1 = __ballot_sync(0xFFFFFFFFu, a1);
@@ -956,6 +979,10 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     n_new += __popc(m);
                 };
                 auto publish = [&]() {
+                    if (!snap) {
+                        __syncwarp();
+                        return;
+                    }
                     if (lane == 0u) sh.step[b] = StepDesc{L, n_act, slot, 0u};
                     __syncwarp();
                     if (lane == 0u) mbar_arrive(&sh.tab_full[b]);
@@ -968,7 +995,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     const uint32_t g0 = L >= 0 ? v.gate[q0] : 0u;
                     const bool a0 = lane < n_cand && (p0.x | p0.y) != 0ull;
                     if (lane < n_cand) s.bits[q0] = a0 ? kActive : (unsigned char)0;
-                    if (a0) { tb[q0] = p0; tg[q0] = st; }
+                    if (a0 && snap) { tb[q0] = p0; tg[q0] = st; }
                     if (L < 0 && a0 && p0.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, 0xFFFFFFFFu, gcol);
                     const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0);
                     if (a0) ab[__popc(m0 & lt_mask)] = (uint16_t)q0;
@@ -1034,12 +1061,19 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     }
                 }
                 __syncwarp();
-                if (lane == 0u) mbar_arrive(&sh.win_free[slot]);
-                st++;
+                // the emitters see no fast-forward step: the walker releases
+                // its window for them too
+                if (lane == 0u) {
+                    if (ff) mbar_arrive_count(&sh.win_free[slot], NE + 1u);
+                    else mbar_arrive(&sh.win_free[slot]);
+                }
+                if (ff) ff_buf ^= 1u;
+                else st++;
                 slot = slot == 0u ? nring - 1u : slot - 1u;   // window L - 1
                 n_prev = n_act;
                 n_add = n_new;
                 if (L < 0) break;
+                if (split_col && !tail && L == mid) break;      // the head's last step
                 if (L == 0) { L = -1; continue; }
                 if (n_prev + n_add == 0u && (uint32_t)(L - 1) < lmin) break;
                 L--;
