@@ -102,7 +102,7 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     B.status = c.take<Status>(1);
     B.circ = c.take<CircuitDev>(bd.max_circuits);
     B.tiles = c.take<uint2>(L.max_tiles);
-    B.items = c.take<uint32_t>(L.max_cols + bd.max_circuits);    // + a tail item per circuit
+    B.items = c.take<uint32_t>(L.max_cols + (kMaxSegments - 1u) * bd.max_circuits);   // + segment items
     B.col_circ = c.take<uint32_t>(L.max_cols);
     if (params_bytes) *params_bytes = align_up(c.off, 256);
     B.ops_arena = c.take<uint4>(bd.max_ops);
@@ -577,23 +577,24 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
         if (recs_total > bd.max_recs) return fail(GP_ERR_CAPACITY, "total record lookbacks exceed max_recs");
         if (det_total > bd.max_detectors) return fail(GP_ERR_CAPACITY, "total detectors exceed max_detectors");
         if (loc_total > bd.max_locations) return fail(GP_ERR_CAPACITY, "total noise locations exceed max_locations");
-        if (cols_total > L.max_cols || tiles_total > L.max_tiles) return fail(GP_ERR_CAPACITY, "batch too large for the driver");
+        if (cols_total > L.max_cols || tiles_total > L.max_tiles || cols_total > kColMask)
+            return fail(GP_ERR_CAPACITY, "batch too large for the driver");
     }
     // stage-1 work order: observable words first (they span whole circuits;
-    // with the role-split walk each is two items, the tail half first), then
-    // detector words in order
+    // with the role-split walk each is kMaxSegments items, one per segment,
+    // the latest-starting first), then detector words in order
     const uint32_t want1 = d->tuning.stage1_blocks_per_sm ? d->tuning.stage1_blocks_per_sm : 1u;
     const bool split_walk = stage1_shape(bd.max_qubits, want1, d->smem_limit).split != 0u;
     uint32_t ni = 0;
     for (uint32_t b = 0; b < n_circuits; b++) {
         const CircuitDev &C = hc[b];
         for (uint32_t k = 0; k < C.n_cols; k++) hcolc[C.col_base + k] = b;
-        if (C.n_obs && split_walk) hitems[ni++] = (C.col_base + C.n_cols - 1) | kTailItem;
     }
-    for (uint32_t b = 0; b < n_circuits; b++) {
-        const CircuitDev &C = hc[b];
-        if (C.n_obs) hitems[ni++] = C.col_base + C.n_cols - 1;
-    }
+    for (uint32_t k = split_walk ? kMaxSegments : 1u; k-- > 0;)
+        for (uint32_t b = 0; b < n_circuits; b++) {
+            const CircuitDev &C = hc[b];
+            if (C.n_obs) hitems[ni++] = (C.col_base + C.n_cols - 1) | (k << kSegShift);
+        }
     for (uint32_t b = 0; b < n_circuits; b++) {
         const CircuitDev &C = hc[b];
         const uint32_t nd = C.n_cols - (C.n_obs ? 1u : 0u);

@@ -21,7 +21,11 @@ constexpr uint64_t kPoolSlack = 1ull << 22;  // record-pool slack for unused chu
 constexpr int kPackThreads = 256;       // layer packing block size
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
-constexpr uint32_t kTailItem = 0x80000000u;     // work item: the tail half of a long walk
+// stage-1 work item: column id | segment << kSegShift (segments of a long
+// observable walk that separate blocks share)
+constexpr uint32_t kSegShift = 30;
+constexpr uint32_t kColMask = (1u << kSegShift) - 1u;
+constexpr uint32_t kMaxSegments = 3;
 constexpr uint32_t kObsColFlag = 0x80000000u;   // set on the column id of an
                                                 // observable word in a mask
 

@@ -52,7 +52,7 @@ namespace gpdem {
 namespace {
 
 constexpr int kSegCache = 256;      // layer segments cached for the producer
-constexpr uint32_t kSplitMinLayers = 64;   // observable walks at least this long are split
+constexpr uint32_t kSplitMinLayers = 64;   // observable walks this long are split in two (twice: three)
 constexpr int kMaxBufs = 4;         // window ring slots at most
 
 struct Smem {
@@ -841,8 +841,8 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         const uint32_t item = sh.item;
         if (item >= P.n_items || sh.bail || sh.tmo) break;
         const uint32_t item_word = B.items[item];
-        const bool tail = (item_word & kTailItem) != 0u;
-        const uint32_t gcol = item_word & ~kTailItem;
+        const uint32_t seg = item_word >> kSegShift;      // segment of a split walk
+        const uint32_t gcol = item_word & kColMask;
         const uint32_t cidx = B.col_circ[gcol];
         const CircuitDev &C = B.circ[cidx];
         const uint32_t local = gcol - C.col_base;
@@ -860,14 +860,23 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         if (n_ent == 0u) { __syncthreads(); continue; }
         const uint32_t lmax = sh.lmax - 1u;
         const uint32_t lmin = s.ent_l[0];
-        // a long observable walk is shared by two blocks (two work items):
-        // the head emits the steps lmax .. mid; the tail fast-forwards through
-        // them (gates undone, nothing emitted or published) and emits the
-        // steps mid - 1 .. -1.  Fast-forwarding costs about 0.6 of an emitting
-        // step, so mid near 2/7 of lmax balances the two.
-        const bool split_col = is_obs && lmax >= kSplitMinLayers;
-        const int mid = split_col ? max(1, (int)(2u * lmax / 7u)) : -2;
-        if (tail && !split_col) { __syncthreads(); continue; }
+        // a long observable walk is shared by up to three blocks (one work
+        // item each): segment k emits the steps emit_hi .. emit_lo and
+        // fast-forwards through the steps above emit_hi first (gates undone,
+        // nothing emitted or published).  A fast-forward step costs about
+        // 0.73 of an emitting one, so segments of equal time emit, from the
+        // top: 79 % / 21 % of the walk (two segments), 74.5 % / 20 % / 5.5 %
+        // (three).
+        const uint32_t n_seg = !is_obs ? 1u : (lmax >= 2u * kSplitMinLayers ? 3u : (lmax >= kSplitMinLayers ? 2u : 1u));
+        if (seg >= n_seg) { __syncthreads(); continue; }
+        int b1 = -1, b2 = -1;                             // segment boundaries
+        if (n_seg == 2u) b1 = max(1, (int)(3u * lmax / 14u));
+        if (n_seg == 3u) {
+            b1 = max(2, (int)(51u * lmax / 200u));
+            b2 = min(b1 - 1, max(1, (int)(11u * lmax / 200u)));
+        }
+        const int emit_hi = seg == 0u ? (int)lmax : (seg == 1u ? b1 - 1 : b2 - 1);
+        const int emit_lo = seg + 1u == n_seg ? -1 : (seg == 0u ? b1 : b2);
         const LayerGeo geo = layer_geo(nq);
         const unsigned char *qbase = B.qidx + (size_t)C.qidx_off * 16u;
         const uint2 *lbase = B.lists + 2ull * C.op_base;
@@ -881,12 +890,12 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
             int L = (int)lmax;
             bool ok = true;
             uint32_t slot = slot_of(L);
-            // fast-forward steps (tail, L >= mid) keep their active lists in
-            // the two act buffers alternately, arranged so that the last one
-            // lands where the first emitting step reads its predecessor's
+            // fast-forward steps (L > emit_hi) keep their active lists in the
+            // two act buffers alternately, arranged so that the last one lands
+            // where the first emitting step reads its predecessor's
             uint32_t ff_buf = 0u;
-            if (tail) {
-                const uint32_t n_ff = lmax - (uint32_t)mid + 1u;
+            if (emit_hi < (int)lmax) {
+                const uint32_t n_ff = lmax - (uint32_t)emit_hi;
                 ff_buf = ((st & 1u) ^ 1u) ^ ((n_ff - 1u) & 1u);
             }
             // the gates of L undone for one candidate (registers from the
@@ -928,7 +937,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                 return kNone;
             };
             for (;;) {
-                const bool ff = tail && L >= mid;
+                const bool ff = L > emit_hi;
                 const bool snap = !ff;            // a snapshot is published for the emitters
                 const uint32_t b = st & 1u;
                 if (!wait_warp(&sh.win_full[slot], (full_par >> slot) & 1u)) { ok = false; break; }
@@ -1073,7 +1082,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                 n_prev = n_act;
                 n_add = n_new;
                 if (L < 0) break;
-                if (split_col && !tail && L == mid) break;      // the head's last step
+                if (emit_lo >= 0 && L == emit_lo) break;        // the segment's last step
                 if (L == 0) { L = -1; continue; }
                 if (n_prev + n_add == 0u && (uint32_t)(L - 1) < lmin) break;
                 L--;
