@@ -446,7 +446,15 @@ def serve_section(args) -> dict:
                                      [float(x) for x in np.mean(np.array(step_parts), axis=0)])),
         }
 
-    loads = [run(r, 5 + n) for n, r in enumerate(rates)]
+    # the Python loop is the client, not the server: keep the interpreter's
+    # collector from pausing it in the middle of a load
+    import gc
+    gc.collect()
+    gc.disable()
+    try:
+        loads = [run(r, 5 + n) for n, r in enumerate(rates)]
+    finally:
+        gc.enable()
     srv.close()
     return {
         "workload": f"{P} patches (surface d=5..25 odd : BB [[144,12,12]] = 3:1), Poisson per-cycle requests, "
