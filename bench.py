@@ -565,7 +565,9 @@ def run_ours(args):
     stage_mean = {n: float(st[:, i].mean()) for i, n in enumerate(stage_names)}
     dom = max(stage_mean, key=stage_mean.get)
 
-    # algorithmic bytes (per launch of each stage; definitions in the design doc)
+    # algorithmic bytes per launch of each stage: the bytes a stage must read
+    # and write once (16 B per row, 4 B per record, location and class id,
+    # 12 B per mask word, 24 B per hyperedge plus its detector ids)
     words = mask_word_count(host, mclass)
     n_ops, n_recs = circ.n_ops, int(circ.recs.size)
     b_in = 16 * n_ops + 4 * n_recs + 4 * circ.n_locations
