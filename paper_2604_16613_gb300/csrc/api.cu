@@ -121,7 +121,6 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     B.obs_rows = c.take<uint32_t>(bd.max_ops);
     B.obs_count = c.take<uint32_t>(bd.max_circuits);
     B.mech_cnt = c.take<uint32_t>(bd.max_mechanisms);
-    B.mech_fill = c.take<uint32_t>(bd.max_mechanisms);
     B.mech_off = c.take<uint2>((uint64_t)bd.max_mechanisms + 1);
     B.mech_info = c.take<unsigned long long>(bd.max_mechanisms);
     B.slot_col = c.take<uint32_t>(L.rec_cap);
@@ -141,6 +140,7 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     B.prob = c.take<float>(bd.max_mechanisms);
     B.logodds = c.take<float>(bd.max_mechanisms);
     B.class_slot = c.take<uint32_t>(bd.max_mechanisms);
+    B.edge_mech = c.take<uint32_t>(bd.max_mechanisms);
     B.edge_circ = c.take<uint32_t>(bd.max_mechanisms);
     B.circ_edges = c.take<uint32_t>(bd.max_circuits);
     B.gacc = c.take<unsigned long long>(2ull * std::max<uint32_t>(bd.max_locations, 1));
@@ -209,7 +209,6 @@ gp_status full_reset(gp_driver *d, cudaStream_t s) {
     launch_init_table(d->B.table, (size_t)1 << L.table_log2, s);
     GP_CUDA(cudaGetLastError());
     GP_CUDA(cudaMemsetAsync(d->B.mech_cnt, 0, sizeof(uint32_t) * (size_t)d->bounds.max_mechanisms, s));
-    GP_CUDA(cudaMemsetAsync(d->B.mech_fill, 0, sizeof(uint32_t) * (size_t)d->bounds.max_mechanisms, s));
     GP_CUDA(cudaMemsetAsync(d->B.gacc, 0, 2 * sizeof(unsigned long long) * std::max<uint32_t>(d->bounds.max_locations, 1), s));
     GP_CUDA(cudaMemsetAsync(d->B.records, 0xFF, sizeof(uint4) * L.rec_cap, s));
     GP_CUDA(cudaMemsetAsync(d->B.lists, 0, sizeof(uint2) * (2ull * d->bounds.max_ops + 4), s));

@@ -88,7 +88,8 @@ struct Status {
 struct TabSlot {
     unsigned long long entry;   // key_hi << 32 | claiming mechanism, or kEmpty
     uint32_t min;               // smallest member mechanism
-    uint32_t cls;               // hyperedge index once compacted
+    uint32_t cls;               // detector count of the mask (set by the claim),
+                                // then the hyperedge index once compacted
     unsigned long long acc_lo;  // 128-bit fixed-point sum of t over members
     unsigned long long acc_hi;
 };
@@ -119,8 +120,9 @@ struct Buffers {
     uint32_t *det_row;          // per detector: its row
     uint32_t *obs_rows;         // per circuit (at op_base): OBSERVABLE rows
     uint32_t *obs_count;        // per circuit
-    uint32_t *mech_cnt;         // per mechanism: mask words produced (stage 1)
-    uint32_t *mech_fill;        // per mechanism: words placed so far (scatter)
+    uint32_t *mech_cnt;         // per mechanism: mask words produced (stage 1),
+                                // counted back down to 0 by the scatter
+    uint32_t *edge_mech;        // per hyperedge: its class's smallest mechanism
     uint2 *mech_off;            // per mechanism: start of its words (.x), n + 1
     unsigned long long *mech_info;   // loc | kind << 32 | comp << 40 | circuit << 48
     uint32_t *slot_col;         // mask words in mechanism order: column ids

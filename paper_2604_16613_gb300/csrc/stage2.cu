@@ -3,7 +3,9 @@
 // Stage 1 leaves mask-word records {mechanism, column, word} in a pool and a
 // word count per mechanism.  Stage 2:
 //   offsets    exclusive scan of the counts -> per-mechanism word ranges (CSR)
-//   scatter    records -> their mechanism's range (the pool cleans itself)
+//   scatter    records -> their mechanism's range, counting the mechanism's
+//              word count back down to 0 (the pool and the counts clean
+//              themselves)
 //   group      one thread per mechanism: sort its words by column, hash them,
 //              claim or join a slot of an open-addressing table whose claims
 //              are verified word by word (grouping is exact whatever the hash
@@ -13,11 +15,12 @@
 //              integer addition makes the sum independent of the order in
 //              which the atomics land
 //   compact    classes are numbered by their smallest member (scan of
-//              "leader" flags and detector counts), each leader writes its
-//              hyperedge: ascending detector ids, observable word,
+//              "leader" flags and detector counts; the scan also lists the
+//              leaders in edge order), one thread per hyperedge writes
+//              it: ascending detector ids, observable word,
 //              P = -expm1(-T) / 2 and w = log1p(-P) - log(P)
-//   finalize   per-mechanism class ids; counters and used table slots are
-//              cleared for the next compile
+//   finalize   per-mechanism class ids; used table slots are cleared for
+//              the next compile
 //   backward   dP/dp_i = (1 - 2P) / 2 * dt_i/dp and dw/dP = -1 / (P (1 - P)),
 //              summed per noise location in fixed point
 // The scans are two-pass reduce-then-scan passes (2048 elements per block)
@@ -71,10 +74,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint2 *
 
 // level 2: exclusive prefix of every value.  Each block adds up the sums of
 // the blocks before it itself (a few hundred values), so no separate pass
-// scans the block sums; block 0 also writes out[n] = the total.
+// scans the block sums; block 0 also writes out[n] = the total.  With a
+// list, the first channel is a 0/1 flag and every flagged index i is listed
+// at its rank: list[out[i].x] = i.
 __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in, const uint32_t *cnt,
                                                                  const uint32_t *n_ptr, const uint2 *bsum,
-                                                                 uint2 *out, const Status *st) {
+                                                                 uint2 *out, uint32_t *list, const Status *st) {
     if (st->code != 0u) return;
     const uint32_t n = *n_ptr;
     const uint32_t b0 = blockIdx.x * kScanBlock;
@@ -103,7 +108,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in
     uint2 run = add2(block_scan2(acc, tmp, tot), prefix);
     for (int k = 0; k < kScanPer; k++) {
         const uint32_t i = b0 + threadIdx.x * kScanPer + k;
-        if (i < n) out[i] = run;
+        if (i < n) {
+            out[i] = run;
+            if (list && v[k].x) list[run.x] = i;
+        }
         run = add2(run, v[k]);
     }
 }
@@ -118,7 +126,7 @@ __global__ void scatter_kernel(Buffers B) {
         const uint4 r = B.records[i];
         if (r.x == kNone) continue;
         B.records[i].x = kNone;
-        const uint32_t pos = B.mech_off[r.x].x + atomicAdd(&B.mech_fill[r.x], 1u);
+        const uint32_t pos = B.mech_off[r.x].x + atomicSub(&B.mech_cnt[r.x], 1u) - 1u;
         B.slot_col[pos] = r.y;
         B.slot_word[pos] = ((unsigned long long)r.w << 32) | r.z;
     }
@@ -198,7 +206,15 @@ __global__ void group_kernel(Buffers B) {
             unsigned long long e = __ldcg(&B.table[pos].entry);
             if (e == kEmpty) {
                 const unsigned long long old = atomicCAS(&B.table[pos].entry, kEmpty, mine);
-                if (old == kEmpty) { slot = pos; break; }
+                if (old == kEmpty) {
+                    // the claim records the class's detector count
+                    uint32_t dets = 0;
+                    for (uint32_t i = 0; i < cnt; i++)
+                        if (!(col[i] & kObsColFlag)) dets += __popcll(w[i]);
+                    B.table[pos].cls = dets;
+                    slot = pos;
+                    break;
+                }
                 e = old;
             }
             if ((uint32_t)(e >> 32) == key_hi && same_mask(B, (uint32_t)e, cnt, col, w)) { slot = pos; break; }
@@ -217,15 +233,14 @@ __global__ void group_kernel(Buffers B) {
     }
 }
 
-// leader flag and detector count of mechanism m
+// leader flag and detector count of mechanism m (the count the class's
+// claim left in its slot)
 __device__ __forceinline__ uint2 leader_info(const Buffers &B, uint32_t m) {
     const uint32_t slot = B.slot_of[m];
-    if (slot == kNone || B.table[slot].min != m) return make_uint2(0, 0);
-    const uint32_t o0 = B.mech_off[m].x, o1 = B.mech_off[m + 1].x;
-    uint32_t dets = 0;
-    for (uint32_t i = o0; i < o1; i++)
-        if (!(B.slot_col[i] & kObsColFlag)) dets += __popcll(B.slot_word[i]);
-    return make_uint2(1, dets);
+    if (slot == kNone) return make_uint2(0, 0);
+    const TabSlot &ts = B.table[slot];
+    if (ts.min != m) return make_uint2(0, 0);
+    return make_uint2(1, ts.cls);
 }
 
 __global__ void leaders_kernel(Buffers B) {
@@ -250,15 +265,15 @@ __global__ void compact_write_kernel(Buffers B) {
         B.status->n_det_entries = tot.y;
         B.det_off[tot.x] = tot.y;
     }
+    const uint32_t E = tot.x;
     const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < N; base += gridDim.x * blockDim.x) {
-        const uint32_t m = base + threadIdx.x;
-        const bool lead = m < N && B.scan_val[m].x != 0u;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
+        const uint32_t e = base + threadIdx.x;
         uint32_t b = 0xFFFFFFFFu;
-        if (lead) {
-            const uint2 off = B.comp_off[m];
-            const uint32_t e = off.x;
-            uint32_t d = off.y;
+        if (e < E) {
+            const uint32_t m = B.edge_mech[e];
+            const uint32_t d0 = B.comp_off[m].y;
+            uint32_t d = d0;
             const uint32_t slot = B.slot_of[m];
             const unsigned long long info = B.mech_info[m];
             b = (uint32_t)(info >> 48);
@@ -287,7 +302,7 @@ __global__ void compact_write_kernel(Buffers B) {
             const TabSlot &ts = B.table[slot];
             const float T = fixed_to_float(ts.acc_lo, ts.acc_hi, kProbShift);
             const float Pc = -0.5f * expm1f(-T);
-            B.det_off[e] = off.y;
+            B.det_off[e] = d0;
             B.obs_mask[e] = obs;
             B.prob[e] = Pc;
             B.logodds[e] = log1pf(-Pc) - logf(Pc);
@@ -297,12 +312,12 @@ __global__ void compact_write_kernel(Buffers B) {
         }
         // edges per circuit: one atomic per circuit present in the warp
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
-        if (lead && (uint32_t)(__ffs(peers) - 1) == lane) atomicAdd(&B.circ_edges[b], (uint32_t)__popc(peers));
+        if (e < E && (uint32_t)(__ffs(peers) - 1) == lane) atomicAdd(&B.circ_edges[b], (uint32_t)__popc(peers));
     }
 }
 
-// per-mechanism class ids and counters reset (i < N), used table slots
-// cleared (i < E): disjoint fields, one pass
+// per-mechanism class ids (i < N), used table slots cleared (i < E):
+// disjoint fields, one pass
 __global__ void finalize_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const uint32_t N = B.status->n_mech, E = B.status->n_edges;
@@ -311,8 +326,6 @@ __global__ void finalize_kernel(Buffers B) {
         if (i < N) {
             const uint32_t slot = B.slot_of[i];
             B.mech_class[i] = (slot == kNone) ? -1 : (int32_t)B.table[slot].cls;
-            B.mech_cnt[i] = 0u;
-            B.mech_fill[i] = 0u;
         }
         if (i < E) {
             TabSlot &ts = B.table[B.class_slot[i]];
@@ -370,13 +383,14 @@ __global__ void init_table_kernel(TabSlot *t, size_t n) {
 
 // exclusive scan of n (read on the device) uint2 values: out[i] = sum of
 // in[0..i), out[n] = the total; blocks of 2048 values, two passes.  With
-// in == nullptr the values are (cnt[i], 0).
+// in == nullptr the values are (cnt[i], 0); with a list, the indices whose
+// first channel is 1 are listed in order.
 void launch_scan_counts(const Buffers &B, const uint2 *in, const uint32_t *cnt, const uint32_t *n_ptr, uint2 *out,
-                        uint32_t max_n, cudaStream_t s, uint32_t *launches) {
+                        uint32_t max_n, cudaStream_t s, uint32_t *launches, uint32_t *list = nullptr) {
     const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
     const uint32_t grid1 = g1 ? g1 : 1u;
     scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, B.status);
-    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, out, B.status);
+    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, out, list, B.status);
     *launches += 2;
 }
 
@@ -397,7 +411,7 @@ void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t ma
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
                     uint32_t *launches) {
     leaders_kernel<<<grid, threads, 0, s>>>(b);
-    launch_scan(b, b.scan_val, &b.status->n_mech, b.comp_off, max_mech, s, launches);
+    launch_scan_counts(b, b.scan_val, nullptr, &b.status->n_mech, b.comp_off, max_mech, s, launches, b.edge_mech);
     compact_write_kernel<<<grid, threads, 0, s>>>(b);
     finalize_kernel<<<grid, threads, 0, s>>>(b);
     *launches += 3;
