@@ -118,17 +118,34 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in
 
 
 // ---- per-mechanism words ----------------------------------------------------
-__global__ void scatter_kernel(Buffers B) {
+// Each thread moves kScatterILP records per round, with every load and atomic
+// of the round in flight before the first store (the kernel is bound by their
+// latency).
+constexpr int kScatterILP = 3;
+
+__global__ void __launch_bounds__(512, 4) scatter_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const Params &P = *B.params;
     const uint32_t n = min(B.status->rec_count, P.rec_cap);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint4 r = B.records[i];
-        if (r.x == kNone) continue;
-        B.records[i].x = kNone;
-        const uint32_t pos = B.mech_off[r.x].x + atomicSub(&B.mech_cnt[r.x], 1u) - 1u;
-        B.slot_col[pos] = r.y;
-        B.slot_word[pos] = ((unsigned long long)r.w << 32) | r.z;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kScatterILP * stride) {
+        uint4 r[kScatterILP];
+#pragma unroll
+        for (int u = 0; u < kScatterILP; u++) {
+            const uint32_t i = i0 + u * stride;
+            r[u] = i < n ? B.records[i] : make_uint4(kNone, 0u, 0u, 0u);
+        }
+        uint32_t pos[kScatterILP];
+#pragma unroll
+        for (int u = 0; u < kScatterILP; u++)
+            if (r[u].x != kNone) pos[u] = __ldg(&B.mech_off[r[u].x].x) + atomicSub(&B.mech_cnt[r[u].x], 1u) - 1u;
+#pragma unroll
+        for (int u = 0; u < kScatterILP; u++) {
+            if (r[u].x == kNone) continue;
+            B.records[i0 + u * stride].x = kNone;
+            B.slot_col[pos[u]] = r[u].y;
+            B.slot_word[pos[u]] = ((unsigned long long)r[u].w << 32) | r[u].z;
+        }
     }
 }
 
@@ -233,21 +250,31 @@ __global__ void group_kernel(Buffers B) {
     }
 }
 
-// leader flag and detector count of mechanism m (the count the class's
-// claim left in its slot)
-__device__ __forceinline__ uint2 leader_info(const Buffers &B, uint32_t m) {
-    const uint32_t slot = B.slot_of[m];
-    if (slot == kNone) return make_uint2(0, 0);
-    const TabSlot &ts = B.table[slot];
-    if (ts.min != m) return make_uint2(0, 0);
-    return make_uint2(1, ts.cls);
-}
-
+// leader flag and detector count of every mechanism: (1, the count the
+// class's claim left in its slot) for the smallest member of a class, else
+// (0, 0).  Four mechanisms per thread and round, their loads in flight
+// together.
 __global__ void leaders_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const uint32_t N = B.status->n_mech;
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x)
-        B.scan_val[m] = leader_info(B, m);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t m0 = blockIdx.x * blockDim.x + threadIdx.x; m0 < N; m0 += 4u * stride) {
+        uint32_t slot[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t m = m0 + u * stride;
+            slot[u] = m < N ? B.slot_of[m] : kNone;
+        }
+        uint2 mc[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            mc[u] = slot[u] != kNone ? *reinterpret_cast<const uint2 *>(&B.table[slot[u]].min) : make_uint2(kNone, 0u);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t m = m0 + u * stride;
+            if (m < N) B.scan_val[m] = mc[u].x == m ? make_uint2(1u, mc[u].y) : make_uint2(0u, 0u);
+        }
+    }
 }
 
 __global__ void compact_write_kernel(Buffers B) {
@@ -317,22 +344,38 @@ __global__ void compact_write_kernel(Buffers B) {
 }
 
 // per-mechanism class ids (i < N), used table slots cleared (i < E):
-// disjoint fields, one pass
+// disjoint fields (cls is read, the others are cleared), one pass; four
+// indices per thread and round, their loads in flight together
 __global__ void finalize_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const uint32_t N = B.status->n_mech, E = B.status->n_edges;
     const uint32_t M = max(N, E);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-        if (i < N) {
-            const uint32_t slot = B.slot_of[i];
-            B.mech_class[i] = (slot == kNone) ? -1 : (int32_t)B.table[slot].cls;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += 4u * stride) {
+        uint32_t slot[4], cs[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = i0 + u * stride;
+            slot[u] = i < N ? B.slot_of[i] : kNone;
+            cs[u] = i < E ? B.class_slot[i] : kNone;
         }
-        if (i < E) {
-            TabSlot &ts = B.table[B.class_slot[i]];
+        uint32_t cls[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) cls[u] = slot[u] != kNone ? B.table[slot[u]].cls : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = i0 + u * stride;
+            if (i < N) B.mech_class[i] = slot[u] == kNone ? -1 : (int32_t)cls[u];
+        }
+        // cls is left alone: other threads may still be reading it (a claim
+        // overwrites it in the next compile)
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (cs[u] == kNone) continue;
+            TabSlot &ts = B.table[cs[u]];
             ts.entry = kEmpty;
             ts.min = kNone;
-            ts.acc_lo = 0ull;
-            ts.acc_hi = 0ull;
+            *reinterpret_cast<uint4 *>(&ts.acc_lo) = make_uint4(0u, 0u, 0u, 0u);   // acc_lo, acc_hi
         }
     }
 }
