@@ -73,35 +73,82 @@ __global__ void __launch_bounds__(kLowerThreads) tile_count_kernel(Buffers B) {
     }
 }
 
-// One block.  An exclusive scan of the tile sums over the whole batch gives
-// each tile's offset (tiles of a circuit are contiguous, so a tile's offset
-// within its circuit is its offset less that of the circuit's first tile);
-// then block scans over the circuits give the batch offsets.
-__global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
-    const Params &P = *B.params;
-    __shared__ uint32_t warp_tmp[kLowerThreads / 32];
-    __shared__ uint32_t carry_layer, carry_meas, carry_mech;
-    __shared__ unsigned long long carry_qidx;
-    __shared__ uint4 carry4;
-    if (threadIdx.x == 0) {
-        carry_layer = 0; carry_meas = 0; carry_mech = 0; carry_qidx = 0;
-        carry4 = make_uint4(0, 0, 0, 0);
+// block-wide exclusive scans of a uint4 (four channels at once) and of a
+// 64-bit value: warp shuffles, then one exchange of the warp totals
+constexpr int kLowerWarps = kLowerThreads / 32;
+
+__device__ __forceinline__ uint4 block_scan4(uint4 v, uint4 *warp_tot, uint4 &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xFFFFFFFFu, x.x, o), b = __shfl_up_sync(0xFFFFFFFFu, x.y, o);
+        const uint32_t c = __shfl_up_sync(0xFFFFFFFFu, x.z, o), d = __shfl_up_sync(0xFFFFFFFFu, x.w, o);
+        if (lane >= o) x = add4(x, make_uint4(a, b, c, d));
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    uint4 before = make_uint4(0, 0, 0, 0), all = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int w = 0; w < kLowerWarps; w++) {
+        const uint4 t = warp_tot[w];
+        if (w < warp) before = add4(before, t);
+        all = add4(all, t);
     }
     __syncthreads();
-    for (uint32_t base = 0; base < P.n_tiles; base += kLowerThreads) {
-        const uint32_t t = base + threadIdx.x;
-        const uint4 v = t < P.n_tiles ? B.tile_sums[t] : make_uint4(0, 0, 0, 0);
-        uint4 ex, tot4;
-        ex.x = block_exclusive_scan<kLowerThreads>(v.x, warp_tmp, tot4.x);
-        ex.y = block_exclusive_scan<kLowerThreads>(v.y, warp_tmp, tot4.y);
-        ex.z = block_exclusive_scan<kLowerThreads>(v.z, warp_tmp, tot4.z);
-        ex.w = block_exclusive_scan<kLowerThreads>(v.w, warp_tmp, tot4.w);
-        const uint4 c = carry4;
-        if (t < P.n_tiles) B.tile_off[t] = add4(ex, c);
-        __syncthreads();
-        if (threadIdx.x == 0) carry4 = add4(c, tot4);
-        __syncthreads();
+    total = all;
+    return add4(before, sub4(x, v));
+}
+
+__device__ __forceinline__ unsigned long long block_scan64(unsigned long long v, unsigned long long *warp_tot,
+                                                           unsigned long long &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
     }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kLowerWarps; w++) {
+        const unsigned long long t = warp_tot[w];
+        if (w < warp) before += t;
+        all += t;
+    }
+    __syncthreads();
+    total = all;
+    return before + x - v;
+}
+
+// One block.  An exclusive scan of the tile sums over the whole batch gives
+// each tile's offset (tiles of a circuit are contiguous, so a tile's offset
+// within its circuit is its offset less that of the circuit's first tile):
+// each thread sums a run of consecutive tiles, one block scan, then each
+// thread writes its run.  Block scans over the circuits then give the batch
+// offsets.
+__global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
+    const Params &P = *B.params;
+    __shared__ uint4 warp_tot4[kLowerWarps];
+    __shared__ unsigned long long warp_tot64[kLowerWarps];
+    {
+        const uint32_t n = P.n_tiles;
+        const uint32_t per = (n + kLowerThreads - 1) / kLowerThreads;
+        const uint32_t t0 = min(n, threadIdx.x * per), t1 = min(n, t0 + per);
+        uint4 acc = make_uint4(0, 0, 0, 0);
+        for (uint32_t t = t0; t < t1; t++) acc = add4(acc, B.tile_sums[t]);
+        uint4 tot;
+        uint4 run = block_scan4(acc, warp_tot4, tot);
+        for (uint32_t t = t0; t < t1; t++) {
+            B.tile_off[t] = run;
+            run = add4(run, B.tile_sums[t]);
+        }
+    }
+    __syncthreads();           // every tile offset written before the circuits read them
+    // running batch offsets (64-bit before the capacity checks, so no wrap)
+    unsigned long long carry_layer = 0, carry_meas = 0, carry_mech = 0, carry_qidx = 0;
     for (uint32_t base = 0; base < P.n_circuits; base += kLowerThreads) {
         const uint32_t b = base + threadIdx.x;
         uint32_t layers = 0, meas = 0, mech = 0, qblocks = 0;
@@ -125,48 +172,32 @@ __global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
             B.obs_count[b] = 0;
             B.circ_edges[b] = 0;
         }
-        uint32_t tot_l, tot_m, tot_x;
-        const uint32_t off_l = block_exclusive_scan<kLowerThreads>(layers, warp_tmp, tot_l);
-        const uint32_t off_m = block_exclusive_scan<kLowerThreads>(meas, warp_tmp, tot_m);
-        const uint32_t off_x = block_exclusive_scan<kLowerThreads>(mech, warp_tmp, tot_x);
-        // 64-bit scan of the index blocks: a circuit's own count fits 32 bits
-        __shared__ unsigned long long qscan[kLowerThreads], qtot;
-        qscan[threadIdx.x] = qblocks;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long r = 0;
-            for (int i = 0; i < kLowerThreads; i++) { const unsigned long long v = qscan[i]; qscan[i] = r; r += v; }
-            qtot = r;
-        }
-        __syncthreads();
+        uint4 tot;
+        const uint4 off = block_scan4(make_uint4(layers, meas, mech, 0u), warp_tot4, tot);
+        unsigned long long qtot;
+        const unsigned long long qoff = block_scan64(qblocks, warp_tot64, qtot);
         if (b < P.n_circuits) {
             CircuitDev &C = B.circ[b];
-            C.layer_base = carry_layer + off_l;
-            C.meas_base = carry_meas + off_m;
-            C.mech_base = carry_mech + off_x;
-            const unsigned long long qo = carry_qidx + qscan[threadIdx.x];
+            C.layer_base = (uint32_t)min(carry_layer + off.x, 0xFFFFFFFFull);
+            C.meas_base = (uint32_t)min(carry_meas + off.y, 0xFFFFFFFFull);
+            C.mech_base = (uint32_t)min(carry_mech + off.z, 0xFFFFFFFFull);
+            const unsigned long long qo = carry_qidx + qoff;
             C.qidx_off = (uint32_t)min(qo, 0xFFFFFFFFull);
             if (qo + qblocks > P.qidx_cap16) report(B.status, GP_ERR_CAPACITY, 9u, b, (uint32_t)min(qo + qblocks, 0xFFFFFFFFull));
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            // 64-bit guards against wrap before comparing with the bounds
-            const unsigned long long L = (unsigned long long)carry_layer + tot_l;
-            const unsigned long long Mm = (unsigned long long)carry_meas + tot_m;
-            const unsigned long long X = (unsigned long long)carry_mech + tot_x;
-            carry_layer = (uint32_t)min(L, 0xFFFFFFFFull);
-            carry_meas = (uint32_t)min(Mm, 0xFFFFFFFFull);
-            carry_mech = (uint32_t)min(X, 0xFFFFFFFFull);
-            carry_qidx += qtot;
-        }
-        __syncthreads();
+        carry_layer += tot.x;
+        carry_meas += tot.y;
+        carry_mech += tot.z;
+        carry_qidx += qtot;
     }
     if (threadIdx.x == 0) {
-        if (carry_layer > P.max_layer_slots) report(B.status, GP_ERR_CAPACITY, 1u, carry_layer, P.max_layer_slots);
+        if (carry_layer > P.max_layer_slots)
+            report(B.status, GP_ERR_CAPACITY, 1u, (uint32_t)min(carry_layer, 0xFFFFFFFFull), P.max_layer_slots);
         if (carry_meas > P.max_meas || carry_meas > kMaxMeasurements)
-            report(B.status, GP_ERR_CAPACITY, 2u, carry_meas, min(P.max_meas, kMaxMeasurements));
-        if (carry_mech > P.max_mech) report(B.status, GP_ERR_CAPACITY, 3u, carry_mech, P.max_mech);
-        B.status->n_mech = carry_mech;
+            report(B.status, GP_ERR_CAPACITY, 2u, (uint32_t)min(carry_meas, 0xFFFFFFFFull), min(P.max_meas, kMaxMeasurements));
+        if (carry_mech > P.max_mech)
+            report(B.status, GP_ERR_CAPACITY, 3u, (uint32_t)min(carry_mech, 0xFFFFFFFFull), P.max_mech);
+        B.status->n_mech = (uint32_t)min(carry_mech, 0xFFFFFFFFull);
     }
     // layer 0 starts at row 0; the sentinel after the last layer is n_ops
     __syncthreads();
