@@ -413,6 +413,7 @@ def serve_section(args) -> dict:
         lat, edges, bad = [], 0, 0
         i = outstanding = steps = 0
         step_ns, step_req, step_parts = [], [], []
+        client_max = 0                      # longest submit or drain call of the client
         while i < n_ev or outstanding:
             now = time.monotonic_ns()
             j = int(np.searchsorted(abs_ns, now, side="right"))
@@ -421,14 +422,17 @@ def serve_section(args) -> dict:
                                                  stop_when_full=True)
                 outstanding += got.size
                 i += got.size
+                client_max = max(client_max, time.monotonic_ns() - now)
             if outstanding:
                 t0 = time.monotonic_ns()
                 k = srv.step()
-                step_ns.append(time.monotonic_ns() - t0)
+                t1 = time.monotonic_ns()
+                step_ns.append(t1 - t0)
                 step_req.append(k)
                 step_parts.append(srv.last_timing())
                 steps += 1
                 d = srv.drain()
+                client_max = max(client_max, time.monotonic_ns() - t1)
                 outstanding -= d["ids"].size
                 lat.append((d["t_done_ns"].astype(np.int64) - d["t_arrival_ns"].astype(np.int64)))
                 edges += int(d["n_edges"].sum())
@@ -440,7 +444,9 @@ def serve_section(args) -> dict:
             "completed_per_s": n_ev / elapsed, "hyperedges_per_s": edges / elapsed, "steps": steps,
             "latency_us_p50": float(np.percentile(lat_us, 50)), "latency_us_p99": float(np.percentile(lat_us, 99)),
             "latency_us_max": float(lat_us.max()),
-            "step_ms_mean": float(np.mean(step_ns) / 1e6), "requests_per_step_mean": float(np.mean(step_req)),
+            "step_ms_mean": float(np.mean(step_ns) / 1e6), "step_ms_p99": float(np.percentile(step_ns, 99) / 1e6),
+            "step_ms_max": float(np.max(step_ns) / 1e6), "client_call_ms_max": client_max / 1e6,
+            "requests_per_step_mean": float(np.mean(step_req)),
             "step_us_mean": dict(zip(["build", "compile", "select", "hand_out", "lowering", "stage1", "group",
                                       "compact"],
                                      [float(x) for x in np.mean(np.array(step_parts), axis=0)])),

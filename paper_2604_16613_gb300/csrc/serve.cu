@@ -372,13 +372,22 @@ void free_host(gp_server *s) {
 }
 
 // a free step buffer holding `edges` hyperedges (plus `extra` detector
-// offsets) and `dets` detector ids, allocated when none fits
+// offsets) and `dets` detector ids, allocated when none fits.  A new buffer
+// is at least twice the largest one so far (up to the device outputs'
+// capacity), so a load that grows pins host memory a few times, not at every
+// new largest step.
 OutBuf *take_outbuf(gp_server *s, uint64_t edges, uint64_t extra, uint64_t dets) {
-    for (OutBuf *b : s->out_pool)
+    uint64_t big_e = 0, big_d = 0;
+    for (OutBuf *b : s->out_pool) {
         if (b->refs == 0 && b->edges_cap >= edges + extra && b->det_cap >= dets) return b;
+        big_e = std::max(big_e, b->edges_cap);
+        big_d = std::max(big_d, b->det_cap);
+    }
     OutBuf *b = new (std::nothrow) OutBuf();
     if (!b) return nullptr;
-    const uint64_t ne = std::max<uint64_t>(edges + extra, 1u << 16) * 5 / 4, nd = std::max<uint64_t>(dets, 1u << 18) * 5 / 4;
+    const uint64_t cap_e = s->out_edges_cap + extra, cap_d = std::max<uint64_t>(s->out_det_cap, 1);
+    const uint64_t ne = std::max({edges + extra, (uint64_t)1 << 16, std::min(2 * big_e, cap_e)});
+    const uint64_t nd = std::max({dets, (uint64_t)1 << 18, std::min(2 * big_d, cap_d)});
     if (cudaMallocHost(&b->doff, 4 * ne) != cudaSuccess || cudaMallocHost(&b->det, 4 * nd) != cudaSuccess ||
         cudaMallocHost(&b->prob, 4 * ne) != cudaSuccess || cudaMallocHost(&b->logodds, 4 * ne) != cudaSuccess ||
         cudaMallocHost(&b->obs, 8 * ne) != cudaSuccess) {
