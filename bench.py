@@ -673,7 +673,7 @@ def main():
                     help="timed compiles per correlation level in the levels section (0 skips it)")
     ap.add_argument("--serve-patches", type=int, default=64,
                     help="patches of the continuous-serving section (0 skips it)")
-    ap.add_argument("--serve-rates", default="250,500,750,1000",
+    ap.add_argument("--serve-rates", default="50,100,250,500,750,1000",
                     help="per-patch request rates (Hz) of the serving loads, comma-separated")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-k", type=int, default=4, help="cycles of one patch merged into a step")

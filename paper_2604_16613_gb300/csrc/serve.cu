@@ -210,6 +210,33 @@ __global__ void seal_write_kernel(Buffers B, const SealDesc *seal, SealOut out, 
     }
 }
 
+// n 4-byte words from device memory into pinned host memory (both ends
+// 16-byte aligned: whole 16-byte moves, then the tail)
+__device__ __forceinline__ void copy_words(uint32_t *dst, const uint32_t *src, uint64_t n, uint64_t t, uint64_t nt) {
+    const uint64_t n4 = n / 4;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (uint64_t i = t; i < n4; i += nt) d4[i] = s4[i];
+    for (uint64_t i = 4 * n4 + t; i < n; i += nt) dst[i] = src[i];
+}
+
+// after the last slot's pass: the step's hyperedges, per-request detector
+// offsets and detector ids into the pinned step buffer, sized by the totals
+// on the device (tot = edges and detector ids over all slots)
+// (the counts are clamped to the buffer's capacity; the host checks them)
+__global__ void seal_copy_kernel(SealOut dev, SealOut host, const uint2 *tot_ptr, uint32_t n_offs_extra,
+                                 uint64_t edges_cap, uint64_t det_cap) {
+    const uint2 tot = *tot_ptr;
+    const uint64_t ne = min((uint64_t)tot.x, edges_cap), no = min((uint64_t)tot.x + n_offs_extra, edges_cap);
+    const uint64_t nd = min((uint64_t)tot.y, det_cap);
+    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    copy_words(host.doff, dev.doff, no, t, nt);
+    copy_words(host.det, dev.det, nd, t, nt);
+    copy_words(reinterpret_cast<uint32_t *>(host.prob), reinterpret_cast<const uint32_t *>(dev.prob), ne, t, nt);
+    copy_words(reinterpret_cast<uint32_t *>(host.logodds), reinterpret_cast<const uint32_t *>(dev.logodds), ne, t, nt);
+    copy_words(reinterpret_cast<uint32_t *>(host.obs), reinterpret_cast<const uint32_t *>(dev.obs), 2 * ne, t, nt);
+}
+
 uint32_t n_comp_host(uint32_t kind, uint32_t level) {
     switch (kind) {
     case K_XERR: case K_ZERR: return 1;
@@ -373,21 +400,17 @@ void free_host(gp_server *s) {
 
 // a free step buffer holding `edges` hyperedges (plus `extra` detector
 // offsets) and `dets` detector ids, allocated when none fits.  A new buffer
-// is at least twice the largest one so far (up to the device outputs'
-// capacity), so a load that grows pins host memory a few times, not at every
-// new largest step.
+// has twice the room asked for (within the device outputs' capacity), so a
+// load that grows pins host memory a few times, not at every new largest
+// step.
 OutBuf *take_outbuf(gp_server *s, uint64_t edges, uint64_t extra, uint64_t dets) {
-    uint64_t big_e = 0, big_d = 0;
-    for (OutBuf *b : s->out_pool) {
+    for (OutBuf *b : s->out_pool)
         if (b->refs == 0 && b->edges_cap >= edges + extra && b->det_cap >= dets) return b;
-        big_e = std::max(big_e, b->edges_cap);
-        big_d = std::max(big_d, b->det_cap);
-    }
     OutBuf *b = new (std::nothrow) OutBuf();
     if (!b) return nullptr;
     const uint64_t cap_e = s->out_edges_cap + extra, cap_d = std::max<uint64_t>(s->out_det_cap, 1);
-    const uint64_t ne = std::max({edges + extra, (uint64_t)1 << 16, std::min(2 * big_e, cap_e)});
-    const uint64_t nd = std::max({dets, (uint64_t)1 << 18, std::min(2 * big_d, cap_d)});
+    const uint64_t ne = std::max(edges + extra, std::min(std::max<uint64_t>(2 * (edges + extra), 1u << 16), cap_e));
+    const uint64_t nd = std::max(dets, std::min(std::max<uint64_t>(2 * dets, 1u << 18), cap_d));
     if (cudaMallocHost(&b->doff, 4 * ne) != cudaSuccess || cudaMallocHost(&b->det, 4 * nd) != cudaSuccess ||
         cudaMallocHost(&b->prob, 4 * ne) != cudaSuccess || cudaMallocHost(&b->logodds, 4 * ne) != cudaSuccess ||
         cudaMallocHost(&b->obs, 8 * ne) != cudaSuccess) {
@@ -970,33 +993,32 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         const uint32_t grid = 4u * s->n_sms;
         seal_horizon_kernel<<<n_win, 256, 0, st>>>(B, s->d_seal, s->d_rec_tab, c.max_horizon, n_win, s->d_horizon);
         win_edges_kernel<<<1, 32, 0, st>>>(B, n_win, s->d_win_e0);
-        uint32_t launches = 0;
-        for (uint32_t r = 0; r < n_pass; r++) {
-            seal_flags_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->d_cyc_tab, s->W + 1u, r);
-            launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, st, &launches);
-            slot_starts_kernel<<<1, 256, 0, st>>>(B, n_win, s->d_win_e0, r, s->d_starts, s->out.doff);
-            seal_write_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->out, s->d_starts + (size_t)r * rs, r, n_win);
-        }
-        SV_CUDA(cudaGetLastError());
-        SV_CUDA(cudaMemcpyAsync(s->h_starts, s->d_starts, (size_t)n_pass * rs * sizeof(uint2), cudaMemcpyDeviceToHost, st));
-        SV_CUDA(cudaMemcpyAsync(s->h_horizon, s->d_horizon, n_win * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        SV_CUDA(cudaStreamSynchronize(st));
-        const uint2 tot = s->h_starts[(size_t)(n_pass - 1u) * rs + n_win];
-        const uint64_t n_offs = tot.x + (uint64_t)n_pass * n_win;
-        ob = take_outbuf(s, tot.x, (uint64_t)n_pass * n_win, tot.y);
+        // the step buffer is taken before the passes, for the batch's whole
+        // output (the sealed part is at most that), so one kernel can fill
+        // it and one synchronisation ends the step
+        ob = take_outbuf(s, view.n_edges, (uint64_t)n_pass * n_win, view.n_det_entries);
         if (!ob) cst = sfail(GP_ERR_CUDA, "cudaMallocHost of a result buffer failed");
         if (cst == GP_OK) {
-            SV_CUDA(cudaMemcpyAsync(ob->doff, s->out.doff, n_offs * 4ull, cudaMemcpyDeviceToHost, st));
-            if (tot.y) SV_CUDA(cudaMemcpyAsync(ob->det, s->out.det, tot.y * 4ull, cudaMemcpyDeviceToHost, st));
-            if (tot.x) {
-                SV_CUDA(cudaMemcpyAsync(ob->prob, s->out.prob, tot.x * 4ull, cudaMemcpyDeviceToHost, st));
-                SV_CUDA(cudaMemcpyAsync(ob->logodds, s->out.logodds, tot.x * 4ull, cudaMemcpyDeviceToHost, st));
-                SV_CUDA(cudaMemcpyAsync(ob->obs, s->out.obs, tot.x * 8ull, cudaMemcpyDeviceToHost, st));
+            uint32_t launches = 0;
+            for (uint32_t r = 0; r < n_pass; r++) {
+                seal_flags_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->d_cyc_tab, s->W + 1u, r);
+                launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, st, &launches);
+                slot_starts_kernel<<<1, 256, 0, st>>>(B, n_win, s->d_win_e0, r, s->d_starts, s->out.doff);
+                seal_write_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->out, s->d_starts + (size_t)r * rs, r, n_win);
             }
+            const SealOut host{ob->doff, ob->det, ob->prob, ob->logodds, ob->obs};
+            seal_copy_kernel<<<grid, 256, 0, st>>>(s->out, host, s->d_starts + (size_t)(n_pass - 1u) * rs + n_win,
+                                                    n_pass * n_win, ob->edges_cap, ob->det_cap);
+            SV_CUDA(cudaGetLastError());
+            SV_CUDA(cudaMemcpyAsync(s->h_starts, s->d_starts, (size_t)n_pass * rs * sizeof(uint2), cudaMemcpyDeviceToHost, st));
+            SV_CUDA(cudaMemcpyAsync(s->h_horizon, s->d_horizon, n_win * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             SV_CUDA(cudaStreamSynchronize(st));
+            const uint2 tot = s->h_starts[(size_t)(n_pass - 1u) * rs + n_win];
+            if (tot.x + (uint64_t)n_pass * n_win > ob->edges_cap || tot.y > ob->det_cap)
+                cst = sfail(GP_ERR_CAPACITY, "sealed output larger than the step's whole output");
+            for (uint32_t w = 0; w < n_win; w++)
+                if (s->h_horizon[w]) win_status[w] = GP_ERR_HORIZON;
         }
-        for (uint32_t w = 0; w < n_win; w++)
-            if (s->h_horizon[w]) win_status[w] = GP_ERR_HORIZON;
     }
     const uint64_t t_selected = now_ns();
     // every request's hyperedges are one slice of the step buffer
