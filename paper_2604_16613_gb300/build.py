@@ -1,6 +1,6 @@
 """Build the sm_103a shared library ``_lib/libgpdem.so`` in-tree with nvcc.
 
-The four translation units compile in parallel (one ``-gencode`` for
+The six translation units compile in parallel (one ``-gencode`` for
 sm_103a); the objects are then linked into a shared library with the CUDA
 runtime linked statically.  Rebuilds only when a source or header is newer
 than the library.
