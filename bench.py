@@ -408,6 +408,7 @@ def serve_section(args) -> dict:
         ev_t, ev_p = ev_t[order], ev_p[order]
         n_ev = ev_t.size
         start = time.monotonic_ns() + 2_000_000
+        deadline = start + int((10 * T + 30) * 1e9)     # a stuck server fails the load, never hangs the bench
         abs_ns = (start + ev_t * 1e9).astype(np.uint64)
         ev_patch, ev_cycle = pids[ev_p], mid[ev_p]
         lat, edges, bad = [], 0, 0
@@ -425,6 +426,8 @@ def serve_section(args) -> dict:
                 client_max = max(client_max, time.monotonic_ns() - now)
             if outstanding:
                 t0 = time.monotonic_ns()
+                if t0 > deadline:
+                    raise RuntimeError(f"serve load {rate:g} Hz: the server stopped completing requests")
                 k = srv.step()
                 t1 = time.monotonic_ns()
                 step_ns.append(t1 - t0)

@@ -239,7 +239,10 @@ class Server:
                 except native.GpError as e:
                     if e.code != native.GP_ERR_CAPACITY or pending == 0:
                         raise
-                    pending -= self.step(level)
+                    done = self.step(level)
+                    if done == 0:
+                        raise RuntimeError("server made no progress")
+                    pending -= done
                     for r in self.completed():
                         out[owner[r]].update(self.edges(self.result(r)))
                         self.release(r)
