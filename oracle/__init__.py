@@ -40,36 +40,41 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def load_library(path: str):
+    """Load an oracle shared library and declare its entry points (the built
+    oracle, or a copy that a test compiled from a modified source)."""
+    lib = ctypes.CDLL(path)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    f64p = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    lib.orc_analyze.argtypes = [u32p, ctypes.c_uint64, u32p, ctypes.c_uint64, ctypes.c_uint32,
+                                f64p, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(vp),
+                                ctypes.c_char_p, ctypes.c_int]
+    lib.orc_analyze.restype = ctypes.c_int
+    lib.orc_free.argtypes = [vp]
+    for name, rt in [("orc_n_detectors", ctypes.c_uint32), ("orc_n_observables", ctypes.c_uint32),
+                     ("orc_n_mechanisms", ctypes.c_uint64), ("orc_n_classes", ctypes.c_uint64)]:
+        getattr(lib, name).argtypes = [vp]
+        getattr(lib, name).restype = rt
+    for name, rt in [("orc_mech_op", u64p), ("orc_mech_comp", u32p), ("orc_mech_loc", u32p),
+                     ("orc_mech_q", f64p), ("orc_mech_mask_off", u64p), ("orc_mech_mask", u32p),
+                     ("orc_mech_class", u64p), ("orc_class_mask_off", u64p),
+                     ("orc_class_mask", u32p), ("orc_class_p", f64p), ("orc_class_p_iter", f64p),
+                     ("orc_class_w", f64p), ("orc_class_size", u64p)]:
+        getattr(lib, name).argtypes = [vp]
+        getattr(lib, name).restype = rt
+    lib.orc_gradient.argtypes = [vp, f64p, f64p, f64p]
+    lib.orc_gradient.restype = None
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        u32p = ctypes.POINTER(ctypes.c_uint32)
-        u64p = ctypes.POINTER(ctypes.c_uint64)
-        f64p = ctypes.POINTER(ctypes.c_double)
-        vp = ctypes.c_void_p
-        lib.orc_analyze.argtypes = [u32p, ctypes.c_uint64, u32p, ctypes.c_uint64, ctypes.c_uint32,
-                                    f64p, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(vp),
-                                    ctypes.c_char_p, ctypes.c_int]
-        lib.orc_analyze.restype = ctypes.c_int
-        lib.orc_free.argtypes = [vp]
-        for name, rt in [("orc_n_detectors", ctypes.c_uint32), ("orc_n_observables", ctypes.c_uint32),
-                         ("orc_n_mechanisms", ctypes.c_uint64), ("orc_n_classes", ctypes.c_uint64)]:
-            getattr(lib, name).argtypes = [vp]
-            getattr(lib, name).restype = rt
-        for name, rt in [("orc_mech_op", u64p), ("orc_mech_comp", u32p), ("orc_mech_loc", u32p),
-                         ("orc_mech_q", f64p), ("orc_mech_mask_off", u64p), ("orc_mech_mask", u32p),
-                         ("orc_mech_class", u64p), ("orc_class_mask_off", u64p),
-                         ("orc_class_mask", u32p), ("orc_class_p", f64p), ("orc_class_p_iter", f64p),
-                         ("orc_class_w", f64p), ("orc_class_size", u64p)]:
-            getattr(lib, name).argtypes = [vp]
-            getattr(lib, name).restype = rt
-        lib.orc_gradient.argtypes = [vp, f64p, f64p, f64p]
-        lib.orc_gradient.restype = None
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = load_library(build())
+        return _lib
 
 
 class OracleError(RuntimeError):
@@ -143,7 +148,7 @@ class OracleDem:
 
     def gradient(self, gP: np.ndarray, gW: np.ndarray, n_locations: int) -> np.ndarray:
         """d/dp of sum_c gP[c] P_c + gW[c] w_c (classes in this object's order)."""
-        lib = _load()
+        lib = self._handle.lib
         gP = np.ascontiguousarray(gP, dtype=np.float64)
         gW = np.ascontiguousarray(gW, dtype=np.float64)
         g = np.zeros(max(n_locations, 1), dtype=np.float64)
@@ -165,9 +170,10 @@ class _Handle:
 
 
 def analyze(ops: np.ndarray, recs: np.ndarray, n_qubits: int, noise: np.ndarray,
-            level="L2") -> OracleDem:
-    """Run the oracle on a flat circuit (see circuits.py for the format)."""
-    lib = _load()
+            level="L2", lib=None) -> OracleDem:
+    """Run the oracle on a flat circuit (see circuits.py for the format);
+    `lib` selects another loaded copy (default: the built oracle)."""
+    lib = lib or _load()
     ops = np.ascontiguousarray(ops, dtype=np.uint32).reshape(-1, 4)
     recs = np.ascontiguousarray(recs, dtype=np.uint32).reshape(-1)
     noise = np.ascontiguousarray(noise, dtype=np.float64).reshape(-1)
@@ -206,6 +212,6 @@ def analyze(ops: np.ndarray, recs: np.ndarray, n_qubits: int, noise: np.ndarray,
     return dem
 
 
-def analyze_circuit(circuit, noise=None, level="L2") -> OracleDem:
+def analyze_circuit(circuit, noise=None, level="L2", lib=None) -> OracleDem:
     noise = circuit.default_noise if noise is None else noise
-    return analyze(circuit.ops, circuit.recs, circuit.n_qubits, noise, level)
+    return analyze(circuit.ops, circuit.recs, circuit.n_qubits, noise, level, lib)
