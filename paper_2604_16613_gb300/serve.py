@@ -12,9 +12,10 @@ import ctypes
 import numpy as np
 
 from . import native
-from .circuits import NOISE_KINDS, TICK, MEASURE_KINDS
+from .circuits import DEPOLARIZE1, DEPOLARIZE2, MEASURE_KINDS, TICK, X_ERROR, Z_ERROR
 
-_COMP = {32: (1, 1, 1), 33: (1, 1, 1), 34: (2, 3, 3), 35: (6, 10, 15)}
+# components per noise channel at L0, L1, L2
+_COMP = {X_ERROR: (1, 1, 1), Z_ERROR: (1, 1, 1), DEPOLARIZE1: (2, 3, 3), DEPOLARIZE2: (6, 10, 15)}
 
 
 def cycle_sizes(block: dict) -> dict:
