@@ -161,6 +161,29 @@ def peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+def host_cpu() -> dict:
+    """The host's CPU model and logical core count (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "arch": platform.machine()}
+
+
 def cpu_baseline(circ, noise, budget_s: float = 12.0, max_runs: int = 40) -> dict:
     """The CPU oracle as it stands, one core, on the same workload."""
     import oracle
@@ -174,9 +197,10 @@ def cpu_baseline(circ, noise, budget_s: float = 12.0, max_runs: int = 40) -> dic
         el = time.perf_counter() - t0
         if el >= budget_s or runs >= max_runs:
             break
+    hc = host_cpu()
     return {"value": nm / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{runs} full oracle compiles of the d=25 workload ({el:.1f} s, 1 thread, "
-                      f"{platform.machine()} host)"}
+                      f"{platform.machine()} host)", **hc}
 
 
 def _oracle_branch(args):
@@ -205,7 +229,8 @@ def cpu_batch_baseline(branches, budget_s: float = 10.0) -> dict:
                 break
     el = time.perf_counter() - t0
     return {"value": n_mech / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {len(work)} branches in {el:.1f} s (pool start included), one per process"}
+            "sample": f"{done} of {len(work)} branches in {el:.1f} s (pool start included), one per process",
+            **host_cpu()}
 
 
 def batch_section(args, world: int) -> dict:
@@ -244,6 +269,31 @@ def batch_section(args, world: int) -> dict:
         reps.append(e0.elapsed_time(e1))
     total_cycles = int(cyc.sum())
     batched_pc = np.array(reps) * 1e3 / total_cycles
+    # when does each branch's model become available?  In one batch every
+    # branch is ready when the batch finishes.  Sub-batches trade throughput
+    # for latency: branch i of sub-batch k is ready when sub-batches 0..k have
+    # run back to back (times from the start of the first).
+    sub = {}
+    loc0 = np.cumsum([0] + [b.n_locations for b in branches])
+    for size in (64, 16):
+        ready = []
+        for _ in range(max(2, args.batch_reps // 2)):
+            t_run, ready_run = 0.0, []
+            for k in range(0, n, size):
+                part = dcs[k:k + size]
+                nzk = nz[loc0[k]:loc0[min(n, k + size)]]
+                e0.record(stream)
+                drv.compile(part, nzk)
+                e1.record(stream)
+                e1.synchronize()
+                t_run += e0.elapsed_time(e1)
+                ready_run += [t_run] * len(part)
+            ready.append(ready_run)
+        ready = np.array(ready)
+        sub[str(size)] = {"branch_ready_ms_p50": float(np.percentile(ready, 50)),
+                          "branch_ready_ms_p99": float(np.percentile(ready, 99)),
+                          "ms_all_branches_p50": float(np.median(ready[:, -1])),
+                          "mechanisms_per_s": n_mech / (np.median(ready[:, -1]) / 1e3)}
     del drv, dem
     torch.cuda.empty_cache()
     # plain: one branch at a time
@@ -269,13 +319,114 @@ def batch_section(args, world: int) -> dict:
                     "per_cycle_us_p50": float(np.percentile(batched_pc, 50)),
                     "per_cycle_us_p99": float(np.percentile(batched_pc, 99)),
                     "mechanisms_per_s": n_mech / (np.median(reps) / 1e3),
+                    "branch_ready_ms_p50": float(np.percentile(reps, 50)),
+                    "branch_ready_ms_p99": float(np.percentile(reps, 99)),
                     "tuning": {k: v for k, v in tune.items() if k != "ms"}},
+        "sub_batches": sub,
+        "latency_note": "per_cycle_us is the batch time divided by the cycles of all branches (amortised "
+                        "throughput); branch_ready_ms is when a branch's model is available: in one batch, "
+                        "the whole batch's time for every branch",
         "cpu_all_cores": cpu,
         "plain": {"ms_per_branch_p50": float(np.median(plain_ms)),
                   "per_cycle_us_p50": float(np.percentile(plain_pc, 50)),
                   "per_cycle_us_p99": float(np.percentile(plain_pc, 99)),
                   "mechanisms_per_s": n_mech / (sum(plain_ms) / 1e3)},
     }
+
+
+def sweep_section(args) -> list:
+    """Plain compiles of the rotated surface code (d rounds, log-uniform
+    p in [1e-4, 3e-3], seed 2, L2) over d = 3 ... 25: device time per compile
+    (CUDA events, L2 flushed before each, ``--sweep-steps`` compiles after
+    warm-up), mechanisms/s, per-cycle p50/p99 and the pipeline's fraction of
+    the measured HBM bandwidth (the same algorithmic-byte formula as the
+    headline)."""
+    import torch
+    from paper_2604_16613_gb300 import circuits as C
+    from paper_2604_16613_gb300.dem import DeviceCircuit, Driver
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hbm_peak, _ = peaks()
+    rows = []
+    for d in [int(x) for x in args.sweep_d.split(",") if x]:
+        circ = C.rotated_surface_code_memory(d, d, C.NoiseModel.uniform(1e-3))
+        noise = torch.tensor(C.log_uniform_noise(circ.n_locations, seed=2).astype(np.float32), device="cuda")
+        drv = Driver.for_circuits([circ])
+        dc = DeviceCircuit(circ)
+        for _ in range(5):
+            dem = drv.compile(dc, noise)
+        host = dem.to_host()
+        mclass = dem.mech_class.cpu().numpy()
+        n_mech = int((mclass >= 0).sum())
+        ms = []
+        for _ in range(args.sweep_steps):
+            flush.fill_(1)
+            e0.record(stream)
+            drv.compile(dc, noise)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ms = np.array(ms)
+        words = mask_word_count(host, mclass)
+        b_in = 16 * circ.n_ops + 4 * int(circ.recs.size) + 4 * circ.n_locations
+        b_alg = b_in + n_mech * 32 + 2 * 12 * words + dem.n_edges * 16 + 4 * host["det_idx"].size
+        t = float(np.median(ms))
+        rows.append({"d": d, "rounds": d, "qubits": circ.n_qubits, "detectors": circ.n_detectors,
+                     "mechanisms": n_mech, "hyperedges": dem.n_edges, "ms_per_compile_p50": t,
+                     "mechanisms_per_s": n_mech / (t * 1e-3),
+                     "per_cycle_us_p50": float(np.percentile(ms, 50) * 1e3 / d),
+                     "per_cycle_us_p99": float(np.percentile(ms, 99) * 1e3 / d),
+                     "pipeline_alg_bytes": int(b_alg),
+                     "pipeline_frac": b_alg / (t * 1e-3) / 1e9 / hbm_peak})
+        del drv, dem
+    del flush
+    torch.cuda.empty_cache()
+    return rows
+
+
+def bb_section(args) -> dict:
+    """Bivariate bicycle [[144,12,12]] memory, 12 rounds, p = 1e-3, L2:
+    forward compile and adjoint (the gradient of a loss linear in every
+    hyperedge's P and w with respect to every noise location), device time
+    of each (CUDA events, L2 flushed before each step)."""
+    import torch
+    from paper_2604_16613_gb300 import circuits as C
+    from paper_2604_16613_gb300.dem import DeviceCircuit, Driver
+    circ = C.bb_memory(12, C.NoiseModel.uniform(1e-3), seed=3)
+    noise = torch.tensor(np.asarray(circ.default_noise, np.float32), device="cuda")
+    drv = Driver.for_circuits([circ])
+    dc = DeviceCircuit(circ)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(5):
+        dem = drv.compile(dc, noise)
+    n_mech = int((dem.mech_class >= 0).sum().item())
+    rng = np.random.default_rng(13)
+    gp = torch.tensor(rng.normal(size=dem.n_edges), dtype=torch.float32, device="cuda")
+    gw = torch.tensor(rng.normal(size=dem.n_edges) * 1e-3, dtype=torch.float32, device="cuda")
+    drv.backward(gp, gw)
+    fwd, bwd = [], []
+    for _ in range(args.bb_steps):
+        flush.fill_(1)
+        ev[0].record(stream)
+        drv.compile(dc, noise)
+        ev[1].record(stream)
+        drv.backward(gp, gw)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        fwd.append(ev[0].elapsed_time(ev[1]))
+        bwd.append(ev[1].elapsed_time(ev[2]))
+    del flush
+    torch.cuda.empty_cache()
+    return {"workload": "bivariate bicycle [[144,12,12]] memory, 12 rounds, p=1e-3, L2, forward + adjoint",
+            "qubits": circ.n_qubits, "detectors": circ.n_detectors, "mechanisms": n_mech,
+            "hyperedges": dem.n_edges, "forward_ms_p50": float(np.median(fwd)),
+            "forward_ms_p99": float(np.percentile(fwd, 99)), "adjoint_ms_p50": float(np.median(bwd)),
+            "adjoint_ms_p99": float(np.percentile(bwd, 99)),
+            "forward_mechanisms_per_s": n_mech / (np.median(fwd) * 1e-3),
+            "per_cycle_us_p50": float(np.median(np.array(fwd) + np.array(bwd)) * 1e3 / 12)}
 
 
 def levels_section(args) -> list:
@@ -498,7 +649,8 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
         "per_cycle_us": {"p50": float(np.percentile(per_cycle, 50)), "p99": float(np.percentile(per_cycle, 99))},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full oracle compiles of the d=25 workload, 1 thread"},
+                         "sample": f"{args.steps} full oracle compiles of the d=25 workload, 1 thread",
+                         **host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -643,6 +795,10 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline and world == 1:      # the oracle's baseline: N = 1 only
             result["cpu_baseline"] = cpu_baseline(circ, noise)
+        if args.sweep_steps > 0:
+            result["sweep"] = sweep_section(args)
+        if args.bb_steps > 0:
+            result["bb"] = bb_section(args)
         if args.levels_steps > 0:
             result["levels"] = levels_section(args)
         if args.calib_steps > 0:
@@ -672,6 +828,11 @@ def main():
     ap.add_argument("--batch-reps", type=int, default=10)
     ap.add_argument("--calib-steps", type=int, default=100,
                     help="loss evaluations of the noise-recalibration fit (0 skips it)")
+    ap.add_argument("--sweep-steps", type=int, default=1000,
+                    help="timed compiles per distance of the d-sweep (0 skips it)")
+    ap.add_argument("--sweep-d", default="3,5,7,9,11,15,21,25")
+    ap.add_argument("--bb-steps", type=int, default=200,
+                    help="timed forward + adjoint steps of the [[144,12,12]] section (0 skips it)")
     ap.add_argument("--levels-steps", type=int, default=50,
                     help="timed compiles per correlation level in the levels section (0 skips it)")
     ap.add_argument("--serve-patches", type=int, default=64,

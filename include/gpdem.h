@@ -154,7 +154,10 @@ typedef struct gp_driver gp_driver;
  * gp_driver_create carves its buffers from). */
 gp_status gp_workspace_size(const gp_bounds *bounds, uint64_t *bytes);
 
-/* Create a driver on the current CUDA device.  d_workspace: device memory of
+/* Create a driver on the current CUDA device (Sec. 3.4, buffer reuse: the
+ * paper builds its driver once from a maximal circuit, then compiles every
+ * realised circuit within it into the same buffers; here the maximal circuit
+ * is given by its bounds).  d_workspace: device memory of
  * at least gp_workspace_size bytes, 256-byte aligned, owned by the caller and
  * kept alive until gp_driver_destroy; NULL lets the driver allocate (and
  * free) its own.  Pinned host staging buffers are allocated here, never
@@ -179,7 +182,11 @@ gp_status gp_compile_batch(gp_driver *drv, const gp_circuit *circuits,
                            int inputs_on_device, gp_level level, void *stream,
                            gp_dem_view *out);
 
-/* gp_compile_batch with one circuit. */
+/* gp_compile_batch with one circuit: the paper's just-in-time compile of one
+ * realised circuit into its decoding hypergraph (Secs. 3.1-3.2; its usage
+ * listing, lst:basic-example, builds the driver once and then compiles each
+ * realised circuit with its noise vector).  Same arguments, ownership and
+ * errors as gp_compile_batch with n_circuits = 1. */
 gp_status gp_compile(gp_driver *drv, const gp_circuit *circuit,
                      const float *noise, int inputs_on_device, gp_level level,
                      void *stream, gp_dem_view *out);
@@ -195,7 +202,11 @@ gp_status gp_compile(gp_driver *drv, const gp_circuit *circuit,
 gp_status gp_backward(gp_driver *drv, const float *g_prob,
                       const float *g_logodds, float *g_noise, void *stream);
 
-/* View of the last successful compile. */
+/* View of the last successful compile: the detector error model of
+ * Sec. 2.1.4 (hyperedges as detector lists with observable masks,
+ * probabilities and weights), as device arrays owned by the driver and
+ * valid until its next compile.  GP_ERR_INVALID when the driver holds no
+ * successful compile. */
 gp_status gp_result_view(const gp_driver *drv, gp_dem_view *out);
 
 /* Host copy of the last successful compile's hyperedges into caller-owned
@@ -227,8 +238,33 @@ gp_status gp_last_timing(const gp_driver *drv, float times_us[4]);
 /* Number of kernel launches issued by the last compile / backward call. */
 uint32_t gp_last_launch_count(const gp_driver *drv);
 
-/* Thread-local message describing the last failure on this thread. */
+/* Thread-local message describing the last failure on this thread (not in
+ * the paper: the error channel of this C interface).  The pointer stays
+ * valid until the next failing call on the same thread. */
 const char *gp_last_error(void);
+
+/* Test knobs (not in the paper).  They exist so that the test-suite can
+ * reach code paths that real inputs almost never take:
+ *   weak_hash     0: the grouping hash as designed.  1: every mask gets the
+ *                 same 32-bit tag, so every probe that meets another class's
+ *                 slot must tell the masks apart by comparing them word by
+ *                 word.  2: every mask also gets the same first slot (one
+ *                 probe chain for all classes; small circuits only).
+ *                 Grouping stays exact in every mode; only speed changes.
+ *   wait_limit    polls before a bounded device wait gives up and the
+ *                 compile returns GP_ERR_TIMEOUT (0: 2^22, the default).
+ *   stall_windows 1: stage 1 stages no layer window, so the first wait of
+ *                 every walk can only run out (the timeout path, without a
+ *                 hang and without a copy in flight).
+ * The knobs apply to the driver's later compiles until changed; a driver
+ * starts with all of them 0. */
+typedef struct {
+    uint32_t weak_hash;
+    uint32_t wait_limit;
+    uint32_t stall_windows;
+    uint32_t reserved;            /* must be 0 */
+} gp_debug;
+gp_status gp_set_debug(gp_driver *drv, const gp_debug *dbg);
 
 /* Class probabilities for callers that may not allocate device memory.
  *
@@ -241,8 +277,13 @@ const char *gp_last_error(void);
  * of n_mech mechanisms (mech_class[i] in [0, n_classes), anything else is
  * skipped) and each mechanism's component probability q[i] in [0, 1/2], it
  * writes prob[c] = (1 - prod_{i in c} (1 - 2 q_i)) / 2 and, if logodds is not
- * NULL, logodds[c] = log((1 - prob[c]) / prob[c]) for every class c, exactly
- * as gp_compile combines the members of a class.  All pointers are device
+ * NULL, logodds[c] = log((1 - prob[c]) / prob[c]) for every class c: the
+ * same combination as gp_compile's (Eq. pmerge), equal to it within the
+ * library's FP32 tolerance but not bit for bit (gp_compile starts from the
+ * channel parameter p, this call from the component probability q).
+ * Members with q = 0 contribute nothing, q >= 1/2 saturates the class at
+ * prob = 1/2 (logodds 0), and a class with no member of positive q gets
+ * prob = 0 and logodds = +infinity.  All pointers are device
  * pointers owned by the caller; work is queued on `stream` and the call
  * returns without waiting for it.
  *
@@ -250,7 +291,9 @@ const char *gp_last_error(void);
  * GPU that loads the library keeps until the process exits.  More than
  * 524,288 classes gives GP_ERR_CAPACITY.  The first call on a device looks up
  * that array's address on the current device and remembers it; make that
- * first call before any stream capture.  Each call zeroes the part of the
+ * first call before any stream capture.  A device reset (cudaDeviceReset)
+ * after that first call is not supported: the remembered address would be
+ * stale.  Each call zeroes the part of the
  * array it uses before using it, but all calls share the one array: calls
  * whose work overlaps on the GPU (different streams or host threads) race and
  * must be serialised by the caller. */

@@ -187,8 +187,9 @@ struct gp_driver {
     bool exec_timing = false;
     gp_tuning exec_tuning{0, 0, 0, 0};
     uint32_t graph_kernels = 0;
-    // tuning / instrumentation
+    // tuning / instrumentation / test knobs
     gp_tuning tuning{512, 0, 256, 8};
+    gp_debug debug{0, 0, 0, 0};
     bool timing = false;
     cudaEvent_t ev[5] = {};
     float times[4] = {0, 0, 0, 0};
@@ -452,6 +453,14 @@ gp_status gp_get_tuning(const gp_driver *d, gp_tuning *t) {
     return GP_OK;
 }
 
+gp_status gp_set_debug(gp_driver *d, const gp_debug *dbg) {
+    if (!d || !dbg) return fail(GP_ERR_INVALID, "null argument");
+    if (dbg->weak_hash > 2u || dbg->stall_windows > 1u || dbg->reserved != 0u)
+        return fail(GP_ERR_INVALID, "debug: weak_hash 0..2, stall_windows 0 or 1, reserved 0");
+    d->debug = *dbg;
+    return GP_OK;
+}
+
 gp_status gp_enable_timing(gp_driver *d, int enable) {
     if (!d) return fail(GP_ERR_INVALID, "null argument");
     d->timing = enable != 0;
@@ -672,6 +681,9 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     P->rec_cap = (uint32_t)L.rec_cap;
     P->max_qubits = bd.max_qubits;
     P->qidx_cap16 = L.qidx_cap16;
+    P->weak_hash = d->debug.weak_hash;
+    P->wait_limit = d->debug.wait_limit ? d->debug.wait_limit : kWaitPolls;
+    P->stall_windows = d->debug.stall_windows;
     // ---- pipeline: one graph launch ----------------------------------------------
     {
         const gp_status gs = ensure_graph(d);

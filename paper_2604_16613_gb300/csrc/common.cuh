@@ -69,6 +69,11 @@ struct Params {
     uint32_t rec_cap;           // capacity of the record pool
     uint32_t max_qubits;
     uint64_t qidx_cap16;        // capacity of the layer index arena (16-byte units)
+    // test knobs (gp_debug)
+    uint32_t weak_hash;         // 0 full hash, 1 constant tag, 2 constant hash
+    uint32_t wait_limit;        // polls of a bounded wait (never 0 on the device)
+    uint32_t stall_windows;     // 1: stage 1 stages no window
+    uint32_t pad_dbg;
 };
 
 // device status block (read back by the host after every compile)
@@ -283,9 +288,11 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
         : "memory");
     return ok != 0u;
 }
-// bounded wait: false if the phase did not complete within the limit
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); it++)
+// bounded wait: false if the phase did not complete within `limit` polls
+constexpr uint32_t kWaitPolls = 1u << 22;   // default limit of a bounded wait
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity,
+                                                  uint32_t limit = kWaitPolls) {
+    for (uint32_t it = 0; it < limit; it++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -380,6 +387,12 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+// the grouping hash under the weak-hash test modes: 1 keeps the table
+// position (low half) but gives every mask the same tag (high half), 2 gives
+// every mask the same hash
+__device__ __forceinline__ unsigned long long weaken_hash(unsigned long long h, uint32_t mode) {
+    return mode == 0u ? h : (mode == 1u ? (h & 0xFFFFFFFFull) : 0ull);
 }
 
 // ---------------------------------------------------------------------------

@@ -13,11 +13,13 @@
 //  - at most kNoAllocMaxClasses classes per call (8 MiB of accumulators);
 //  - the first call on a device looks up the array's device address for that
 //    device (cudaGetSymbolAddress) and caches it; make that first call before
-//    any stream capture;
+//    any stream capture, and do not reset the device after it (the cached
+//    address would be stale);
 //  - every call clears the accumulators it uses before adding into them, and
 //    all calls share the one array, so calls that overlap on the GPU (on
 //    different streams, or from different host threads) race.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -34,8 +36,10 @@ constexpr int kNoAllocMaxDevices = 64;
 // two 64-bit words (low, high) of a 128-bit fixed-point sum per class
 static __device__ __align__(256) unsigned long long g_noalloc_acc[2ull * kNoAllocMaxClasses];
 
+// per device, the array's address once looked up; read with one acquire
+// load, so calls after the first take no lock
 std::mutex g_noalloc_mu;
-unsigned long long *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::atomic<unsigned long long *> g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 __global__ void noalloc_clear(unsigned long long *acc, uint32_t n_classes) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2u * n_classes; i += gridDim.x * blockDim.x)
@@ -88,24 +92,30 @@ extern "C" gp_status gp_pmerge_noalloc(const int32_t *mech_class, const float *q
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    if (e != cudaSuccess) {
         set_last_error(std::string("gp_pmerge_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
         return GP_ERR_CUDA;
     }
-    unsigned long long *acc = nullptr;
-    {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_last_error("gp_pmerge_noalloc: device " + std::to_string(dev) + " is beyond the " +
+                       std::to_string(kNoAllocMaxDevices) + " devices this entry point supports");
+        return GP_ERR_CUDA;
+    }
+    unsigned long long *acc = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!acc) {
         // one-time set-up per device, with that device current
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        acc = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+        if (!acc) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_acc);
             if (e != cudaSuccess || !p) {
                 set_last_error(std::string("gp_pmerge_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
                 return GP_ERR_CUDA;
             }
-            g_noalloc_ptr[dev] = static_cast<unsigned long long *>(p);
+            acc = static_cast<unsigned long long *>(p);
+            g_noalloc_ptr[dev].store(acc, std::memory_order_release);
         }
-        acc = g_noalloc_ptr[dev];
     }
     if (n_classes == 0) return GP_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

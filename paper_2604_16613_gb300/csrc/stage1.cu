@@ -265,6 +265,8 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
     constexpr uint32_t NCT = NCW * 32;             // consumer threads
     const Params &P = *B.params;
     const uint32_t level = P.level, rec_cap = P.rec_cap;
+    const uint32_t wlim = P.wait_limit;            // polls of a bounded wait
+    const bool stall = P.stall_windows != 0u;      // test knob: no window is staged
     // Pauli components a level keeps (Table tab:correlation-level)
     const uint32_t nc_dep1 = level == 0u ? 2u : 3u, nc_dep2 = level == 0u ? 6u : (level == 1u ? 10u : 15u);
     const uint32_t lane = threadIdx.x & 31u, l16 = lane & 15u, half = lane >> 4;
@@ -283,6 +285,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
     }
     __syncthreads();
     uint32_t phase_bits = 0u;         // mbarrier parity per ring slot (bit i)
+    uint32_t post_par = 0u, posted_any = 0u;   // producer: parity of its posts per slot
     bool timed_out = false;
     // this warp's chunk of the record pool [ck_pos, ck_end) and the next one,
     // requested ahead (its base lives in lane 0 until it is taken)
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
         // descriptor
         auto wait = [&](int L) -> Window {
             const uint32_t slot = slot_of(L);
-            if (!mbar_wait_bounded(&sh.mbar[slot], (phase_bits >> slot) & 1u)) sh.tmo = 1u;
+            if (!mbar_wait_bounded(&sh.mbar[slot], (phase_bits >> slot) & 1u, wlim)) sh.tmo = 1u;
             phase_bits ^= 1u << slot;
             return sh.desc[slot];
         };
@@ -511,13 +514,20 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
         uint32_t cur = n_ent;             // entries with layer <= L
         bool stopped = false;
         int posted = L + 1;               // lowest window published so far
+        // the producer's posts (a stalled producer posts nothing)
+        auto post_tracked = [&](int k) {
+            if (!producer || stall) return;
+            post(k);
+            post_par ^= 1u << slot_of(k);
+            posted_any |= 1u << slot_of(k);
+        };
         for (int k = L; k >= L - (int)nring + 2 && k >= -1; k--) {
-            if (producer) post(k);
+            post_tracked(k);
             posted = k;
         }
         for (;;) {
             if (L - (int)nring + 1 >= -1) {
-                if (producer) post(L - (int)nring + 1);
+                post_tracked(L - (int)nring + 1);
                 posted = L - (int)nring + 1;
             }
             const Window v = wait(L);
@@ -645,12 +655,19 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
         }
         // windows published ahead of an early stop land before their slots
         // are reused
-        for (int k = L - 1; k >= posted; k--) wait(k);
+        if (!stall)
+            for (int k = L - 1; k >= posted; k--) wait(k);
         __syncthreads();
         if (timed_out || sh.tmo) {
             if (threadIdx.x == 0) report(B.status, GP_ERR_TIMEOUT, 1u, gcol, (uint32_t)L);
             break;
         }
+    }
+    // after a wait gave up, copies may still be in flight: the last one posted
+    // to each slot lands before the block exits (full limit)
+    if (producer && lane == 0u) {
+        for (uint32_t i = 0; i < nring; i++)
+            if ((posted_any >> i) & 1u) mbar_wait_bounded(&sh.mbar[i], ((post_par >> i) & 1u) ^ 1u);
     }
 }
 
@@ -750,6 +767,8 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
     static_assert(NW >= 3, "walker, emitters and producer");
     const Params &P = *B.params;
     const uint32_t level = P.level, rec_cap = P.rec_cap;
+    const uint32_t wlim = P.wait_limit;            // polls of a bounded wait
+    const bool stall = P.stall_windows != 0u;      // test knob: no window is staged
     const uint32_t nc_dep1 = level == 0u ? 2u : 3u, nc_dep2 = level == 0u ? 6u : (level == 1u ? 10u : 15u);
     const uint32_t lane = threadIdx.x & 31u, l16 = lane & 15u, half = lane >> 4;
     const uint32_t warp = threadIdx.x >> 5;
@@ -788,7 +807,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
 
     // bounded wait; gives up early once another role has given up
     auto wait_bar = [&](unsigned long long *bar, uint32_t parity) -> bool {
-        for (uint32_t it = 0; it < (1u << 22); it++) {
+        for (uint32_t it = 0; it < wlim; it++) {
             if (mbar_try_wait(bar, parity)) return true;
             if ((it & 31u) == 31u && *tmo_v) return false;
         }
@@ -1254,11 +1273,11 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     uint32_t got = 0;
                     if (lane == 0u) {
                         uint32_t it = 0;
-                        for (; it < (1u << 22); it++) {
+                        for (; it < wlim; it++) {
                             if (mbar_try_wait(&sh.win_free[slot], (free_par >> slot) & 1u)) { got = 1u; break; }
                             if ((it & 15u) == 15u && (*done_v || *tmo_v)) break;
                         }
-                        if (it == (1u << 22)) *tmo_v = 1u;
+                        if (it == wlim) *tmo_v = 1u;
                     }
                     if (!__shfl_sync(0xFFFFFFFFu, got, 0)) break;
                     free_par ^= 1u << slot;
@@ -1266,10 +1285,12 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                 }
                 const uint32_t stop = lane == 0u ? (*done_v | *tmo_v) : 0u;
                 if (__shfl_sync(0xFFFFFFFFu, stop, 0)) break;
-                post(Lp);
+                if (!stall) {
+                    post(Lp);
+                    post_par ^= 1u << slot;
+                    posted_any |= 1u << slot;
+                }
                 free_pend |= 1u << slot;
-                post_par ^= 1u << slot;
-                posted_any |= 1u << slot;
                 Lp--;
             }
             if (lane == 0u) sh.posted_lo = Lp + 1;

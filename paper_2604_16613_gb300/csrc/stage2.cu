@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(512, 4) group_kernel(Buffers B) {
         // one mixing round per (column, word): collisions cost probes, never
         // correctness (claims are verified on the full mask)
         for (uint32_t i = 0; i < cnt; i++) h = mix64(h ^ w[i] ^ (0x9E3779B97F4A7C15ull * (col[i] + 1ull)));
+        h = weaken_hash(h, P.weak_hash);
         const uint32_t key_hi = (uint32_t)(h >> 32);
         const unsigned long long mine = ((unsigned long long)key_hi << 32) | m;
         uint32_t pos = (uint32_t)h & cap_mask, slot = kNone;

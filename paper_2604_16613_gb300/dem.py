@@ -200,6 +200,8 @@ class Dem:
         off, idx = h["det_offsets"], h["det_idx"]
         for e in range(lo, hi):
             key = (tuple(int(x) for x in idx[off[e]:off[e + 1]]), int(h["obs_mask"][e]))
+            if key in out:
+                raise ValueError(f"circuit {circuit}: hyperedge {key} appears twice (a class was split)")
             out[key] = (float(h["prob"][e]), float(h["logodds"][e]))
         return out
 
@@ -295,6 +297,13 @@ class Driver:
         t = native.GpTuning()
         native.check(self.lib.gp_get_tuning(self.handle, ctypes.byref(t)))
         return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def set_debug(self, weak_hash: int = 0, wait_limit: int = 0, stall_windows: int = 0):
+        """Test knobs of gp_set_debug: the weak grouping hashes (1: one tag for
+        every mask, 2: one hash for every mask), the polls before a device
+        wait gives up (0: the default), and a stage 1 that stages no window."""
+        d = native.GpDebug(weak_hash, wait_limit, stall_windows, 0)
+        native.check(self.lib.gp_set_debug(self.handle, ctypes.byref(d)))
 
     def enable_timing(self, on: bool = True):
         native.check(self.lib.gp_enable_timing(self.handle, int(on)))

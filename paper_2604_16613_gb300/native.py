@@ -22,7 +22,7 @@ LEVELS = {"L0": 0, "L1": 1, "L2": 2, 0: 0, 1: 1, 2: 2}
 EXPORTED = [
     "gp_workspace_size", "gp_driver_create", "gp_driver_destroy", "gp_compile_batch", "gp_compile",
     "gp_backward", "gp_result_view", "gp_result_to_host", "gp_set_tuning", "gp_get_tuning", "gp_enable_timing",
-    "gp_last_timing", "gp_last_launch_count", "gp_last_error", "gp_pmerge_noalloc",
+    "gp_last_timing", "gp_last_launch_count", "gp_last_error", "gp_set_debug", "gp_pmerge_noalloc",
     "gp_server_create", "gp_server_destroy", "gp_server_open_patch", "gp_server_close_patch",
     "gp_server_submit", "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release",
     "gp_server_register_cycle", "gp_server_submit_registered", "gp_server_submit_registered_many",
@@ -59,6 +59,11 @@ class GpDemView(ctypes.Structure):
 class GpTuning(ctypes.Structure):
     _fields_ = [("stage1_threads", ctypes.c_uint32), ("stage1_blocks_per_sm", ctypes.c_uint32),
                 ("stage2_threads", ctypes.c_uint32), ("stage2_blocks_per_sm", ctypes.c_uint32)]
+
+
+class GpDebug(ctypes.Structure):
+    _fields_ = [("weak_hash", ctypes.c_uint32), ("wait_limit", ctypes.c_uint32),
+                ("stall_windows", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class GpServerConfig(ctypes.Structure):
@@ -120,6 +125,7 @@ def load(path: str = LIB_PATH):
         lib.gp_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.gp_last_launch_count.argtypes = [vp]
         lib.gp_last_launch_count.restype = u32
+        lib.gp_set_debug.argtypes = [vp, ctypes.POINTER(GpDebug)]
         lib.gp_pmerge_noalloc.argtypes = [vp, vp, u32, u32, vp, vp, vp]
         lib.gp_pmerge_noalloc.restype = i32
         lib.gp_server_create.argtypes = [ctypes.POINTER(GpServerConfig), ctypes.POINTER(vp)]
@@ -147,7 +153,7 @@ def load(path: str = LIB_PATH):
         lib.gp_last_error.restype = ctypes.c_char_p
         for name in ("gp_workspace_size", "gp_driver_create", "gp_compile_batch", "gp_compile",
                      "gp_backward", "gp_result_view", "gp_result_to_host", "gp_set_tuning",
-                     "gp_get_tuning", "gp_enable_timing", "gp_last_timing"):
+                     "gp_get_tuning", "gp_enable_timing", "gp_last_timing", "gp_set_debug"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib

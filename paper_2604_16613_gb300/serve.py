@@ -213,8 +213,22 @@ class Server:
     def edges(res: dict) -> dict:
         """{(detector tuple, observable mask): (P, w)} of one request's result."""
         off, det = res["det_offsets"], res["det_idx"]
-        return {(tuple(int(x) for x in det[off[i]:off[i + 1]]), int(res["obs_mask"][i])):
-                (float(res["prob"][i]), float(res["logodds"][i])) for i in range(len(res["prob"]))}
+        out = {}
+        for i in range(len(res["prob"])):
+            key = (tuple(int(x) for x in det[off[i]:off[i + 1]]), int(res["obs_mask"][i]))
+            if key in out:
+                raise ValueError(f"request {res['request']}: hyperedge {key} delivered twice")
+            out[key] = (float(res["prob"][i]), float(res["logodds"][i]))
+        return out
+
+    @staticmethod
+    def _merge(acc: dict, part: dict, patch: int):
+        """Add one request's hyperedges to a patch's union; a hyperedge
+        delivered by two requests of one patch is an error."""
+        dup = acc.keys() & part.keys()
+        if dup:
+            raise ValueError(f"patch {patch}: hyperedge {next(iter(dup))} delivered by two requests")
+        acc.update(part)
 
     def stream(self, circuits, horizons=None, level="L2", interleave=True) -> list[dict]:
         """Open one patch per circuit, submit every cycle (round-robin over
@@ -245,7 +259,7 @@ class Server:
                         raise RuntimeError("server made no progress")
                     pending -= done
                     for r in self.completed():
-                        out[owner[r]].update(self.edges(self.result(r)))
+                        self._merge(out[owner[r]], self.edges(self.result(r)), owner[r])
                         self.release(r)
             owner[rid] = i
             pending += 1
@@ -255,7 +269,7 @@ class Server:
                 raise RuntimeError("server made no progress")
             pending -= done
             for r in self.completed():
-                out[owner[r]].update(self.edges(self.result(r)))
+                self._merge(out[owner[r]], self.edges(self.result(r)), owner[r])
                 self.release(r)
         for p in pids:
             self.close_patch(p)

@@ -3,6 +3,8 @@
 Masks (hyperedge keys) must match bit-exactly; probabilities within 1e-5
 relative; gradients within 1e-4 relative (or 1e-6 of the largest entry).
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -15,7 +17,7 @@ from paper_2604_16613_gb300 import circuits as C
 from paper_2604_16613_gb300 import native
 from paper_2604_16613_gb300.dem import Bounds, DeviceCircuit, Driver
 
-from parity import compare_edges, oracle_edges
+from parity import compare_arrays, compare_edges, oracle_edges
 
 pytestmark = pytest.mark.gpu
 
@@ -83,7 +85,9 @@ def test_random_circuits_parity():
         noise = circ.default_noise
         level = ["L0", "L1", "L2"][seed % 3]
         _, dem = run(circ, noise, level)
-        compare_edges(dem.edges(), oracle_edges(circ, noise, level).edges(), f"seed {seed}")
+        ref = oracle_edges(circ, noise, level)
+        assert dem.n_edges == ref.n_classes, f"seed {seed}"
+        compare_edges(dem.edges(), ref.edges(), f"seed {seed}")
 
 
 def test_batch_matches_individual_and_oracle():
@@ -97,7 +101,7 @@ def test_batch_matches_individual_and_oracle():
     assert dem.n_circuits == len(circs)
     for b, (c, nz) in enumerate(zip(circs, noises)):
         got = dem.edges(b, host)
-        compare_edges(got, oracle_edges(c, nz).edges(), f"batch circuit {b}")
+        compare_arrays(host, b, oracle_edges(c, nz), f"batch circuit {b}")
         solo = Driver.for_circuits([c]).compile(c, f32(nz)).edges()
         assert got == solo, f"circuit {b}: result differs alone and in the batch"
 
@@ -108,7 +112,7 @@ def test_surface_parity_large(d):
     noise = C.log_uniform_noise(circ.n_locations, seed=2)
     _, dem = run(circ, noise)
     ref = oracle_edges(circ, noise)
-    compare_edges(dem.edges(), ref.edges(), f"d={d}")
+    compare_arrays(dem.to_host(), 0, ref, f"d={d}")
 
 
 def test_surface_d25_full_size():
@@ -122,6 +126,89 @@ def test_surface_d25_full_size():
     assert dem.n_edges == ref.n_classes
     wp, _ = compare_edges(dem.edges(), ref.edges(), "d=25")
     assert wp <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# exact grouping under hash collisions
+# ---------------------------------------------------------------------------
+
+WEAK = [
+    ("surf5-constant-hash", lambda: C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3)), 2),
+    ("surf5-constant-tag", lambda: C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3)), 1),
+    ("surf15-constant-tag", lambda: C.rotated_surface_code_memory(15, 15, C.NoiseModel.uniform(1e-3)), 1),
+    ("bb4-constant-tag", lambda: C.bb_memory(4, C.NoiseModel.uniform(1e-3), seed=3), 1),
+]
+
+
+@pytest.mark.parametrize("name,make,mode", WEAK, ids=[w[0] for w in WEAK])
+def test_weak_hash_grouping_stays_exact(name, make, mode):
+    """The grouping table's claims are verified on whole masks (Sec. 3.2's
+    aggregator only argues that hash collisions are unlikely).  With every
+    mask given the same tag (mode 1) or the same hash (mode 2), every probe
+    that meets another class must be told apart by the word-by-word check;
+    the model must still equal the oracle's exactly, class for class."""
+    circ = make()
+    noise = f32(C.log_uniform_noise(circ.n_locations, seed=2))
+    drv = Driver.for_circuits([circ])
+    dc, nz = DeviceCircuit(circ), torch.tensor(noise, device="cuda")
+    normal = drv.compile(dc, nz).to_host()
+    drv.set_debug(weak_hash=mode)
+    weak = drv.compile(dc, nz).to_host()
+    compare_arrays(weak, 0, oracle_edges(circ, noise), name)
+    for k in ("det_offsets", "det_idx", "obs_mask", "prob", "logodds"):
+        assert np.array_equal(weak[k], normal[k]), k
+
+
+def test_weak_hash_random_batch_stays_exact():
+    """A batch of random circuits (all gate kinds, both bases) grouped with a
+    single hash value for every mask."""
+    circs = [C.random_circuit(3000 + s) for s in range(24)]
+    noises = [f32(c.default_noise) for c in circs]
+    drv = Driver.for_circuits(circs)
+    drv.set_debug(weak_hash=2)
+    for level in ("L0", "L2"):
+        host = drv.compile(circs, np.concatenate(noises), level).to_host()
+        for b, (c, nz) in enumerate(zip(circs, noises)):
+            compare_arrays(host, b, oracle_edges(c, nz, level), f"weak batch {level} circuit {b}")
+
+
+# ---------------------------------------------------------------------------
+# bounded device waits
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("walk", ["role-split", "block-wide"])
+def test_device_wait_timeout_is_reported_and_driver_recovers(walk):
+    """Stage 1 with no layer window staged: the first wait of every walk can
+    only run out.  With a short wait limit the compile returns
+    GP_ERR_TIMEOUT quickly (no hang, no fault, nothing left running), and the
+    next compile on the same driver, with the knobs back to normal, equals the
+    oracle and the compile made before the timeout."""
+    circ = C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))
+    noise = f32(C.log_uniform_noise(circ.n_locations, seed=8))
+    bd = Bounds.for_circuits([circ])
+    if walk == "block-wide":
+        bd.max_qubits = 4096          # the role-split tables no longer fit
+    drv = Driver(bd)
+    dc, nz = DeviceCircuit(circ), torch.tensor(noise, device="cuda")
+    before = drv.compile(dc, nz).to_host()
+    drv.set_debug(wait_limit=256, stall_windows=1)
+    t0 = time.perf_counter()
+    msg = expect_error(native.GP_ERR_TIMEOUT, lambda: drv.compile(dc, nz))
+    assert "timed out" in msg
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 30.0
+    drv.set_debug()
+    after = drv.compile(dc, nz).to_host()
+    compare_arrays(after, 0, oracle_edges(circ, noise), f"{walk} after timeout")
+    for k in ("det_offsets", "det_idx", "obs_mask", "prob", "logodds"):
+        assert np.array_equal(after[k], before[k]), k
+
+
+def test_debug_knobs_are_validated():
+    circ = C.rotated_surface_code_memory(3, 3, C.NoiseModel.uniform(1e-3))
+    drv = Driver.for_circuits([circ])
+    expect_error(native.GP_ERR_INVALID, lambda: drv.set_debug(weak_hash=3))
+    expect_error(native.GP_ERR_INVALID, lambda: drv.set_debug(stall_windows=2))
 
 
 # ---------------------------------------------------------------------------

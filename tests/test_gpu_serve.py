@@ -59,10 +59,12 @@ def test_stream_equals_full_compile(wl, name, K):
     srv = Server.for_circuits([circ], max_cycles_per_step=K, max_horizon=H)
     got = srv.stream([circ], [H])[0]
     ref = gpu_full(circ)
+    orc = oracle_edges(circ, f32(circ.default_noise))
+    assert len(got) == len(ref) == orc.n_classes
     assert set(got) == set(ref)
     for k, (p, w) in ref.items():
         assert got[k][0] == p and got[k][1] == w, k
-    compare_edges(got, oracle_edges(circ, f32(circ.default_noise)).edges(), f"{name} K={K}")
+    compare_edges(got, orc.edges(), f"{name} K={K}")
 
 
 def test_levels(wl):
@@ -70,7 +72,9 @@ def test_levels(wl):
     srv = Server.for_circuits([circ], max_cycles_per_step=2, max_horizon=H)
     for level in ("L0", "L1"):
         got = srv.stream([circ], [H], level=level)[0]
-        compare_edges(got, oracle_edges(circ, f32(circ.default_noise), level).edges(), level)
+        orc = oracle_edges(circ, f32(circ.default_noise), level)
+        assert len(got) == orc.n_classes, level
+        compare_edges(got, orc.edges(), level)
 
 
 def test_mix_equals_alone(wl):

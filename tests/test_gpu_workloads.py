@@ -1,6 +1,9 @@
 """GPU parity on the other workloads of the paper: bivariate bicycle memory
 (forward and adjoint), adaptive [[4,2,2]]-concatenated branches compiled as
 one batch, the autotuner and the autograd function."""
+import multiprocessing as mp
+import os
+
 import numpy as np
 import pytest
 
@@ -13,7 +16,7 @@ from paper_2604_16613_gb300 import circuits as C
 from paper_2604_16613_gb300.autotune import autotune
 from paper_2604_16613_gb300.dem import Bounds, DemFunction, DeviceCircuit, Driver
 
-from parity import compare_edges, oracle_edges
+from parity import compare_arrays, compare_edges, oracle_arrays, oracle_edges
 
 pytestmark = pytest.mark.gpu
 
@@ -100,7 +103,32 @@ def test_concatenated_branches_one_batch():
     dem = drv.compile([DeviceCircuit(b) for b in branches], torch.tensor(np.concatenate(noises), device="cuda"))
     host = dem.to_host()
     for i, (b, nz) in enumerate(zip(branches, noises)):
-        compare_edges(dem.edges(i, host), oracle_edges(b, nz).edges(), f"branch {i}")
+        compare_arrays(host, i, oracle_edges(b, nz), f"branch {i}")
+
+
+def test_adaptive_256_branch_batch_parity():
+    """The benchmark's batched workload at full size: 256 realised branches of
+    the adaptive [[4,2,2]]-concatenated surface code (outer distance 10,
+    10-30 cycles each, seed 4; Secs. 5.1-5.2), compiled as one batch with the
+    benchmark's bounds and autotuned launch shape.  Every branch is compared
+    with the oracle: same number of hyperedges, identical masks, P and w
+    within tolerance.  The oracle runs first, in a spawn process pool."""
+    branches = C.adaptive_branches(n=256, d=10, lo=10, hi=30, seed=4)
+    noises = [f32(b.default_noise) for b in branches]
+    tasks = [(b.ops, b.recs, b.n_qubits, nz.astype(np.float64), "L2") for b, nz in zip(branches, noises)]
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        refs = pool.map(oracle_arrays, tasks, chunksize=4)
+    nz = torch.tensor(np.concatenate(noises), device="cuda")
+    dcs = [DeviceCircuit(b) for b in branches]
+    bd = Bounds.for_circuits(branches)
+    bd.max_det_entries = 8 * bd.max_mechanisms
+    drv = Driver(bd)
+    autotune(drv, dcs, nz, repeats=2)
+    dem = drv.compile(dcs, nz)
+    assert dem.n_circuits == 256
+    host = dem.to_host()
+    for i, ref in enumerate(refs):
+        compare_arrays(host, i, ref, f"branch {i}")
 
 
 def test_autotune_does_not_change_results():

@@ -81,3 +81,45 @@ def test_noalloc_rejects_too_many_classes():
     rc = lib.gp_pmerge_noalloc(None, None, 0, (1 << 19) + 1, None, None, None)
     assert rc == native.GP_ERR_CAPACITY
     assert b"524288" in lib.gp_last_error()
+
+
+def test_noalloc_edge_cases_closed_form():
+    """Documented edge behaviour on a hand-built case, against the closed
+    form P = (1 - prod(1 - 2 q)) / 2 in FP64: class ids -1 and n_classes are
+    skipped, q = 0 contributes nothing, q >= 1/2 saturates the class at 1/2,
+    a class without a positive member gets P = 0, and logodds may be NULL."""
+    lib = native.load()
+    n_classes = 5
+    mech_class = np.array([0, 0, 1, -1, 5, 2, 2, 3, 1, 0], dtype=np.int32)
+    q = np.array([1e-3, 2e-2, 0.0, 0.3, 0.4, 0.5, 1e-4, 0.0, 3e-4, 0.7], dtype=np.float32)
+    q[9] = 0.25          # keep class 0 below saturation; class 2 holds q = 1/2
+    expect = np.zeros(n_classes)
+    for c in range(n_classes):
+        qs = q[mech_class == c].astype(np.float64)
+        expect[c] = 0.5 * (1.0 - np.prod(1.0 - 2.0 * np.minimum(qs, 0.5)))
+    sat = torch.tensor([0.7], dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    mc = torch.tensor(mech_class, device="cuda")
+    qd = torch.tensor(q, device="cuda")
+    for call in range(2):
+        prob = torch.full((n_classes,), float("nan"), dtype=torch.float32, device="cuda")
+        rc = lib.gp_pmerge_noalloc(ctypes.c_void_p(mc.data_ptr()), ctypes.c_void_p(qd.data_ptr()), mech_class.size,
+                                   n_classes, ctypes.c_void_p(prob.data_ptr()), None,
+                                   ctypes.c_void_p(stream.cuda_stream))
+        assert rc == native.GP_OK, lib.gp_last_error()
+        torch.cuda.synchronize()
+        p = prob.cpu().numpy().astype(np.float64)
+        assert p[3] == 0.0 and p[4] == 0.0                     # no positive member, or no member at all
+        assert p[2] == pytest.approx(0.5, abs=1e-7)            # q = 1/2 saturates
+        for c in (0, 1):
+            assert abs(p[c] - expect[c]) <= P_RTOL * expect[c], (call, c, p[c], expect[c])
+    # a lone member with q above 1/2 also saturates at 1/2, with log-odds 0
+    one = torch.zeros(1, dtype=torch.int32, device="cuda")
+    prob = torch.empty(1, dtype=torch.float32, device="cuda")
+    lo = torch.empty(1, dtype=torch.float32, device="cuda")
+    rc = lib.gp_pmerge_noalloc(ctypes.c_void_p(one.data_ptr()), ctypes.c_void_p(sat.data_ptr()), 1, 1,
+                               ctypes.c_void_p(prob.data_ptr()), ctypes.c_void_p(lo.data_ptr()),
+                               ctypes.c_void_p(stream.cuda_stream))
+    assert rc == native.GP_OK, lib.gp_last_error()
+    torch.cuda.synchronize()
+    assert prob.item() == pytest.approx(0.5, abs=1e-7) and abs(lo.item()) < 1e-6
