@@ -41,6 +41,7 @@ struct Layout {
     uint64_t max_det_entries;
     uint64_t qidx_cap16;         // layer index arena, 16-byte units
     uint64_t rec_cap;
+    uint32_t ov_cap;             // overflow words (beyond kInlineWords per mechanism)
     // byte offsets in the workspace
     uint64_t total = 0;
     uint64_t params_bytes = 0;   // Params + Status + circuits + tiles + items + col_circ
@@ -87,6 +88,9 @@ Layout make_layout(const gp_bounds &b) {
     // workloads here average 2 to 2.5), plus the unused chunk tails that
     // stage-1 warps may leave
     L.rec_cap = std::min<uint64_t>(4ull * b.max_mechanisms + kPoolSlack, 0xFFFFFFF0ull);
+    // words beyond the inline slots: the workloads here put 0 to 6 % of their
+    // mechanisms above four words; a quarter of the mechanisms plus 2^16 spare
+    L.ov_cap = (uint32_t)std::min<uint64_t>((uint64_t)b.max_mechanisms / 4u + 65536u, 0xFFFFFFF0ull);
     // one qubit index block per layer slot at the widest circuit
     L.qidx_cap16 = (uint64_t)L.max_layer_slots * (layer_geo(b.max_qubits).bytes / 16u);
     return L;
@@ -120,11 +124,13 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     B.det_row = c.take<uint32_t>(std::max<uint32_t>(bd.max_detectors, 1));
     B.obs_rows = c.take<uint32_t>(bd.max_ops);
     B.obs_count = c.take<uint32_t>(bd.max_circuits);
-    B.mech_cnt = c.take<uint32_t>(bd.max_mechanisms);
-    B.mech_off = c.take<uint2>((uint64_t)bd.max_mechanisms + 1);
+    B.mech_key = c.take<unsigned long long>(bd.max_mechanisms);
     B.mech_info = c.take<unsigned long long>(bd.max_mechanisms);
-    B.slot_col = c.take<uint32_t>(L.rec_cap);
-    B.slot_word = c.take<unsigned long long>(L.rec_cap);
+    B.inl_col = c.take<uint32_t>((uint64_t)kInlineWords * bd.max_mechanisms);
+    B.inl_word = c.take<unsigned long long>((uint64_t)kInlineWords * bd.max_mechanisms);
+    B.ov_rec = c.take<uint4>(L.ov_cap);
+    B.ov_mech = c.take<uint32_t>(L.ov_cap);
+    B.ov_head = c.take<uint32_t>(bd.max_mechanisms);
     B.slot_of = c.take<uint32_t>(bd.max_mechanisms);
     B.mech_class = c.take<int32_t>(bd.max_mechanisms);
     B.table = c.take<TabSlot>(1ull << L.table_log2);
@@ -209,7 +215,8 @@ gp_status full_reset(gp_driver *d, cudaStream_t s) {
     const Layout &L = d->L;
     launch_init_table(d->B.table, (size_t)1 << L.table_log2, s);
     GP_CUDA(cudaGetLastError());
-    GP_CUDA(cudaMemsetAsync(d->B.mech_cnt, 0, sizeof(uint32_t) * (size_t)d->bounds.max_mechanisms, s));
+    GP_CUDA(cudaMemsetAsync(d->B.mech_key, 0, sizeof(unsigned long long) * (size_t)d->bounds.max_mechanisms, s));
+    GP_CUDA(cudaMemsetAsync(d->B.ov_head, 0xFF, sizeof(uint32_t) * (size_t)d->bounds.max_mechanisms, s));
     GP_CUDA(cudaMemsetAsync(d->B.gacc, 0, 2 * sizeof(unsigned long long) * std::max<uint32_t>(d->bounds.max_locations, 1), s));
     GP_CUDA(cudaMemsetAsync(d->B.records, 0xFF, sizeof(uint4) * L.rec_cap, s));
     GP_CUDA(cudaMemsetAsync(d->B.lists, 0, sizeof(uint2) * (2ull * d->bounds.max_ops + 4), s));
@@ -255,6 +262,7 @@ std::string describe(const Status &st) {
         else if (a == 8) snprintf(buf, sizeof buf, "mask-word pool of %u entries is full (it holds 4 words per mechanism of max_mechanisms on average plus 2^22 spare)", c);
         else if (a == 9) snprintf(buf, sizeof buf, "circuit %u: the per-layer qubit index needs %u x 16 bytes, more than max_layers x max_qubits allow", b, c);
         else if (a == 10) snprintf(buf, sizeof buf, "circuit %u layer %u: more than %u rows in one TICK layer", b, c, kMaxLayerRows);
+        else if (a == 11) snprintf(buf, sizeof buf, "overflow list of %u mask words is full (mechanisms with more than %d words keep the rest there; it holds a quarter of max_mechanisms plus 65536)", c, kInlineWords);
         else snprintf(buf, sizeof buf, "capacity exceeded (%u, %u, %u)", a, b, c);
         break;
     default:
@@ -684,6 +692,7 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     P->weak_hash = d->debug.weak_hash;
     P->wait_limit = d->debug.wait_limit ? d->debug.wait_limit : kWaitPolls;
     P->stall_windows = d->debug.stall_windows;
+    P->ov_cap = L.ov_cap;
     // ---- pipeline: one graph launch ----------------------------------------------
     {
         const gp_status gs = ensure_graph(d);

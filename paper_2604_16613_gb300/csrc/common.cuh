@@ -16,6 +16,8 @@ constexpr int kRowTile = 512;           // circuit rows per lowering tile
 constexpr int kLowerThreads = 256;      // 2 rows per thread
 constexpr int kMaxEntries = 1024;       // (measurement, word) pairs per column
 constexpr int kMaxMaskWords = 16;       // hard cap of mask words per mechanism
+constexpr int kInlineWords = 4;         // mask words kept beside each mechanism;
+                                        // the rest go to the overflow list
 constexpr int kMechPerBlockScan = 1024; // mechanisms per compaction block
 constexpr uint64_t kPoolSlack = 1ull << 22;  // record-pool slack for unused chunk tails
 constexpr int kPackThreads = 256;       // layer packing block size
@@ -73,7 +75,7 @@ struct Params {
     uint32_t weak_hash;         // 0 full hash, 1 constant tag, 2 constant hash
     uint32_t wait_limit;        // polls of a bounded wait (never 0 on the device)
     uint32_t stall_windows;     // 1: stage 1 stages no window
-    uint32_t pad_dbg;
+    uint32_t ov_cap;            // capacity of the overflow word list
 };
 
 // device status block (read back by the host after every compile)
@@ -86,7 +88,9 @@ struct Status {
     uint32_t n_scan_blocks;
     uint32_t queue_head;        // stage-1 work queue
     uint32_t rec_count;         // records handed out from the pool
-    uint32_t pad[6];
+    uint32_t ov_count;          // overflow words taken (mechanisms with more
+                                // than kInlineWords words)
+    uint32_t pad[5];
 };
 
 // one slot of the grouping hash table (one 32-byte sector)
@@ -125,14 +129,17 @@ struct Buffers {
     uint32_t *det_row;          // per detector: its row
     uint32_t *obs_rows;         // per circuit (at op_base): OBSERVABLE rows
     uint32_t *obs_count;        // per circuit
-    uint32_t *mech_cnt;         // per mechanism: mask words produced (stage 1),
-                                // counted back down to 0 by the scatter
+    unsigned long long *mech_key;    // per mechanism: word count (low byte) plus
+                                // the sum of its words' hashes (grouping key);
+                                // zero between compiles
     uint32_t *edge_mech;        // per hyperedge: its class's smallest mechanism
-    uint2 *mech_off;            // per mechanism: start of its words (.x), n + 1
     unsigned long long *mech_info;   // loc | kind << 32 | comp << 40 | circuit << 48
-    uint32_t *slot_col;         // mask words in mechanism order: column ids
+    uint32_t *inl_col;          // per mechanism, kInlineWords slots: column ids
                                 // (kObsColFlag on the observable word)
-    unsigned long long *slot_word;   // ... and the words
+    unsigned long long *inl_word;    // ... and the words
+    uint4 *ov_rec;              // overflow words {column, word lo, word hi, next}
+    uint32_t *ov_mech;          // mechanism of each overflow word
+    uint32_t *ov_head;          // per mechanism: first overflow word or kNone
     uint32_t *slot_of;          // per mechanism: hash-table slot or kNone
     int32_t *mech_class;        // per mechanism: edge or -1
     TabSlot *table;             // grouping hash table

@@ -294,10 +294,29 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
     // producer warp: first layer held by the segment cache
     uint32_t seg_lo = 0xFFFFFFFFu;
 
+    // positions [a, b) of the record pool (within its capacity) marked empty
+    // by the warp: every position handed out is a record or empty, so the
+    // scatter never reads a stale record
+    auto fill_empty = [&](uint32_t a, uint32_t b) {
+        b = min(b, rec_cap);
+        for (uint32_t i = a + lane; i < b; i += 32u) B.records[i].x = kNone;
+    };
+    // at the end: the unused rest of the current chunk and the chunk
+    // requested ahead (warp-uniform)
+    auto flush_chunks = [&]() {
+        fill_empty(ck_pos, ck_end);
+        ck_pos = ck_end;
+        if (has_next) {
+            const uint32_t nb = __shfl_sync(0xFFFFFFFFu, ck_next, 0);
+            if (nb < rec_cap) fill_empty(nb, nb + wchunk);
+            has_next = false;
+        }
+    };
     // room for `need` more records in this warp's chunk (warp-uniform);
     // false once the pool is exhausted (reported)
     auto warp_room = [&](uint32_t need) -> bool {
         if (ck_end - ck_pos >= need) return true;
+        fill_empty(ck_pos, ck_end);
         uint32_t nb = 0;
         if (has_next) {
             nb = __shfl_sync(0xFFFFFFFFu, ck_next, 0);
@@ -451,7 +470,6 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
             if (w != 0ull) {
                 const uint32_t mech = mech_base + r.y + l16;
                 B.records[ck_pos + __popc(m & lt_mask)] = make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
-                atomicAdd(&B.mech_cnt[mech], 1u);
             }
             ck_pos += cnt;
         };
@@ -663,6 +681,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
             break;
         }
     }
+    flush_chunks();
     // after a wait gave up, copies may still be in flight: the last one posted
     // to each slot lands before the block exits (full limit)
     if (producer && lane == 0u) {
@@ -820,8 +839,22 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         if (__all_sync(0xFFFFFFFFu, mbar_try_wait(bar, parity))) return true;     // usually done already
         return __all_sync(0xFFFFFFFFu, wait_bar(bar, parity));
     };
+    auto fill_empty = [&](uint32_t a, uint32_t b) {
+        b = min(b, rec_cap);
+        for (uint32_t i = a + lane; i < b; i += 32u) B.records[i].x = kNone;
+    };
+    auto flush_chunks = [&]() {
+        fill_empty(ck_pos, ck_end);
+        ck_pos = ck_end;
+        if (has_next) {
+            const uint32_t nb = __shfl_sync(0xFFFFFFFFu, ck_next, 0);
+            if (nb < rec_cap) fill_empty(nb, nb + wchunk);
+            has_next = false;
+        }
+    };
     auto warp_room = [&](uint32_t need) -> bool {
         if (ck_end - ck_pos >= need) return true;
+        fill_empty(ck_pos, ck_end);
         uint32_t nb = 0;
         if (has_next) {
             nb = __shfl_sync(0xFFFFFFFFu, ck_next, 0);
@@ -1180,7 +1213,6 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                         const uint32_t mech = mech_base + r.y + l16;
                         B.records[ck_pos + __popc(m & lt_mask)] =
                             make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
-                        atomicAdd(&B.mech_cnt[mech], 1u);
                     }
                     ck_pos += cnt;
                 };
@@ -1317,6 +1349,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
             break;
         }
     }
+    flush_chunks();
     // copies still in flight (after a timeout) land before the block exits
     if (producer && lane == 0u) {
         for (uint32_t i = 0; i < nring; i++)

@@ -1,30 +1,34 @@
 // stage2.cu -- probability aggregation (Sec. 3.2) and the adjoint.
 //
-// Stage 1 leaves mask-word records {mechanism, column, word} in a pool and a
-// word count per mechanism.  Stage 2:
-//   offsets    exclusive scan of the counts -> per-mechanism word ranges (CSR)
-//   scatter    records -> their mechanism's range, counting the mechanism's
-//              word count back down to 0 (the pool and the counts clean
-//              themselves)
-//   group      one thread per mechanism: sort its words by column, hash them,
-//              claim or join a slot of an open-addressing table whose claims
-//              are verified word by word (grouping is exact whatever the hash
-//              does), keep the smallest member, and add t_i = -log(1 - 2 q_i)
-//              to the class sum as an exact 128-bit fixed-point integer:
-//              1 - 2P = prod(1 - 2 q_i) = exp(-sum t_i) (Eq. pmerge), and
-//              integer addition makes the sum independent of the order in
-//              which the atomics land
-//   compact    classes are numbered by their smallest member (scan of
-//              "leader" flags and detector counts; the scan also lists the
-//              leaders in edge order), one thread per hyperedge writes
-//              it: ascending detector ids, observable word,
-//              P = -expm1(-T) / 2 and w = log1p(-P) - log(P)
-//   finalize   per-mechanism class ids; used table slots are cleared for
-//              the next compile
+// Stage 1 leaves mask-word records {mechanism, column, word} in a pool (every
+// position of the pool handed out is either a record or marked empty).
+// Stage 2:
+//   scatter    per record: one 64-bit atomic add into the mechanism's key
+//              (word count in the low byte, the sum of its words' hashes
+//              above: equal masks give equal keys whatever the order the
+//              words arrive in), whose old value says where the word goes:
+//              one of the mechanism's kInlineWords slots, or its overflow
+//              list
+//   group      one thread per mechanism: hash the key, claim or join a slot
+//              of an open-addressing table whose claims are verified on the
+//              whole mask (word count and every (column, word) pair), so the
+//              grouping is exact whatever the hash does; keep the smallest
+//              member and add t_i = -log(1 - 2 q_i) to the class sum as an
+//              exact 128-bit fixed-point integer: 1 - 2P = prod(1 - 2 q_i) =
+//              exp(-sum t_i) (Eq. pmerge), and integer addition makes the sum
+//              independent of the order in which the atomics land
+//   compact    classes are numbered by their smallest member: a two-pass scan
+//              whose input is read straight from the table (1 and the class's
+//              detector count for the smallest member of a class, else 0)
+//              lists the leaders in edge order with their detector offsets;
+//              then one thread per hyperedge writes it: ascending detector
+//              ids, observable word, P = -expm1(-T) / 2 and
+//              w = log1p(-P) - log(P)
+//   finalize   per-mechanism class ids; keys, overflow heads and used table
+//              slots are cleared for the next compile
 //   backward   dP/dp_i = (1 - 2P) / 2 * dt_i/dp and dw/dP = -1 / (P (1 - P)),
 //              summed per noise location in fixed point
-// The scans are two-pass reduce-then-scan passes (2048 elements per block)
-// with every grid fixed by the driver's bounds, so the whole sequence can be
+// Every grid is fixed by the driver's bounds, so the whole sequence can be
 // captured once and replayed.
 #include "common.cuh"
 
@@ -118,6 +122,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in
 
 
 // ---- per-mechanism words ----------------------------------------------------
+// Hash of one (column, word) pair; a mechanism's key adds these up (mod 2^64,
+// low byte masked off for the word count).
+__device__ __forceinline__ unsigned long long word_hash(uint32_t col, unsigned long long w) {
+    return mix64(w ^ (0x9E3779B97F4A7C15ull * (col + 1ull)));
+}
+
 // Each thread moves kScatterILP records per round, with every load and atomic
 // of the round in flight before the first store (the kernel is bound by their
 // latency).
@@ -133,51 +143,122 @@ __global__ void __launch_bounds__(512, 4) scatter_kernel(Buffers B) {
 #pragma unroll
         for (int u = 0; u < kScatterILP; u++) {
             const uint32_t i = i0 + u * stride;
-            r[u] = i < n ? B.records[i] : make_uint4(kNone, 0u, 0u, 0u);
+            r[u] = i < n ? __ldcs(&B.records[i]) : make_uint4(kNone, 0u, 0u, 0u);
         }
-        uint32_t pos[kScatterILP];
-#pragma unroll
-        for (int u = 0; u < kScatterILP; u++)
-            if (r[u].x != kNone) pos[u] = __ldg(&B.mech_off[r[u].x].x) + atomicSub(&B.mech_cnt[r[u].x], 1u) - 1u;
+        uint32_t k[kScatterILP];
 #pragma unroll
         for (int u = 0; u < kScatterILP; u++) {
             if (r[u].x == kNone) continue;
-            B.records[i0 + u * stride].x = kNone;
-            B.slot_col[pos[u]] = r[u].y;
-            B.slot_word[pos[u]] = ((unsigned long long)r[u].w << 32) | r[u].z;
+            const unsigned long long w = ((unsigned long long)r[u].w << 32) | r[u].z;
+            const unsigned long long add = (word_hash(r[u].y, w) & ~0xFFull) | 1ull;
+            k[u] = (uint32_t)(atomicAdd(&B.mech_key[r[u].x], add) & 0xFFull);
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterILP; u++) {
+            if (r[u].x == kNone) continue;
+            const uint32_t m = r[u].x;
+            const unsigned long long w = ((unsigned long long)r[u].w << 32) | r[u].z;
+            if (k[u] < (uint32_t)kInlineWords) {
+                B.inl_col[(size_t)kInlineWords * m + k[u]] = r[u].y;
+                B.inl_word[(size_t)kInlineWords * m + k[u]] = w;
+            } else {
+                const uint32_t j = atomicAdd(&B.status->ov_count, 1u);
+                if (j < P.ov_cap) {
+                    const uint32_t next = atomicExch(&B.ov_head[m], j);
+                    B.ov_rec[j] = make_uint4(r[u].y, r[u].z, r[u].w, next);
+                    B.ov_mech[j] = m;
+                } else {
+                    report(B.status, GP_ERR_CAPACITY, 11u, j, P.ov_cap);
+                }
+            }
         }
     }
 }
 
-// words of mechanism m sorted by column id (insertion sort: a handful)
-__device__ __forceinline__ uint32_t load_sorted(const Buffers &B, uint32_t m, uint32_t *col,
-                                                unsigned long long *w) {
-    const uint32_t o0 = B.mech_off[m].x, cnt = B.mech_off[m + 1].x - o0;
-    for (uint32_t i = 0; i < cnt; i++) {
-        const uint32_t c = B.slot_col[o0 + i];
-        const unsigned long long x = B.slot_word[o0 + i];
-        uint32_t j = i;
-        while (j > 0 && col[j - 1] > c) { col[j] = col[j - 1]; w[j] = w[j - 1]; j--; }
-        col[j] = c;
-        w[j] = x;
+// the (column, word) pairs of mechanism m with `cnt` words: the inline slots,
+// then its overflow list
+__device__ __forceinline__ void load_words(const Buffers &B, uint32_t m, uint32_t cnt, uint32_t *col,
+                                           unsigned long long *w) {
+    const uint4 c4 = *reinterpret_cast<const uint4 *>(&B.inl_col[(size_t)kInlineWords * m]);
+    const ulonglong2 w01 = *reinterpret_cast<const ulonglong2 *>(&B.inl_word[(size_t)kInlineWords * m]);
+    const ulonglong2 w23 = *reinterpret_cast<const ulonglong2 *>(&B.inl_word[(size_t)kInlineWords * m + 2]);
+    col[0] = c4.x; col[1] = c4.y; col[2] = c4.z; col[3] = c4.w;
+    w[0] = w01.x; w[1] = w01.y; w[2] = w23.x; w[3] = w23.y;
+    if (cnt > (uint32_t)kInlineWords) {
+        uint32_t j = B.ov_head[m];
+        for (uint32_t i = kInlineWords; i < cnt && j != kNone; i++) {
+            const uint4 r = B.ov_rec[j];
+            col[i] = r.x;
+            w[i] = ((unsigned long long)r.z << 32) | r.y;
+            j = r.w;
+        }
     }
-    return cnt;
 }
 
-// mask of mechanism rep equal to the sorted words col/w (exact): every word
-// of rep found at its column among them, counts equal
+// mask of mechanism rep equal to the words col/w of a mechanism with cnt
+// words (exact): the counts agree and every word of rep is found at its
+// column among them (columns are distinct within a mask)
 __device__ __forceinline__ bool same_mask(const Buffers &B, uint32_t rep, uint32_t cnt, const uint32_t *col,
                                           const unsigned long long *w) {
-    const uint32_t r0 = B.mech_off[rep].x;
-    if (B.mech_off[rep + 1].x - r0 != cnt) return false;
+    if ((uint32_t)(B.mech_key[rep] & 0xFFull) != cnt) return false;
+    uint32_t rc[kMaxMaskWords];
+    unsigned long long rw[kMaxMaskWords];
+    load_words(B, rep, cnt, rc, rw);
     for (uint32_t j = 0; j < cnt; j++) {
-        const uint32_t c = B.slot_col[r0 + j];
-        const unsigned long long x = B.slot_word[r0 + j];
         uint32_t i = 0;
-        while (i < cnt && col[i] != c) i++;
-        if (i == cnt || w[i] != x) return false;
+        while (i < cnt && col[i] != rc[j]) i++;
+        if (i == cnt || w[i] != rw[j]) return false;
     }
     return true;
+}
+
+// the same for masks of at most kInlineWords words, everything in registers
+__device__ __forceinline__ bool same_mask_inline(const Buffers &B, uint32_t rep, uint32_t cnt,
+                                                 const uint32_t (&col)[kInlineWords],
+                                                 const unsigned long long (&w)[kInlineWords]) {
+    if ((uint32_t)(B.mech_key[rep] & 0xFFull) != cnt) return false;
+    const uint4 c4 = *reinterpret_cast<const uint4 *>(&B.inl_col[(size_t)kInlineWords * rep]);
+    const ulonglong2 w01 = *reinterpret_cast<const ulonglong2 *>(&B.inl_word[(size_t)kInlineWords * rep]);
+    const ulonglong2 w23 = *reinterpret_cast<const ulonglong2 *>(&B.inl_word[(size_t)kInlineWords * rep + 2]);
+    const uint32_t rc[kInlineWords] = {c4.x, c4.y, c4.z, c4.w};
+    const unsigned long long rw[kInlineWords] = {w01.x, w01.y, w23.x, w23.y};
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < kInlineWords; j++) {
+        if ((uint32_t)j >= cnt) break;
+        bool found = false;
+#pragma unroll
+        for (int i = 0; i < kInlineWords; i++)
+            found |= (uint32_t)i < cnt && col[i] == rc[j] && w[i] == rw[j];
+        ok &= found;
+    }
+    return ok;
+}
+
+// Claim or join the class of mechanism m (hash h, detector count dets of
+// its mask) in the open-addressing table; eq(rep) says whether the claimant
+// rep of a slot with the same tag has the same mask.  Returns the slot, or
+// kNone when the table is full.
+template <class Eq>
+__device__ __forceinline__ uint32_t claim_or_join(const Buffers &B, unsigned long long h, uint32_t m,
+                                                  uint32_t cap_mask, uint32_t dets, Eq eq) {
+    const uint32_t key_hi = (uint32_t)(h >> 32);
+    const unsigned long long mine = ((unsigned long long)key_hi << 32) | m;
+    uint32_t pos = (uint32_t)h & cap_mask;
+    for (uint32_t probe = 0; probe <= cap_mask; probe++) {
+        unsigned long long e = __ldcg(&B.table[pos].entry);
+        if (e == kEmpty) {
+            const unsigned long long old = atomicCAS(&B.table[pos].entry, kEmpty, mine);
+            if (old == kEmpty) {
+                B.table[pos].cls = dets;      // the claim records the class's detector count
+                return pos;
+            }
+            e = old;
+        }
+        if ((uint32_t)(e >> 32) == key_hi && eq((uint32_t)e)) return pos;
+        pos = (pos + 1u) & cap_mask;
+    }
+    return kNone;
 }
 
 __global__ void __launch_bounds__(512, 4) group_kernel(Buffers B) {
@@ -187,7 +268,8 @@ __global__ void __launch_bounds__(512, 4) group_kernel(Buffers B) {
     const uint32_t cap_mask = (1u << P.table_log2) - 1u;
     const float *noise = P.noise;
     for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
-        const uint32_t cnt = B.mech_off[m + 1].x - B.mech_off[m].x;
+        const unsigned long long key = B.mech_key[m];
+        const uint32_t cnt = (uint32_t)(key & 0xFFull);
         if (cnt == 0u) { B.slot_of[m] = kNone; continue; }
         if (cnt > S) {
             report(B.status, GP_ERR_CAPACITY, 4u, m, cnt);
@@ -208,34 +290,31 @@ __global__ void __launch_bounds__(512, 4) group_kernel(Buffers B) {
         channel_ck(kind, c, k);
         float t = -log1pf(-c * p) / k;
         if (!(t < 1048576.0f)) t = 1048576.0f;     // q = 1/2 saturates P at 1/2
-        uint32_t col[kMaxMaskWords];
-        unsigned long long w[kMaxMaskWords];
-        load_sorted(B, m, col, w);
-        unsigned long long h = 0x243F6A8885A308D3ull;
-        // one mixing round per (column, word): collisions cost probes, never
-        // correctness (claims are verified on the full mask)
-        for (uint32_t i = 0; i < cnt; i++) h = mix64(h ^ w[i] ^ (0x9E3779B97F4A7C15ull * (col[i] + 1ull)));
-        h = weaken_hash(h, P.weak_hash);
-        const uint32_t key_hi = (uint32_t)(h >> 32);
-        const unsigned long long mine = ((unsigned long long)key_hi << 32) | m;
-        uint32_t pos = (uint32_t)h & cap_mask, slot = kNone;
-        for (uint32_t probe = 0; probe <= cap_mask; probe++) {
-            unsigned long long e = __ldcg(&B.table[pos].entry);
-            if (e == kEmpty) {
-                const unsigned long long old = atomicCAS(&B.table[pos].entry, kEmpty, mine);
-                if (old == kEmpty) {
-                    // the claim records the class's detector count
-                    uint32_t dets = 0;
-                    for (uint32_t i = 0; i < cnt; i++)
-                        if (!(col[i] & kObsColFlag)) dets += __popcll(w[i]);
-                    B.table[pos].cls = dets;
-                    slot = pos;
-                    break;
-                }
-                e = old;
-            }
-            if ((uint32_t)(e >> 32) == key_hi && same_mask(B, (uint32_t)e, cnt, col, w)) { slot = pos; break; }
-            pos = (pos + 1u) & cap_mask;
+        // collisions cost probes, never correctness (claims are verified on
+        // the whole mask)
+        const unsigned long long h = weaken_hash(mix64(key ^ 0x243F6A8885A308D3ull), P.weak_hash);
+        uint32_t slot;
+        if (cnt <= (uint32_t)kInlineWords) {
+            const uint4 c4 = *reinterpret_cast<const uint4 *>(&B.inl_col[(size_t)kInlineWords * m]);
+            const ulonglong2 w01 = *reinterpret_cast<const ulonglong2 *>(&B.inl_word[(size_t)kInlineWords * m]);
+            const ulonglong2 w23 = *reinterpret_cast<const ulonglong2 *>(&B.inl_word[(size_t)kInlineWords * m + 2]);
+            const uint32_t col[kInlineWords] = {c4.x, c4.y, c4.z, c4.w};
+            const unsigned long long w[kInlineWords] = {w01.x, w01.y, w23.x, w23.y};
+            uint32_t dets = 0;
+#pragma unroll
+            for (int i = 0; i < kInlineWords; i++)
+                if ((uint32_t)i < cnt && !(col[i] & kObsColFlag)) dets += __popcll(w[i]);
+            slot = claim_or_join(B, h, m, cap_mask, dets,
+                                 [&](uint32_t rep) { return same_mask_inline(B, rep, cnt, col, w); });
+        } else {
+            uint32_t col[kMaxMaskWords];
+            unsigned long long w[kMaxMaskWords];
+            load_words(B, m, cnt, col, w);
+            uint32_t dets = 0;
+            for (uint32_t i = 0; i < cnt; i++)
+                if (!(col[i] & kObsColFlag)) dets += __popcll(w[i]);
+            slot = claim_or_join(B, h, m, cap_mask, dets,
+                                 [&](uint32_t rep) { return same_mask(B, rep, cnt, col, w); });
         }
         if (slot == kNone) {
             report(B.status, GP_ERR_CAPACITY, 6u, m, cap_mask + 1u);
@@ -250,74 +329,118 @@ __global__ void __launch_bounds__(512, 4) group_kernel(Buffers B) {
     }
 }
 
-// leader flag and detector count of every mechanism: (1, the count the
-// class's claim left in its slot) for the smallest member of a class, else
-// (0, 0).  Four mechanisms per thread and round, their loads in flight
-// together.
-__global__ void leaders_kernel(Buffers B) {
+// ---- compaction scan: classes numbered by their smallest member ------------
+// Input of mechanism i: (1, the detector count its class's claim left in the
+// slot) when i is the smallest member of its class, else (0, 0).
+__device__ __forceinline__ uint2 leader_in(const Buffers &B, uint32_t i) {
+    const uint32_t slot = B.slot_of[i];
+    if (slot == kNone) return make_uint2(0u, 0u);
+    const uint2 mc = *reinterpret_cast<const uint2 *>(&B.table[slot].min);
+    return mc.x == i ? make_uint2(1u, mc.y) : make_uint2(0u, 0u);
+}
+
+__global__ void __launch_bounds__(kScanThreads) leader_reduce_kernel(Buffers B) {
     if (B.status->code != 0u) return;
-    const uint32_t N = B.status->n_mech;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t m0 = blockIdx.x * blockDim.x + threadIdx.x; m0 < N; m0 += 4u * stride) {
-        uint32_t slot[4];
+    const uint32_t n = B.status->n_mech;
+    const uint32_t b0 = blockIdx.x * kScanBlock;
+    if (b0 >= n) return;
+    uint2 v[kScanPer];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t m = m0 + u * stride;
-            slot[u] = m < N ? B.slot_of[m] : kNone;
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+        v[k] = i < n ? leader_in(B, i) : make_uint2(0u, 0u);
+    }
+    uint2 acc = make_uint2(0u, 0u);
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) acc = add2(acc, v[k]);
+    __shared__ uint32_t tmp[kScanThreads / 32];
+    uint2 tot;
+    block_scan2(acc, tmp, tot);
+    if (threadIdx.x == 0) B.scan_bsum[blockIdx.x] = tot;
+}
+
+// Each block adds up the sums of the blocks before it itself; every leader
+// gets its edge index (its rank) and detector offset: edge_mech[e] = leader,
+// det_off[e] = offset.  Block 0 writes the totals (edge count, detector
+// entries, det_off[E]) and checks them against the bounds.
+__global__ void __launch_bounds__(kScanThreads) leader_down_kernel(Buffers B) {
+    if (B.status->code != 0u) return;
+    const uint32_t n = B.status->n_mech;
+    const uint32_t b0 = blockIdx.x * kScanBlock;
+    const uint32_t nb = (n + kScanBlock - 1) / kScanBlock;
+    __shared__ uint32_t tmp[kScanThreads / 32];
+    if (blockIdx.x == 0) {
+        uint2 all = make_uint2(0, 0);
+        for (uint32_t i = threadIdx.x; i < nb; i += kScanThreads) all = add2(all, B.scan_bsum[i]);
+        uint2 tot;
+        block_scan2(all, tmp, tot);
+        if (threadIdx.x == 0) {
+            if ((unsigned long long)tot.y > B.params->max_det_entries) {
+                report(B.status, GP_ERR_CAPACITY, 7u, tot.y,
+                       (uint32_t)(B.params->max_det_entries > 0xFFFFFFFFull ? 0xFFFFFFFFull
+                                                                            : B.params->max_det_entries));
+            } else {
+                B.status->n_edges = tot.x;
+                B.status->n_det_entries = tot.y;
+                B.det_off[tot.x] = tot.y;
+            }
         }
-        uint2 mc[4];
+    }
+    if (b0 >= n) return;
+    uint2 before = make_uint2(0, 0);
+    for (uint32_t i = threadIdx.x; i < blockIdx.x; i += kScanThreads) before = add2(before, B.scan_bsum[i]);
+    uint2 prefix;
+    block_scan2(before, tmp, prefix);
+    uint2 v[kScanPer];
+    uint2 acc = make_uint2(0, 0);
 #pragma unroll
-        for (int u = 0; u < 4; u++)
-            mc[u] = slot[u] != kNone ? *reinterpret_cast<const uint2 *>(&B.table[slot[u]].min) : make_uint2(kNone, 0u);
+    for (int k = 0; k < kScanPer; k++) {
+        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+        v[k] = i < n ? leader_in(B, i) : make_uint2(0u, 0u);
+        acc = add2(acc, v[k]);
+    }
+    uint2 tot;
+    uint2 run = add2(block_scan2(acc, tmp, tot), prefix);
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t m = m0 + u * stride;
-            if (m < N) B.scan_val[m] = mc[u].x == m ? make_uint2(1u, mc[u].y) : make_uint2(0u, 0u);
+    for (int k = 0; k < kScanPer; k++) {
+        if (v[k].x) {
+            B.edge_mech[run.x] = b0 + threadIdx.x * kScanPer + k;
+            B.det_off[run.x] = run.y;
         }
+        run = add2(run, v[k]);
     }
 }
 
 __global__ void compact_write_kernel(Buffers B) {
     if (B.status->code != 0u) return;
-    const uint32_t N = B.status->n_mech;
-    const uint2 tot = B.comp_off[N];
-    if ((unsigned long long)tot.y > B.params->max_det_entries) {
-        if (blockIdx.x == 0 && threadIdx.x == 0)
-            report(B.status, GP_ERR_CAPACITY, 7u, tot.y,
-                   (uint32_t)(B.params->max_det_entries > 0xFFFFFFFFull ? 0xFFFFFFFFull : B.params->max_det_entries));
-        return;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        B.status->n_edges = tot.x;
-        B.status->n_det_entries = tot.y;
-        B.det_off[tot.x] = tot.y;
-    }
-    const uint32_t E = tot.x;
+    const uint32_t E = B.status->n_edges;
     const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
         const uint32_t e = base + threadIdx.x;
         uint32_t b = 0xFFFFFFFFu;
         if (e < E) {
             const uint32_t m = B.edge_mech[e];
-            const uint32_t d0 = B.comp_off[m].y;
-            uint32_t d = d0;
+            uint32_t d = B.det_off[e];
             const uint32_t slot = B.slot_of[m];
             const unsigned long long info = B.mech_info[m];
             b = (uint32_t)(info >> 48);
             const uint32_t col_base = B.circ[b].col_base;
-            const uint32_t o0 = B.mech_off[m].x, cnt = B.mech_off[m + 1].x - o0;
+            const uint32_t cnt = (uint32_t)(B.mech_key[m] & 0xFFull);
+            uint32_t col[kMaxMaskWords];
+            unsigned long long w[kMaxMaskWords];
+            load_words(B, m, cnt, col, w);
             unsigned long long obs = 0ull;
-            // words in ascending column order (selection over the range), so
-            // the detector ids come out ascending
+            // words in ascending column order (selection), so the detector
+            // ids come out ascending
             uint32_t prev = 0u;
             for (uint32_t k = 0; k < cnt; k++) {
                 uint32_t cmin = 0xFFFFFFFFu, jmin = 0u;
                 for (uint32_t j = 0; j < cnt; j++) {
-                    const uint32_t c = B.slot_col[o0 + j];
+                    const uint32_t c = col[j];
                     if ((k == 0u || c > prev) && c < cmin) { cmin = c; jmin = j; }
                 }
                 prev = cmin;
-                unsigned long long x = B.slot_word[o0 + jmin];
+                unsigned long long x = w[jmin];
                 if (cmin & kObsColFlag) { obs ^= x; continue; }
                 const uint32_t base_id = (cmin - col_base) * 64u;
                 while (x) {
@@ -329,7 +452,6 @@ __global__ void compact_write_kernel(Buffers B) {
             const TabSlot &ts = B.table[slot];
             const float T = fixed_to_float(ts.acc_lo, ts.acc_hi, kProbShift);
             const float Pc = -0.5f * expm1f(-T);
-            B.det_off[e] = d0;
             B.obs_mask[e] = obs;
             B.prob[e] = Pc;
             B.logodds[e] = log1pf(-Pc) - logf(Pc);
@@ -343,21 +465,23 @@ __global__ void compact_write_kernel(Buffers B) {
     }
 }
 
-// per-mechanism class ids (i < N), used table slots cleared (i < E):
-// disjoint fields (cls is read, the others are cleared), one pass; four
-// indices per thread and round, their loads in flight together
+// per-mechanism class ids and cleared keys (i < N), used table slots cleared
+// (i < E), overflow heads reset (i < overflow words): disjoint fields, one
+// pass; four indices per thread and round, their loads in flight together
 __global__ void finalize_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const uint32_t N = B.status->n_mech, E = B.status->n_edges;
-    const uint32_t M = max(N, E);
+    const uint32_t OV = min(B.status->ov_count, B.params->ov_cap);
+    const uint32_t M = max(max(N, E), OV);
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += 4u * stride) {
-        uint32_t slot[4], cs[4];
+        uint32_t slot[4], cs[4], om[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const uint32_t i = i0 + u * stride;
             slot[u] = i < N ? B.slot_of[i] : kNone;
             cs[u] = i < E ? B.class_slot[i] : kNone;
+            om[u] = i < OV ? B.ov_mech[i] : kNone;
         }
         uint32_t cls[4];
 #pragma unroll
@@ -365,7 +489,11 @@ __global__ void finalize_kernel(Buffers B) {
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const uint32_t i = i0 + u * stride;
-            if (i < N) B.mech_class[i] = slot[u] == kNone ? -1 : (int32_t)cls[u];
+            if (i < N) {
+                B.mech_class[i] = slot[u] == kNone ? -1 : (int32_t)cls[u];
+                B.mech_key[i] = 0ull;
+            }
+            if (om[u] != kNone) B.ov_head[om[u]] = kNone;
         }
         // cls is left alone: other threads may still be reading it (a claim
         // overwrites it in the next compile)
@@ -425,27 +553,20 @@ __global__ void init_table_kernel(TabSlot *t, size_t n) {
 }  // namespace
 
 // exclusive scan of n (read on the device) uint2 values: out[i] = sum of
-// in[0..i), out[n] = the total; blocks of 2048 values, two passes.  With
-// in == nullptr the values are (cnt[i], 0); with a list, the indices whose
-// first channel is 1 are listed in order.
-void launch_scan_counts(const Buffers &B, const uint2 *in, const uint32_t *cnt, const uint32_t *n_ptr, uint2 *out,
-                        uint32_t max_n, cudaStream_t s, uint32_t *launches, uint32_t *list = nullptr) {
-    const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
-    const uint32_t grid1 = g1 ? g1 : 1u;
-    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, B.status);
-    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, cnt, n_ptr, B.scan_bsum, out, list, B.status);
-    *launches += 2;
-}
-
+// in[0..i), out[n] = the total; blocks of 2048 values, two passes (the
+// server's selection scans)
 void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
                  cudaStream_t s, uint32_t *launches) {
-    launch_scan_counts(B, in, nullptr, n_ptr, out, max_n, s, launches);
+    const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
+    const uint32_t grid1 = g1 ? g1 : 1u;
+    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, nullptr, n_ptr, B.scan_bsum, B.status);
+    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, nullptr, n_ptr, B.scan_bsum, out, nullptr, B.status);
+    *launches += 2;
 }
 
 void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
                   uint32_t *launches) {
-    // offsets of the per-mechanism word ranges: scan of the word counts
-    launch_scan_counts(b, nullptr, b.mech_cnt, &b.status->n_mech, b.mech_off, max_mech, s, launches);
+    (void)max_mech;
     scatter_kernel<<<grid, threads, 0, s>>>(b);
     group_kernel<<<grid, threads, 0, s>>>(b);
     *launches += 2;
@@ -453,11 +574,13 @@ void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t ma
 
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
                     uint32_t *launches) {
-    leaders_kernel<<<grid, threads, 0, s>>>(b);
-    launch_scan_counts(b, b.scan_val, nullptr, &b.status->n_mech, b.comp_off, max_mech, s, launches, b.edge_mech);
+    const uint32_t g1 = (max_mech + kScanBlock - 1) / kScanBlock;
+    const uint32_t grid1 = g1 ? g1 : 1u;
+    leader_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(b);
+    leader_down_kernel<<<grid1, kScanThreads, 0, s>>>(b);
     compact_write_kernel<<<grid, threads, 0, s>>>(b);
     finalize_kernel<<<grid, threads, 0, s>>>(b);
-    *launches += 3;
+    *launches += 4;
 }
 
 void launch_backward(const Buffers &b, const float *g_prob, const float *g_logodds, float *g_noise,
