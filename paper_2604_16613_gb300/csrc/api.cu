@@ -204,6 +204,7 @@ struct gp_driver {
 
 namespace gpdem {
 const Buffers &driver_buffers(const gp_driver *d) { return d->B; }
+uint32_t driver_sms(const gp_driver *d) { return (uint32_t)d->n_sms; }
 uint32_t driver_max_det_entries(const gp_driver *d) {
     return (uint32_t)std::min<uint64_t>(d->L.max_det_entries, 0xFFFFFFFFull);
 }
@@ -291,13 +292,13 @@ gp_status enqueue_pipeline(gp_driver *d, cudaStream_t s, uint32_t *kernels) {
     const uint32_t grid1 = std::min<uint32_t>((uint32_t)d->n_sms * bps, std::max<uint32_t>(L.max_cols, 1u));
     GP_CUDA(cudaMemcpyAsync(d->B.params, d->h_params, d->params_bytes, cudaMemcpyHostToDevice, s));
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[0], s, cudaEventRecordExternal));
-    launch_lowering(d->B, L.max_tiles, L.max_layer_slots, bd.max_qubits, s, kernels);
+    launch_lowering(d->B, L.max_tiles, L.max_layer_slots, bd.max_qubits, (uint32_t)d->n_sms, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[1], s, cudaEventRecordExternal));
     launch_stage1(d->B, grid1, d->tuning.stage1_threads, bd.max_qubits, shape1, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[2], s, cudaEventRecordExternal));
     launch_group(d->B, grid2, d->tuning.stage2_threads, bd.max_mechanisms, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[3], s, cudaEventRecordExternal));
-    launch_compact(d->B, grid2, d->tuning.stage2_threads, bd.max_mechanisms, s, kernels);
+    launch_compact(d->B, grid2, d->tuning.stage2_threads, bd.max_mechanisms, (uint32_t)d->n_sms, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[4], s, cudaEventRecordExternal));
     GP_CUDA(cudaGetLastError());
     GP_CUDA(cudaMemcpyAsync(d->h_status, d->B.status, sizeof(Status), cudaMemcpyDeviceToHost, s));

@@ -443,8 +443,8 @@ struct CopyJob {
     uint64_t bytes;
 };
 void launch_gather_host(const CopyJob *jobs, uint32_t n_jobs, uint64_t max_bytes, uint32_t n_sms, cudaStream_t s);
-void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, cudaStream_t s,
-                     uint32_t *launches);
+void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, uint32_t n_sms,
+                     cudaStream_t s, uint32_t *launches);
 cudaError_t lowering_setup(uint32_t max_qubits);
 // shared-memory shape of the stage-1 walk: window buffers, list entries a
 // buffer holds, bytes of a buffer and of the whole block, and which walk
@@ -462,12 +462,14 @@ void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t m
                    cudaStream_t s, uint32_t *launches);
 const void *stage1_kernel_ptr(uint32_t threads, uint32_t split);
 void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
-void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
+void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, uint32_t n_sms, cudaStream_t s,
+                    uint32_t *launches);
 void launch_init_table(TabSlot *t, size_t n, cudaStream_t s);
 // the device buffers of a driver (for the server's selection kernels)
 const Buffers &driver_buffers(const gp_driver *d);
 uint32_t driver_max_det_entries(const gp_driver *d);
-void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
+uint32_t driver_sms(const gp_driver *d);      // SMs of the driver's device
+void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n, uint32_t n_sms,
                  cudaStream_t s, uint32_t *launches);
 void launch_backward(const Buffers &b, const float *g_prob, const float *g_logodds, float *g_noise,
                      uint32_t n_mech, uint32_t n_loc, uint32_t grid, uint32_t threads, cudaStream_t s, uint32_t *launches);

@@ -2,7 +2,8 @@
 // realised circuit is lowered to a layered space-time structure before the
 // backward wave runs).
 //
-// Four launches, no device-wide waits:
+// Four launches, no device-wide waits (grid-stride loops, grids capped by the
+// SM count):
 //   tile_count   per tile of 512 rows: counts of TICKs, measurements,
 //                detectors and mechanisms (components at the chosen level)
 //   tile_scan    one block: per-circuit scan of the tile counts, circuit
@@ -45,10 +46,11 @@ __device__ __forceinline__ uint4 sub4(uint4 a, uint4 b) {
     return make_uint4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
 
-__global__ void __launch_bounds__(kLowerThreads) tile_count_kernel(Buffers B) {
-    const Params &P = *B.params;
-    const uint32_t t = blockIdx.x;
-    if (t >= P.n_tiles) return;
+// Tiles, layer slots and scan chunks are visited by grid-stride loops whose
+// trip counts depend only on blockIdx and the compile's sizes, so every
+// block-wide barrier inside them (including status_set's) is reached by the
+// whole block; grids are capped by the SM count, not by the driver's bounds.
+__device__ __forceinline__ void tile_count_one(const Buffers &B, const Params &P, uint32_t t, uint4 *red) {
     const uint2 tile = B.tiles[t];
     const CircuitDev &C = B.circ[tile.x];
     const uint32_t r0 = tile.y + threadIdx.x * kRowsPerThread;
@@ -56,7 +58,6 @@ __global__ void __launch_bounds__(kLowerThreads) tile_count_kernel(Buffers B) {
     uint4 acc = make_uint4(0, 0, 0, 0);
     for (uint32_t r = r0; r < r1; r++) acc = add4(acc, row_counts(C.ops[r], P.level));
     // block reduction of four counters
-    __shared__ uint4 red[kLowerThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xFFFFFFFFu, acc.x, o);
@@ -71,6 +72,14 @@ __global__ void __launch_bounds__(kLowerThreads) tile_count_kernel(Buffers B) {
         for (int w = 0; w < kLowerThreads / 32; w++) s = add4(s, red[w]);
         B.tile_sums[t] = s;
     }
+    __syncthreads();           // red is reused by the block's next tile
+}
+
+__global__ void __launch_bounds__(kLowerThreads) tile_count_kernel(Buffers B) {
+    const Params &P = *B.params;
+    __shared__ uint4 red[kLowerThreads / 32];
+    for (uint32_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x)
+        tile_count_one(B, P, t, red);
 }
 
 // block-wide exclusive scans of a uint4 (four channels at once) and of a
@@ -210,11 +219,7 @@ __global__ void __launch_bounds__(kLowerThreads) tile_scan_kernel(Buffers B) {
     }
 }
 
-__global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
-    const Params &P = *B.params;
-    const uint32_t t = blockIdx.x;
-    if (t >= P.n_tiles) return;
-    if (status_set(B.status)) return;
+__device__ __forceinline__ void tile_lower_one(const Buffers &B, const Params &P, uint32_t t, uint32_t *warp_tmp) {
     const uint2 tile = B.tiles[t];
     const uint32_t b = tile.x;
     const CircuitDev &C = B.circ[b];
@@ -222,7 +227,6 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
     const uint32_t r1 = min(r0 + kRowsPerThread, C.n_ops);
     uint4 mine = make_uint4(0, 0, 0, 0);
     for (uint32_t r = r0; r < r1; r++) mine = add4(mine, row_counts(C.ops[r], P.level));
-    __shared__ uint32_t warp_tmp[kLowerThreads / 32];
     uint32_t tot;
     const uint4 toff = sub4(B.tile_off[t], B.tile_off[C.tile_first]);
     uint4 run;
@@ -290,6 +294,15 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
     }
 }
 
+__global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
+    const Params &P = *B.params;
+    __shared__ uint32_t warp_tmp[kLowerThreads / 32];
+    for (uint32_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x) {
+        if (status_set(B.status)) return;      // the whole block, every iteration
+        tile_lower_one(B, P, t, warp_tmp);
+    }
+}
+
 // One block per layer slot.  Slots are numbered across the batch; circuit b
 // owns slots [layer_base, layer_base + n_layers] (the last one is the end
 // sentinel, which has no rows).
@@ -298,11 +311,8 @@ __global__ void __launch_bounds__(kLowerThreads) tile_lower_kernel(Buffers B) {
 // lengths, after-gate entries in the low half and before-gate entries in
 // the high half (a layer has at most kMaxLayerRows rows, so neither half
 // can carry into the other), later turned into fill positions.
-__global__ void __launch_bounds__(kPackThreads) layer_index_kernel(Buffers B) {
-    extern __shared__ uint32_t lsm[];
-    const Params &P = *B.params;
-    if (status_set(B.status)) return;
-    const uint32_t g = blockIdx.x;
+__device__ __forceinline__ void layer_index_one(const Buffers &B, const Params &P, uint32_t g, uint32_t *lsm,
+                                                uint32_t *warp_tmp) {
     // circuit owning slot g (circuits are laid out in slot order)
     uint32_t lo = 0, hi = P.n_circuits;
     while (hi - lo > 1) {
@@ -361,7 +371,6 @@ __global__ void __launch_bounds__(kPackThreads) layer_index_kernel(Buffers B) {
     __syncthreads();
     // exclusive scan of the packed counts: each thread a contiguous run of
     // qubits, one block scan over the runs
-    __shared__ uint32_t warp_tmp[kPackThreads / 32];
     const uint32_t per = (nq + kPackThreads - 1) / kPackThreads;
     const uint32_t q0 = min(threadIdx.x * per, nq), q1 = min(q0 + per, nq);
     uint32_t local = 0;
@@ -425,6 +434,21 @@ __global__ void __launch_bounds__(kPackThreads) layer_index_kernel(Buffers B) {
     }
 }
 
+__global__ void __launch_bounds__(kPackThreads) layer_index_kernel(Buffers B) {
+    extern __shared__ uint32_t lsm[];
+    __shared__ uint32_t warp_tmp[kPackThreads / 32];
+    const Params &P = *B.params;
+    // slots of the whole batch: those of the last circuit end it
+    const CircuitDev &last = B.circ[P.n_circuits - 1u];
+    const uint32_t n_slots = last.layer_base + last.n_layers + 1u;
+    for (uint32_t g = blockIdx.x; g < n_slots; g += gridDim.x) {
+        // the whole block, every iteration: the barriers also separate one
+        // slot's use of the shared arrays from the next one's
+        if (status_set(B.status)) return;
+        layer_index_one(B, P, g, lsm, warp_tmp);
+    }
+}
+
 // Host arrays gathered into device arenas by the GPU itself, through the
 // coherent host memory of a Grace-Blackwell node (pageable memory is
 // addressable from the device there): block (x, j) copies its share of job
@@ -461,13 +485,17 @@ void launch_gather_host(const CopyJob *jobs, uint32_t n_jobs, uint64_t max_bytes
     gather_host_kernel<<<dim3(gx, n_jobs), 256, 0, s>>>(jobs, n_jobs);
 }
 
-void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, cudaStream_t s,
-                     uint32_t *launches) {
-    const uint32_t grid = n_tiles ? n_tiles : 1u;
+void launch_lowering(const Buffers &b, uint32_t n_tiles, uint32_t layer_slots, uint32_t max_qubits, uint32_t n_sms,
+                     cudaStream_t s, uint32_t *launches) {
+    // grid-stride kernels: at most eight blocks per SM, fewer when the
+    // bounds allow fewer tiles or layer slots
+    const uint32_t cap = 8u * std::max(n_sms, 1u);
+    const uint32_t grid = std::max(1u, std::min(n_tiles, cap));
+    const uint32_t grid_l = std::max(1u, std::min(layer_slots, cap));
     tile_count_kernel<<<grid, kLowerThreads, 0, s>>>(b);
     tile_scan_kernel<<<1, kLowerThreads, 0, s>>>(b);
     tile_lower_kernel<<<grid, kLowerThreads, 0, s>>>(b);
-    layer_index_kernel<<<layer_slots, kPackThreads, 2u * max_qubits * sizeof(uint32_t), s>>>(b);
+    layer_index_kernel<<<grid_l, kPackThreads, 2u * max_qubits * sizeof(uint32_t), s>>>(b);
     *launches += 4;
 }
 

@@ -1002,7 +1002,7 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
             uint32_t launches = 0;
             for (uint32_t r = 0; r < n_pass; r++) {
                 seal_flags_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->d_cyc_tab, s->W + 1u, r);
-                launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, st, &launches);
+                launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, driver_sms(s->drv), st, &launches);
                 slot_starts_kernel<<<1, 256, 0, st>>>(B, n_win, s->d_win_e0, r, s->d_starts, s->out.doff);
                 seal_write_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->out, s->d_starts + (size_t)r * rs, r, n_win);
             }

@@ -30,6 +30,8 @@
 //              summed per noise location in fixed point
 // Every grid is fixed by the driver's bounds, so the whole sequence can be
 // captured once and replayed.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gpdem {
@@ -52,41 +54,37 @@ __device__ __forceinline__ uint2 block_scan2(uint2 v, uint32_t *tmp, uint2 &tota
 }
 
 // ---- hierarchical exclusive scan of uint2 values ---------------------------
-// level 1: per block of 2048 values, the sum
-// (in == nullptr: the values are the word counts `cnt`, second channel 0)
-__device__ __forceinline__ uint2 scan_in(const uint2 *in, const uint32_t *cnt, uint32_t i) {
-    return in ? in[i] : make_uint2(cnt[i], 0u);
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint2 *in, const uint32_t *cnt,
-                                                                   const uint32_t *n_ptr, uint2 *bsum,
-                                                                   const Status *st) {
+// Chunks of kScanBlock values; each block takes chunks blockIdx.x,
+// blockIdx.x + gridDim.x, ... (trip counts uniform over the block, so the
+// barriers of the block scans are reached by every thread), and the grid is
+// capped by the SM count rather than sized by the driver's bounds.
+// Pass 1: the sum of every chunk.
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint2 *in, const uint32_t *n_ptr,
+                                                                   uint2 *bsum, const Status *st) {
     if (st->code != 0u) return;
     const uint32_t n = *n_ptr;
-    const uint32_t b0 = blockIdx.x * kScanBlock;
-    if (b0 >= n) return;
-    uint2 acc = make_uint2(0, 0);
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
-        if (i < n) acc = add2(acc, scan_in(in, cnt, i));
-    }
+    const uint32_t nb = (n + kScanBlock - 1) / kScanBlock;
     __shared__ uint32_t tmp[kScanThreads / 32];
-    uint2 tot;
-    block_scan2(acc, tmp, tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    for (uint32_t c = blockIdx.x; c < nb; c += gridDim.x) {
+        const uint32_t b0 = c * kScanBlock;
+        uint2 acc = make_uint2(0, 0);
+        for (int k = 0; k < kScanPer; k++) {
+            const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+            if (i < n) acc = add2(acc, in[i]);
+        }
+        uint2 tot;
+        block_scan2(acc, tmp, tot);
+        if (threadIdx.x == 0) bsum[c] = tot;
+    }
 }
 
-// level 2: exclusive prefix of every value.  Each block adds up the sums of
-// the blocks before it itself (a few hundred values), so no separate pass
-// scans the block sums; block 0 also writes out[n] = the total.  With a
-// list, the first channel is a 0/1 flag and every flagged index i is listed
-// at its rank: list[out[i].x] = i.
-__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in, const uint32_t *cnt,
-                                                                 const uint32_t *n_ptr, const uint2 *bsum,
-                                                                 uint2 *out, uint32_t *list, const Status *st) {
+// Pass 2: exclusive prefix of every value.  Each chunk adds up the sums of
+// the chunks before it itself (a few hundred values), so no separate pass
+// scans the chunk sums; block 0 also writes out[n] = the total.
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in, const uint32_t *n_ptr,
+                                                                 const uint2 *bsum, uint2 *out, const Status *st) {
     if (st->code != 0u) return;
     const uint32_t n = *n_ptr;
-    const uint32_t b0 = blockIdx.x * kScanBlock;
     const uint32_t nb = (n + kScanBlock - 1) / kScanBlock;
     __shared__ uint32_t tmp[kScanThreads / 32];
     if (blockIdx.x == 0) {
@@ -96,27 +94,26 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint2 *in
         block_scan2(all, tmp, tot);
         if (threadIdx.x == 0) out[n] = tot;
     }
-    if (b0 >= n) return;
-    uint2 before = make_uint2(0, 0);
-    for (uint32_t i = threadIdx.x; i < blockIdx.x; i += kScanThreads) before = add2(before, bsum[i]);
-    uint2 prefix;
-    block_scan2(before, tmp, prefix);
-    uint2 v[kScanPer];
-    uint2 acc = make_uint2(0, 0);
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
-        v[k] = i < n ? scan_in(in, cnt, i) : make_uint2(0, 0);
-        acc = add2(acc, v[k]);
-    }
-    uint2 tot;
-    uint2 run = add2(block_scan2(acc, tmp, tot), prefix);
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
-        if (i < n) {
-            out[i] = run;
-            if (list && v[k].x) list[run.x] = i;
+    for (uint32_t c = blockIdx.x; c < nb; c += gridDim.x) {
+        const uint32_t b0 = c * kScanBlock;
+        uint2 before = make_uint2(0, 0);
+        for (uint32_t i = threadIdx.x; i < c; i += kScanThreads) before = add2(before, bsum[i]);
+        uint2 prefix;
+        block_scan2(before, tmp, prefix);
+        uint2 v[kScanPer];
+        uint2 acc = make_uint2(0, 0);
+        for (int k = 0; k < kScanPer; k++) {
+            const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+            v[k] = i < n ? in[i] : make_uint2(0, 0);
+            acc = add2(acc, v[k]);
         }
-        run = add2(run, v[k]);
+        uint2 tot;
+        uint2 run = add2(block_scan2(acc, tmp, tot), prefix);
+        for (int k = 0; k < kScanPer; k++) {
+            const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+            if (i < n) out[i] = run;
+            run = add2(run, v[k]);
+        }
     }
 }
 
@@ -342,31 +339,38 @@ __device__ __forceinline__ uint2 leader_in(const Buffers &B, uint32_t i) {
 __global__ void __launch_bounds__(kScanThreads) leader_reduce_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const uint32_t n = B.status->n_mech;
-    const uint32_t b0 = blockIdx.x * kScanBlock;
-    if (b0 >= n) return;
-    uint2 v[kScanPer];
-#pragma unroll
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
-        v[k] = i < n ? leader_in(B, i) : make_uint2(0u, 0u);
-    }
-    uint2 acc = make_uint2(0u, 0u);
-#pragma unroll
-    for (int k = 0; k < kScanPer; k++) acc = add2(acc, v[k]);
+    const uint32_t nb = (n + kScanBlock - 1) / kScanBlock;
     __shared__ uint32_t tmp[kScanThreads / 32];
-    uint2 tot;
-    block_scan2(acc, tmp, tot);
-    if (threadIdx.x == 0) B.scan_bsum[blockIdx.x] = tot;
+    for (uint32_t c = blockIdx.x; c < nb; c += gridDim.x) {
+        const uint32_t b0 = c * kScanBlock;
+        uint2 v[kScanPer];
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+            v[k] = i < n ? leader_in(B, i) : make_uint2(0u, 0u);
+        }
+        uint2 acc = make_uint2(0u, 0u);
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) acc = add2(acc, v[k]);
+        // the inputs, once, for the second pass (coalesced 8-byte writes)
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+            if (i < n) B.scan_val[i] = v[k];
+        }
+        uint2 tot;
+        block_scan2(acc, tmp, tot);
+        if (threadIdx.x == 0) B.scan_bsum[c] = tot;
+    }
 }
 
-// Each block adds up the sums of the blocks before it itself; every leader
+// Each chunk adds up the sums of the chunks before it itself; every leader
 // gets its edge index (its rank) and detector offset: edge_mech[e] = leader,
 // det_off[e] = offset.  Block 0 writes the totals (edge count, detector
 // entries, det_off[E]) and checks them against the bounds.
 __global__ void __launch_bounds__(kScanThreads) leader_down_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const uint32_t n = B.status->n_mech;
-    const uint32_t b0 = blockIdx.x * kScanBlock;
     const uint32_t nb = (n + kScanBlock - 1) / kScanBlock;
     __shared__ uint32_t tmp[kScanThreads / 32];
     if (blockIdx.x == 0) {
@@ -386,28 +390,30 @@ __global__ void __launch_bounds__(kScanThreads) leader_down_kernel(Buffers B) {
             }
         }
     }
-    if (b0 >= n) return;
-    uint2 before = make_uint2(0, 0);
-    for (uint32_t i = threadIdx.x; i < blockIdx.x; i += kScanThreads) before = add2(before, B.scan_bsum[i]);
-    uint2 prefix;
-    block_scan2(before, tmp, prefix);
-    uint2 v[kScanPer];
-    uint2 acc = make_uint2(0, 0);
+    for (uint32_t c = blockIdx.x; c < nb; c += gridDim.x) {
+        const uint32_t b0 = c * kScanBlock;
+        uint2 before = make_uint2(0, 0);
+        for (uint32_t i = threadIdx.x; i < c; i += kScanThreads) before = add2(before, B.scan_bsum[i]);
+        uint2 prefix;
+        block_scan2(before, tmp, prefix);
+        uint2 v[kScanPer];
+        uint2 acc = make_uint2(0, 0);
 #pragma unroll
-    for (int k = 0; k < kScanPer; k++) {
-        const uint32_t i = b0 + threadIdx.x * kScanPer + k;
-        v[k] = i < n ? leader_in(B, i) : make_uint2(0u, 0u);
-        acc = add2(acc, v[k]);
-    }
-    uint2 tot;
-    uint2 run = add2(block_scan2(acc, tmp, tot), prefix);
-#pragma unroll
-    for (int k = 0; k < kScanPer; k++) {
-        if (v[k].x) {
-            B.edge_mech[run.x] = b0 + threadIdx.x * kScanPer + k;
-            B.det_off[run.x] = run.y;
+        for (int k = 0; k < kScanPer; k++) {
+            const uint32_t i = b0 + threadIdx.x * kScanPer + k;
+            v[k] = i < n ? B.scan_val[i] : make_uint2(0u, 0u);
+            acc = add2(acc, v[k]);
         }
-        run = add2(run, v[k]);
+        uint2 tot;
+        uint2 run = add2(block_scan2(acc, tmp, tot), prefix);
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            if (v[k].x) {
+                B.edge_mech[run.x] = b0 + threadIdx.x * kScanPer + k;
+                B.det_off[run.x] = run.y;
+            }
+            run = add2(run, v[k]);
+        }
     }
 }
 
@@ -465,42 +471,52 @@ __global__ void compact_write_kernel(Buffers B) {
     }
 }
 
-// per-mechanism class ids and cleared keys (i < N), used table slots cleared
-// (i < E), overflow heads reset (i < overflow words): disjoint fields, one
-// pass; four indices per thread and round, their loads in flight together
+// per-mechanism class ids and cleared keys (four consecutive mechanisms per
+// thread: one 16-byte load of their slots, one 16-byte store of their ids,
+// two of their keys), used table slots cleared (one edge per thread),
+// overflow heads reset: disjoint fields, one pass
 __global__ void finalize_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const uint32_t N = B.status->n_mech, E = B.status->n_edges;
     const uint32_t OV = min(B.status->ov_count, B.params->ov_cap);
-    const uint32_t M = max(max(N, E), OV);
+    const uint32_t N4 = (N + 3u) / 4u;
+    const uint32_t M = max(max(N4, E), OV);
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += 4u * stride) {
-        uint32_t slot[4], cs[4], om[4];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const uint32_t cs = i < E ? B.class_slot[i] : kNone;
+        const uint32_t om = i < OV ? B.ov_mech[i] : kNone;
+        if (i < N4) {
+            const bool full = 4u * i + 3u < N;
+            uint32_t sl[4];
+            if (full) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(&B.slot_of[4u * i]);
+                sl[0] = v.x; sl[1] = v.y; sl[2] = v.z; sl[3] = v.w;
+            } else {
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t i = i0 + u * stride;
-            slot[u] = i < N ? B.slot_of[i] : kNone;
-            cs[u] = i < E ? B.class_slot[i] : kNone;
-            om[u] = i < OV ? B.ov_mech[i] : kNone;
-        }
-        uint32_t cls[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) cls[u] = slot[u] != kNone ? B.table[slot[u]].cls : 0u;
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t i = i0 + u * stride;
-            if (i < N) {
-                B.mech_class[i] = slot[u] == kNone ? -1 : (int32_t)cls[u];
-                B.mech_key[i] = 0ull;
+                for (int u = 0; u < 4; u++) sl[u] = 4u * i + u < N ? B.slot_of[4u * i + u] : kNone;
             }
-            if (om[u] != kNone) B.ov_head[om[u]] = kNone;
+            int32_t cl[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) cl[u] = sl[u] == kNone ? -1 : (int32_t)B.table[sl[u]].cls;
+            if (full) {
+                *reinterpret_cast<int4 *>(&B.mech_class[4u * i]) = make_int4(cl[0], cl[1], cl[2], cl[3]);
+                ulonglong2 *k2 = reinterpret_cast<ulonglong2 *>(&B.mech_key[4u * i]);
+                k2[0] = make_ulonglong2(0ull, 0ull);
+                k2[1] = make_ulonglong2(0ull, 0ull);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (4u * i + u < N) {
+                        B.mech_class[4u * i + u] = cl[u];
+                        B.mech_key[4u * i + u] = 0ull;
+                    }
+            }
         }
+        if (om != kNone) B.ov_head[om] = kNone;
         // cls is left alone: other threads may still be reading it (a claim
         // overwrites it in the next compile)
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            if (cs[u] == kNone) continue;
-            TabSlot &ts = B.table[cs[u]];
+        if (cs != kNone) {
+            TabSlot &ts = B.table[cs];
             ts.entry = kEmpty;
             ts.min = kNone;
             *reinterpret_cast<uint4 *>(&ts.acc_lo) = make_uint4(0u, 0u, 0u, 0u);   // acc_lo, acc_hi
@@ -553,14 +569,18 @@ __global__ void init_table_kernel(TabSlot *t, size_t n) {
 }  // namespace
 
 // exclusive scan of n (read on the device) uint2 values: out[i] = sum of
-// in[0..i), out[n] = the total; blocks of 2048 values, two passes (the
+// in[0..i), out[n] = the total; chunks of 2048 values, two passes (the
 // server's selection scans)
-void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n,
+static uint32_t scan_grid(uint32_t max_n, uint32_t n_sms) {
+    const uint32_t chunks = (max_n + kScanBlock - 1) / kScanBlock;
+    return std::max(1u, std::min(chunks, 8u * std::max(n_sms, 1u)));
+}
+
+void launch_scan(const Buffers &B, const uint2 *in, const uint32_t *n_ptr, uint2 *out, uint32_t max_n, uint32_t n_sms,
                  cudaStream_t s, uint32_t *launches) {
-    const uint32_t g1 = (max_n + kScanBlock - 1) / kScanBlock;
-    const uint32_t grid1 = g1 ? g1 : 1u;
-    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, nullptr, n_ptr, B.scan_bsum, B.status);
-    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, nullptr, n_ptr, B.scan_bsum, out, nullptr, B.status);
+    const uint32_t grid1 = scan_grid(max_n, n_sms);
+    scan_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, B.status);
+    scan_down_kernel<<<grid1, kScanThreads, 0, s>>>(in, n_ptr, B.scan_bsum, out, B.status);
     *launches += 2;
 }
 
@@ -572,10 +592,9 @@ void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t ma
     *launches += 2;
 }
 
-void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s,
-                    uint32_t *launches) {
-    const uint32_t g1 = (max_mech + kScanBlock - 1) / kScanBlock;
-    const uint32_t grid1 = g1 ? g1 : 1u;
+void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, uint32_t n_sms,
+                    cudaStream_t s, uint32_t *launches) {
+    const uint32_t grid1 = scan_grid(max_mech, n_sms);
     leader_reduce_kernel<<<grid1, kScanThreads, 0, s>>>(b);
     leader_down_kernel<<<grid1, kScanThreads, 0, s>>>(b);
     compact_write_kernel<<<grid, threads, 0, s>>>(b);
