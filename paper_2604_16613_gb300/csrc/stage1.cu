@@ -697,7 +697,11 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
 // publishes for each step a snapshot of its active qubits' planes; the other
 // warps (emitters) evaluate the noise rows of a step from that snapshot while
 // the walker is already on the next one; the last warp stages the layer
-// windows.  The snapshot tables are double-buffered by step parity and
+// windows.  From 512 threads a second walker warp (four from 1024) waits on a
+// named barrier and joins only the steps of more than 64 candidates, which
+// warp 0 hands to it: the long chain of small steps (an observable's walk)
+// keeps its single-warp latency, and the wide steps of detector columns are
+// undone in parallel.  The snapshot tables are double-buffered by step parity and
 // tagged with the step that wrote an entry (a qubit whose tag differs is not
 // active in that step), so they are never cleared.  mbarriers order the
 // roles: window full (producer -> walker), window free (walker, emitters ->
@@ -717,6 +721,11 @@ struct SplitSmem {
     unsigned char *bits;            // walker: kActive / kAdded / 0 per qubit
     unsigned char *win;             // window buffers
 };
+
+// Warps of a block: the first warps walk (two from 512 threads, four from
+// 1024), the last warp stages windows, the rest emit.
+__host__ __device__ constexpr uint32_t split_walkers(uint32_t nt) { return nt >= 1024u ? 4u : (nt >= 512u ? 2u : 1u); }
+__host__ __device__ constexpr uint32_t split_emitters(uint32_t nt) { return nt / 32u - 1u - split_walkers(nt); }
 
 __host__ __device__ inline size_t split_base_bytes(uint32_t maxq) {
     const size_t q8 = round8(maxq);
@@ -763,6 +772,15 @@ struct StepDesc {
     uint32_t end;       // 1: no step; the column is done
 };
 
+// a large step of the walk, as warp 0 hands it to the helper walker warps
+struct WalkStep {
+    int L;
+    uint32_t n_prev, n_cand, slot;
+    uint16_t *ab;
+    const uint16_t *prev;
+    uint32_t b, snap, stamp, cmd;     // cmd 0: the walk is over
+};
+
 struct SplitShared {
     unsigned long long win_full[kMaxBufs], win_free[kMaxBufs];
     unsigned long long tab_full[2], tab_free[2];
@@ -773,6 +791,8 @@ struct SplitShared {
     uint32_t walk_done;     // the walker left the column (the producer stops)
     int stop_layer;         // last layer the walker stepped through
     int posted_lo;          // lowest window the producer posted
+    WalkStep wstep;         // warp 0 -> helper walker warps: the large step
+    uint32_t wcnt[2];       // large step: {active, added}
 };
 
 template <int NT>
@@ -782,8 +802,9 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
     const SplitSmem s = split_carve(smem_raw, maxq);
     __shared__ SplitShared sh;
     constexpr uint32_t NW = NT / 32;
-    constexpr uint32_t NE = NW - 2;                 // emitter warps (1 .. NW-2)
-    static_assert(NW >= 3, "walker, emitters and producer");
+    constexpr uint32_t WW = split_walkers(NT);      // walker warps
+    constexpr uint32_t NE = split_emitters(NT);     // emitter warps
+    static_assert(NE >= 1, "walkers, emitters and producer");
     const Params &P = *B.params;
     const uint32_t level = P.level, rec_cap = P.rec_cap;
     const uint32_t wlim = P.wait_limit;            // polls of a bounded wait
@@ -791,8 +812,8 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
     const uint32_t nc_dep1 = level == 0u ? 2u : 3u, nc_dep2 = level == 0u ? 6u : (level == 1u ? 10u : 15u);
     const uint32_t lane = threadIdx.x & 31u, l16 = lane & 15u, half = lane >> 4;
     const uint32_t warp = threadIdx.x >> 5;
-    const bool walker = warp == 0u, producer = warp == NW - 1u;
-    const uint32_t ew = warp - 1u;                  // emitter index
+    const bool walker = warp < WW, producer = warp == NW - 1u;
+    const uint32_t ew = warp - WW;                  // emitter index
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint32_t windex = window_index_bytes(maxq);
     const uint32_t nring = nbuf >= 2u ? nbuf : 2u;
@@ -888,6 +909,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
             sh.walk_done = 0;
             sh.stop_layer = 0;
             sh.posted_lo = 0;
+            sh.wcnt[0] = sh.wcnt[1] = 0;
         }
         __syncthreads();
         const uint32_t item = sh.item;
@@ -935,7 +957,105 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         const uint4 *seg_g = B.layer_seg + C.layer_base;
         auto slot_of = [&](int L) -> uint32_t { return (uint32_t)(L + 1) % nring; };
 
-        if (walker) {
+        // ---- walker warps.  Warp 0 walks; a step of more than 64 candidates
+        // is split over all walker warps (the helpers wait on a named barrier
+        // in between): the activity pass over the candidates, a barrier, the
+        // gates undone over the active list, a barrier.  The owner rule
+        // leaves every plane a single writer, so the warps need no other
+        // synchronisation; list positions come from shared counters.
+        auto wsync = [&]() {
+            if (WW == 1u) __syncwarp();
+            else asm volatile("bar.sync 1, %0;" ::"n"(WW * 32u) : "memory");
+        };
+        // a position for n entries of this warp's ballot (one shared atomic)
+        auto take = [&](uint32_t *ctr, uint32_t n) -> uint32_t {
+            uint32_t o = 0;
+            if (lane == 0u && n) o = atomicAdd(ctr, n);
+            return __shfl_sync(0xFFFFFFFFu, o, 0);
+        };
+        auto large_activity = [&](uint32_t wid, int Lc, uint32_t np, uint32_t nc, const uint16_t *prv, uint16_t *abl,
+                                  ulonglong2 *tbl, uint32_t *tgl, bool snp, uint32_t stamp) {
+            for (uint32_t base = 64u * wid; base < nc; base += 64u * WW) {
+                const uint32_t i0 = base + lane, i1 = base + lane + 32u;
+                uint32_t q0 = 0, q1 = 0;
+                if (i0 < nc) q0 = i0 < np ? prv[i0] : s.add[i0 - np];
+                if (i1 < nc) q1 = i1 < np ? prv[i1] : s.add[i1 - np];
+                const ulonglong2 p0 = s.pl[q0], p1 = s.pl[q1];
+                const bool a0 = i0 < nc && (p0.x | p0.y) != 0ull;
+                const bool a1 = i1 < nc && (p1.x | p1.y) != 0ull;
+                if (i0 < nc) s.bits[q0] = a0 ? kActive : (unsigned char)0;
+                if (i1 < nc) s.bits[q1] = a1 ? kActive : (unsigned char)0;
+                if (a0 && snp) { tbl[q0] = p0; tgl[q0] = stamp; }
+                if (a1 && snp) { tbl[q1] = p1; tgl[q1] = stamp; }
+                if (Lc < 0 && ((a0 && p0.y != 0ull) || (a1 && p1.y != 0ull)))
+                    report(B.status, GP_ERR_NONDETERMINISTIC, cidx, 0xFFFFFFFFu, gcol);
+                const unsigned m0 = __ballot_sync(0xFFFFFFFFu, a0), m1 = __ballot_sync(0xFFFFFFFFu, a1);
+                const uint32_t o = take(&sh.wcnt[0], (uint32_t)(__popc(m0) + __popc(m1)));
+                if (a0) abl[o + __popc(m0 & lt_mask)] = (uint16_t)q0;
+                if (a1) abl[o + __popc(m0) + __popc(m1 & lt_mask)] = (uint16_t)q1;
+            }
+        };
+        auto undo = [&](uint32_t q, ulonglong2 P, uint32_t g, bool act, int Lc) -> uint32_t {
+            if (!act) return kNone;
+            const uint32_t k = g >> 28, pay = g & 0x0FFFFFFFu;
+            if (k >= GV_CX_C) {
+                const bool pact = s.bits[pay] == kActive;
+                if (pact && (k == GV_CX_T || k == GV_CZ_B)) return kNone;
+                const ulonglong2 Q = s.pl[pay];
+                const bool cxc = k == GV_CX_C, cxt = k == GV_CX_T, cz = !cxc && !cxt;
+                // CX(c,t): x_c ^= x_t, z_t ^= z_c; CZ(a,b): x_a ^= z_b, x_b ^= z_a
+                const unsigned long long ox = P.x ^ (cxc ? Q.x : 0ull) ^ (cz ? Q.y : 0ull);
+                const unsigned long long oz = P.y ^ (cxt ? Q.y : 0ull);
+                const unsigned long long px = Q.x ^ (cxt ? P.x : 0ull) ^ (cz ? P.y : 0ull);
+                const unsigned long long pz = Q.y ^ (cxc ? P.y : 0ull);
+                s.pl[q] = make_ulonglong2(ox, oz);
+                s.pl[pay] = make_ulonglong2(px, pz);
+                return pay;
+            }
+            if (k == K_H) { s.pl[q] = make_ulonglong2(P.y, P.x); return kNone; }
+            if (k == K_S) { s.pl[q] = make_ulonglong2(P.x ^ P.y, P.y); return kNone; }
+            if (k == GV_NONE) return kNone;
+            // measurements and resets
+            ulonglong2 t = P;
+            if (k <= K_MR) {
+                if (t.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)Lc, gcol);
+                if (k != K_M) t = make_ulonglong2(0ull, 0ull);
+                if (k != K_R) t.x ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
+            } else {
+                if (t.x != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)Lc, gcol);
+                if (k != K_MX) t = make_ulonglong2(0ull, 0ull);
+                if (k != K_RX) t.y ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
+            }
+            s.pl[q] = t;
+            return kNone;
+        };
+        auto large_undo = [&](uint32_t wid, int Lc, uint32_t na, const uint16_t *abl, const Window &vw) {
+            for (uint32_t base = 32u * wid; base < na; base += 32u * WW) {
+                const uint32_t i = base + lane;
+                const uint32_t q = i < na ? abl[i] : 0u;
+                const ulonglong2 P = s.pl[q];
+                const uint32_t partner = undo(q, P, i < na ? vw.gate[q] : 0u, i < na, Lc);
+                const bool add = partner != kNone && s.bits[partner] == 0;
+                if (add) s.bits[partner] = kAdded;
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, add);
+                const uint32_t o = take(&sh.wcnt[1], (uint32_t)__popc(m));
+                if (add) s.add[o + __popc(m & lt_mask)] = (uint16_t)partner;
+            }
+        };
+        if (walker && warp != 0u) {
+            // ---- helper walker warps: large steps of warp 0's walk
+            for (;;) {
+                wsync();
+                const WalkStep ws = sh.wstep;
+                if (ws.cmd == 0u) break;
+                const Window vw = sh.desc[ws.slot];
+                large_activity(warp, ws.L, ws.n_prev, ws.n_cand, ws.prev, ws.ab, tab_of(s, ws.b), tag_of(s, ws.b),
+                               ws.snap != 0u, ws.stamp);
+                wsync();
+                if (ws.L >= 0) large_undo(warp, ws.L, sh.wcnt[0], ws.ab, vw);
+                wsync();
+            }
+        } else if (walker && warp == 0u) {
             // ---- walker: candidates of a step = the active qubits of the
             // last step, then the qubits the last step added
             uint32_t n_prev = 0, n_add = 0, cur = n_ent;
@@ -954,40 +1074,6 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
             // activity pass): the owner of a two-qubit gate (its active
             // qubit, or its control / first qubit when both are active)
             // updates both planes; returns the partner it touched
-            auto undo = [&](uint32_t q, ulonglong2 P, uint32_t g, bool act) -> uint32_t {
-                if (!act) return kNone;
-                const uint32_t k = g >> 28, pay = g & 0x0FFFFFFFu;
-                if (k >= GV_CX_C) {
-                    const bool pact = s.bits[pay] == kActive;
-                    if (pact && (k == GV_CX_T || k == GV_CZ_B)) return kNone;
-                    const ulonglong2 Q = s.pl[pay];
-                    const bool cxc = k == GV_CX_C, cxt = k == GV_CX_T, cz = !cxc && !cxt;
-                    // CX(c,t): x_c ^= x_t, z_t ^= z_c; CZ(a,b): x_a ^= z_b, x_b ^= z_a
-                    const unsigned long long ox = P.x ^ (cxc ? Q.x : 0ull) ^ (cz ? Q.y : 0ull);
-                    const unsigned long long oz = P.y ^ (cxt ? Q.y : 0ull);
-                    const unsigned long long px = Q.x ^ (cxt ? P.x : 0ull) ^ (cz ? P.y : 0ull);
-                    const unsigned long long pz = Q.y ^ (cxc ? P.y : 0ull);
-                    s.pl[q] = make_ulonglong2(ox, oz);
-                    s.pl[pay] = make_ulonglong2(px, pz);
-                    return pay;
-                }
-                if (k == K_H) { s.pl[q] = make_ulonglong2(P.y, P.x); return kNone; }
-                if (k == K_S) { s.pl[q] = make_ulonglong2(P.x ^ P.y, P.y); return kNone; }
-                if (k == GV_NONE) return kNone;
-                // measurements and resets
-                ulonglong2 t = P;
-                if (k <= K_MR) {
-                    if (t.y != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)L, gcol);
-                    if (k != K_M) t = make_ulonglong2(0ull, 0ull);
-                    if (k != K_R) t.x ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
-                } else {
-                    if (t.x != 0ull) report(B.status, GP_ERR_NONDETERMINISTIC, cidx, (uint32_t)L, gcol);
-                    if (k != K_MX) t = make_ulonglong2(0ull, 0ull);
-                    if (k != K_RX) t.y ^= meas_word_at(s.ent_m, s.ent_w, n_ent, pay);
-                }
-                s.pl[q] = t;
-                return kNone;
-            };
             for (;;) {
                 const bool ff = L > emit_hi;
                 const bool snap = !ff;            // a snapshot is published for the emitters
@@ -1062,7 +1148,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     if (a0) ab[__popc(m0 & lt_mask)] = (uint16_t)q0;
                     n_act = __popc(m0);
                     publish();
-                    if (L >= 0) append(undo(q0, p0, g0, a0));
+                    if (L >= 0) append(undo(q0, p0, g0, a0, L));
                 } else if (n_cand <= 64u) {
                     // two per lane
                     uint32_t q0, q1, g0, g1;
@@ -1071,25 +1157,23 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     activity(lane, lane + 32u, q0, q1, p0, p1, g0, g1, a0, a1);
                     publish();
                     if (L >= 0) {
-                        append(undo(q0, p0, g0, a0));
-                        append(undo(q1, p1, g1, a1));
+                        append(undo(q0, p0, g0, a0, L));
+                        append(undo(q1, p1, g1, a1, L));
                     }
                 } else {
-                    for (uint32_t base = 0; base < n_cand; base += 64u) {
-                        uint32_t q0, q1, g0, g1;
-                        ulonglong2 p0, p1;
-                        bool a0, a1;
-                        activity(base + lane, base + lane + 32u, q0, q1, p0, p1, g0, g1, a0, a1);
+                    // more than 64 candidates: the helper walker warps join in
+                    if (lane == 0u) {
+                        sh.wcnt[0] = sh.wcnt[1] = 0u;
+                        sh.wstep = WalkStep{L, n_prev, n_cand, slot, ab, prev, b, snap ? 1u : 0u, st, 1u};
                     }
+                    wsync();                                // the helpers wake
+                    large_activity(0u, L, n_prev, n_cand, prev, ab, tb, tg, snap, st);
+                    wsync();                                // every candidate classified
+                    n_act = sh.wcnt[0];
                     publish();
-                    if (L >= 0) {
-                        for (uint32_t base = 0; base < n_act; base += 32u) {
-                            const uint32_t i = base + lane;
-                            const uint32_t q = i < n_act ? ab[i] : 0u;
-                            const ulonglong2 P = s.pl[q];
-                            append(undo(q, P, i < n_act ? v.gate[q] : 0u, i < n_act));
-                        }
-                    }
+                    if (L >= 0) large_undo(0u, L, n_act, ab, v);
+                    wsync();                                // the helpers are done
+                    n_new = sh.wcnt[1];
                 }
                 if (L >= 0) {
                 // measurements of the column at L on inactive qubits
@@ -1139,6 +1223,11 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                 if (n_prev + n_add == 0u && (uint32_t)(L - 1) < lmin) break;
                 L--;
             }
+            // the helpers leave
+            if (WW > 1u) {
+                if (lane == 0u) sh.wstep.cmd = 0u;
+                wsync();
+            }
             if (ok) {
                 // the end-of-column step: the emitters leave on it
                 const uint32_t b = st & 1u;
@@ -1159,7 +1248,9 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
             }
             if (lane == 0u) *(volatile uint32_t *)&sh.walk_done = 1u;
         } else if (!producer) {
-            // ---- emitters: the noise rows of each published step
+            // ---- emitters: the noise rows of each published step; each
+            // half-warp takes one active qubit and evaluates its rows two at
+            // a time, one Pauli component per lane
             for (;;) {
                 const uint32_t b = st & 1u;
                 if (!wait_warp(&sh.tab_full[b], (tfull_par >> b) & 1u)) break;
@@ -1188,6 +1279,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     const ulonglong2 p = tb[x];
                     return t == stamp ? p : make_ulonglong2(0ull, 0ull);
                 };
+                warp_prefetch();
                 auto row_word = [&](uint2 r, uint32_t q) -> unsigned long long {
                     const uint32_t kind = row_kind(r);
                     if (kind < K_XERR) return 0ull;
@@ -1201,22 +1293,19 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     const unsigned long long codes =
                         two ? 0x0EBF7D639CA25184ull : (kind == K_DEP1 ? 0x321ull : (kind == K_XERR ? 1ull : 2ull));
                     const uint32_t code = (uint32_t)(codes >> (4u * l16)) & 0xFu;
-                    return ((code & 1u) ? pa.x : 0ull) ^ ((code & 2u) ? pa.y : 0ull) ^ ((code & 4u) ? pb.x : 0ull) ^
-                           ((code & 8u) ? pb.y : 0ull);
+                    return ((code & 1u) ? pa.x : 0ull) ^ ((code & 2u) ? pa.y : 0ull) ^
+                           ((code & 4u) ? pb.x : 0ull) ^ ((code & 8u) ? pb.y : 0ull);
                 };
                 auto emit = [&](uint2 r, unsigned long long w) {
                     const unsigned m = __ballot_sync(0xFFFFFFFFu, w != 0ull);
                     if (m == 0u) return;
                     const uint32_t cnt = (uint32_t)__popc(m);
                     if (!warp_room(cnt)) return;
-                    if (w != 0ull) {
-                        const uint32_t mech = mech_base + r.y + l16;
+                    if (w != 0ull)
                         B.records[ck_pos + __popc(m & lt_mask)] =
-                            make_uint4(mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
-                    }
+                            make_uint4(mech_base + r.y + l16, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
                     ck_pos += cnt;
                 };
-                warp_prefetch();
                 for (uint32_t base = 2u * ew; base < n_act; base += 2u * NE) {
                     const uint32_t c = base + half;
                     const bool valid = c < n_act;
@@ -1337,7 +1426,8 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                 const uint32_t slot = slot_of(k2);
                 if (producer) {
                     free_pend &= ~(1u << slot);
-                } else if (walker) {
+                } else if (warp == 0u) {
+                    // the walker warp that tracks the window phases
                     if (!wait_bar(&sh.win_full[slot], (full_par >> slot) & 1u)) break;
                     full_par ^= 1u << slot;
                 }
@@ -1379,11 +1469,18 @@ Stage1Shape stage1_shape(uint32_t maxq, uint32_t blocks_per_sm, size_t limit) {
     const size_t budget = blocks_per_sm > 1 ? std::min(limit, per_sm / blocks_per_sm - 1024) : limit;
     const uint32_t wi = window_index_bytes(maxq);
     // the role-split walk when its tables and at least two windows fit, else
-    // the block-wide walk
+    // the block-wide walk.  The deepest ring whose windows hold a whole layer
+    // (about two list entries per qubit: every noise row after the gates of
+    // L and before those of L + 1, two-qubit rows twice) is preferred; a
+    // window that does not fit is read from global memory, which costs more
+    // than a shallower ring.
+    const size_t layer_entries = 2 * (size_t)maxq + 64;
     for (int split = 1; split >= 0; split--) {
         const size_t base = split ? split_base_bytes(maxq) : smem_base_bytes(maxq);
+        for (uint32_t pass = 0; pass < 2; pass++)
         for (uint32_t nbuf = split ? 4u : 3u; nbuf >= 2; nbuf--) {
-            if (budget < base + (size_t)nbuf * (wi + 512 * 8)) continue;
+            const size_t want = pass == 0 ? layer_entries : 512;
+            if (budget < base + (size_t)nbuf * (wi + want * 8)) continue;
             size_t cap = (budget - base) / nbuf;
             cap = (cap - wi) / 8;
             cap = std::min<size_t>(cap, 4096) & ~(size_t)15;
