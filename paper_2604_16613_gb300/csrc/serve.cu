@@ -138,8 +138,24 @@ __global__ void seal_flags_kernel(Buffers B, const SealDesc *seal, const uint32_
     }
 }
 
+// What the select phase of a step needs beyond the compile: the windows,
+// the request slots (passes) and the pinned step buffer.  The host fills a
+// pinned copy before each step; a copy inside the captured select graph
+// brings it to the device, so the graph's kernels never change.
+struct SealOut {
+    uint32_t *doff, *det;
+    float *prob, *logodds;
+    unsigned long long *obs;
+};
+struct SelParams {
+    uint32_t n_win, n_pass;
+    uint64_t edges_cap, det_cap;
+    SealOut host;
+};
+
 // first hyperedge of every window (from the compile's per-circuit counts)
-__global__ void win_edges_kernel(Buffers B, uint32_t n_win, uint32_t *win_e0) {
+__global__ void win_edges_kernel(Buffers B, const SelParams *sp, uint32_t *win_e0) {
+    const uint32_t n_win = sp->n_win;
     if (threadIdx.x == 0) {
         uint32_t run = 0;
         for (uint32_t w = 0; w < n_win; w++) {
@@ -154,9 +170,9 @@ __global__ void win_edges_kernel(Buffers B, uint32_t n_win, uint32_t *win_e0) {
 // every window (after those of slots 0 .. r-1); the last detector offset of
 // every request (r, w) -- offsets are per request, and request (r, w) is the
 // (r n_win + w)-th, so its offsets sit r n_win + w entries after its edges
-__global__ void slot_starts_kernel(Buffers B, uint32_t n_win, const uint32_t *win_e0, uint32_t r, uint2 *starts,
+__global__ void slot_starts_kernel(Buffers B, const SelParams *sp, const uint32_t *win_e0, uint32_t r, uint2 *starts,
                                    uint32_t *doff) {
-    const uint32_t E = B.status->n_edges;
+    const uint32_t E = B.status->n_edges, n_win = sp->n_win;
     const uint2 base = r ? starts[(size_t)(r - 1u) * (n_win + 1u) + n_win] : make_uint2(0u, 0u);
     uint2 *row = starts + (size_t)r * (n_win + 1u);
     for (uint32_t w = threadIdx.x; w <= n_win; w += blockDim.x) {
@@ -171,8 +187,8 @@ __global__ void slot_starts_kernel(Buffers B, uint32_t n_win, const uint32_t *wi
 // a mechanism of records-only cycle c flipping a detector after cycle c + H:
 // the window's horizon was too short
 __global__ void seal_horizon_kernel(Buffers B, const SealDesc *seal, const uint2 *rec_tab, uint32_t max_h,
-                                    uint32_t n_win, uint32_t *horizon) {
-    for (uint32_t w = blockIdx.x; w < n_win; w += gridDim.x) {
+                                    const SelParams *sp, uint32_t *horizon) {
+    for (uint32_t w = blockIdx.x; w < sp->n_win; w += gridDim.x) {
         const uint32_t m0 = B.circ[w].mech_base, n = seal[w].n_mech_rec, nr = seal[w].n_rec;
         const uint2 *tab = rec_tab + (size_t)w * max_h;
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -187,15 +203,10 @@ __global__ void seal_horizon_kernel(Buffers B, const SealDesc *seal, const uint2
     }
 }
 
-struct SealOut {
-    uint32_t *doff, *det;
-    float *prob, *logodds;
-    unsigned long long *obs;
-};
-
-__global__ void seal_write_kernel(Buffers B, const SealDesc *seal, SealOut out, const uint2 *row, uint32_t r,
-                                  uint32_t n_win) {
-    const uint32_t E = B.status->n_edges;
+__global__ void seal_write_kernel(Buffers B, const SealDesc *seal, SealOut out, const uint2 *starts, uint32_t r,
+                                  const SelParams *sp) {
+    const uint32_t E = B.status->n_edges, n_win = sp->n_win;
+    const uint2 *row = starts + (size_t)r * (n_win + 1u);
     const uint2 base = row[0];
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         if (B.scan_val[e].x == 0u) continue;
@@ -224,9 +235,12 @@ __device__ __forceinline__ void copy_words(uint32_t *dst, const uint32_t *src, u
 // offsets and detector ids into the pinned step buffer, sized by the totals
 // on the device (tot = edges and detector ids over all slots)
 // (the counts are clamped to the buffer's capacity; the host checks them)
-__global__ void seal_copy_kernel(SealOut dev, SealOut host, const uint2 *tot_ptr, uint32_t n_offs_extra,
-                                 uint64_t edges_cap, uint64_t det_cap) {
-    const uint2 tot = *tot_ptr;
+__global__ void seal_copy_kernel(SealOut dev, const SelParams *sp, const uint2 *starts) {
+    const uint32_t n_win = sp->n_win, n_pass = sp->n_pass;
+    const SealOut host = sp->host;
+    const uint64_t edges_cap = sp->edges_cap, det_cap = sp->det_cap;
+    const uint32_t n_offs_extra = n_pass * n_win;
+    const uint2 tot = starts[(size_t)(n_pass - 1u) * (n_win + 1u) + n_win];
     const uint64_t ne = min((uint64_t)tot.x, edges_cap), no = min((uint64_t)tot.x + n_offs_extra, edges_cap);
     const uint64_t nd = min((uint64_t)tot.y, det_cap);
     const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
@@ -341,6 +355,10 @@ struct gp_server {
     uint32_t *d_cyc_tab = nullptr;       // per window: detector offset of each cycle
     uint32_t *d_win_e0 = nullptr;        // per window: first hyperedge
     uint2 *d_starts = nullptr;           // per request slot and window: output starts
+    SelParams *d_sel = nullptr;          // the select phase's per-step parameters
+    SelParams *h_sel = nullptr;          // ... their pinned host copy
+    cudaStream_t cap_stream = nullptr;   // captures the select graphs
+    std::vector<cudaGraphExec_t> sel_exec;   // select phase, one graph per pass count
     float times[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // last step: build, compile, select, hand-out,
                                                  // then the compile's device stages (us)
     SealOut out{};
@@ -391,7 +409,7 @@ void free_outbuf(OutBuf *b) {
 
 void free_host(gp_server *s) {
     for (Patch &p : s->patches) free_registered(p);
-    void *ptrs[] = {s->h_desc, s->h_stage_ops, s->h_stage_recs, s->h_stage_noise, s->h_horizon, s->h_starts};
+    void *ptrs[] = {s->h_desc, s->h_stage_ops, s->h_stage_recs, s->h_stage_noise, s->h_horizon, s->h_starts, s->h_sel};
     for (void *p : ptrs)
         if (p) cudaFreeHost(p);
     for (OutBuf *b : s->out_pool) free_outbuf(b);
@@ -526,6 +544,7 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
         s->d_cyc_tab = carve_dev<uint32_t>(base, off, Bt * (W + 1));
         s->d_win_e0 = carve_dev<uint32_t>(base, off, Bt + 1);
         s->d_starts = carve_dev<uint2>(base, off, (uint64_t)c.max_cycles_per_step * (Bt + 1));
+        s->d_sel = carve_dev<SelParams>(base, off, 1);
         s->out.prob = carve_dev<float>(base, off, s->out_edges_cap);
         s->out.logodds = carve_dev<float>(base, off, s->out_edges_cap);
         s->out.obs = carve_dev<unsigned long long>(base, off, s->out_edges_cap);
@@ -555,8 +574,12 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
         cudaMallocHost(&s->h_stage_recs, sizeof(uint32_t) * std::max<uint64_t>((uint64_t)c.max_pending * c.max_cycle_recs, 1)) != cudaSuccess ||
         cudaMallocHost(&s->h_stage_noise, sizeof(float) * std::max<uint64_t>((uint64_t)c.max_pending * c.max_cycle_locations, 1)) != cudaSuccess ||
         cudaMallocHost(&s->h_horizon, sizeof(uint32_t) * Bt) != cudaSuccess ||
-        cudaMallocHost(&s->h_starts, sizeof(uint2) * (uint64_t)c.max_cycles_per_step * (Bt + 1)) != cudaSuccess)
+        cudaMallocHost(&s->h_starts, sizeof(uint2) * (uint64_t)c.max_cycles_per_step * (Bt + 1)) != cudaSuccess ||
+        cudaMallocHost(&s->h_sel, sizeof(SelParams)) != cudaSuccess)
         return cleanup(sfail(GP_ERR_CUDA, "cudaMallocHost of the server staging failed"));
+    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup(sfail(GP_ERR_CUDA, "cudaStreamCreate failed"));
+    s->sel_exec.assign(c.max_cycles_per_step + 1u, nullptr);
     for (uint32_t i = 0; i < c.max_pending; i++) s->free_stage.push_back(c.max_pending - 1 - i);
     *out = s;
     return GP_OK;
@@ -564,6 +587,9 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
 
 void gp_server_destroy(gp_server *s) {
     if (!s) return;
+    for (cudaGraphExec_t g : s->sel_exec)
+        if (g) cudaGraphExecDestroy(g);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->drv) gp_driver_destroy(s->drv);
     if (s->dmem) cudaFree(s->dmem);
     free_host(s);
@@ -632,6 +658,55 @@ gp_status gp_server_close_patch(gp_server *s, uint32_t patch) {
 }  // extern "C"
 
 namespace {
+
+// The select phase of a step with n_pass request slots, captured once as a
+// graph on the server's own stream and replayed on the caller's: clear the
+// horizon flags, bring the step's parameters to the device, the horizon
+// check, each window's first hyperedge, and per request slot the flags, the
+// scan, the starts and the write; then the copy into the pinned step buffer
+// and the read-back of the starts and the horizon flags.  Every size and
+// pointer that changes from step to step is read on the device from the
+// parameter block, so one graph per pass count serves every step.
+gp_status ensure_select_graph(gp_server *s, uint32_t n_pass) {
+    if (s->sel_exec[n_pass]) return GP_OK;
+    const gp_server_config &c = s->cfg;
+    const uint32_t Bt = c.max_batch;
+    const Buffers &B = driver_buffers(s->drv);
+    const uint32_t grid = 4u * s->n_sms;
+    const uint32_t grid_h = std::max(1u, std::min<uint32_t>(Bt, 8u * s->n_sms));
+    cudaStream_t cs = s->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return sfail(GP_ERR_CUDA, std::string("select graph capture: ") + cudaGetErrorString(e));
+    uint32_t launches = 0;
+    cudaMemsetAsync(s->d_horizon, 0, Bt * sizeof(uint32_t), cs);
+    cudaMemcpyAsync(s->d_sel, s->h_sel, sizeof(SelParams), cudaMemcpyHostToDevice, cs);
+    seal_horizon_kernel<<<grid_h, 256, 0, cs>>>(B, s->d_seal, s->d_rec_tab, c.max_horizon, s->d_sel, s->d_horizon);
+    win_edges_kernel<<<1, 32, 0, cs>>>(B, s->d_sel, s->d_win_e0);
+    for (uint32_t r = 0; r < n_pass; r++) {
+        seal_flags_kernel<<<grid, 256, 0, cs>>>(B, s->d_seal, s->d_cyc_tab, s->W + 1u, r);
+        launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, driver_sms(s->drv), cs, &launches);
+        slot_starts_kernel<<<1, 256, 0, cs>>>(B, s->d_sel, s->d_win_e0, r, s->d_starts, s->out.doff);
+        seal_write_kernel<<<grid, 256, 0, cs>>>(B, s->d_seal, s->out, s->d_starts, r, s->d_sel);
+    }
+    seal_copy_kernel<<<grid, 256, 0, cs>>>(s->out, s->d_sel, s->d_starts);
+    cudaMemcpyAsync(s->h_starts, s->d_starts, (size_t)n_pass * (Bt + 1u) * sizeof(uint2), cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(s->h_horizon, s->d_horizon, Bt * sizeof(uint32_t), cudaMemcpyDeviceToHost, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t launch_err = cudaGetLastError();
+    e = cudaStreamEndCapture(cs, &g);
+    if (launch_err != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return sfail(GP_ERR_CUDA, std::string("select graph capture: ") +
+                                      cudaGetErrorString(launch_err != cudaSuccess ? launch_err : e));
+    }
+    e = cudaGraphInstantiate(&s->sel_exec[n_pass], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->sel_exec[n_pass] = nullptr;
+        return sfail(GP_ERR_CUDA, std::string("select graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return GP_OK;
+}
 
 // checks of a cycle about to become patch p's next one; fills its sizes
 gp_status scan_cycle(const gp_server *s, const Patch &p, const gp_circuit *cyc, const float *noise, CycleScan &sc) {
@@ -976,7 +1051,6 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     SV_CUDA(cudaMemcpyAsync(s->d_cyc_tab, hctab, (size_t)n_win * (s->W + 1u) * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     if (x_ops) SV_CUDA(cudaMemcpyAsync(s->d_extra_ops, hxops, x_ops * sizeof(uint4), cudaMemcpyHostToDevice, st));
     if (x_recs) SV_CUDA(cudaMemcpyAsync(s->d_extra_recs, hxrecs, x_recs * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    SV_CUDA(cudaMemsetAsync(s->d_horizon, 0, n_win * sizeof(uint32_t), st));
     assemble_kernel<<<dim3(nseg, kSegBlocksY), 256, 0, st>>>(s->d_seg, nseg, s->arena_ops, s->arena_recs, s->arena_noise);
     SV_CUDA(cudaGetLastError());
     const uint64_t t_built = now_ns();
@@ -989,29 +1063,19 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     const uint32_t rs = n_win + 1u;             // entries of one slot's row of starts
     OutBuf *ob = nullptr;
     if (cst == GP_OK && view.n_edges) {
-        const Buffers &B = driver_buffers(s->drv);
-        const uint32_t grid = 4u * s->n_sms;
-        seal_horizon_kernel<<<n_win, 256, 0, st>>>(B, s->d_seal, s->d_rec_tab, c.max_horizon, n_win, s->d_horizon);
-        win_edges_kernel<<<1, 32, 0, st>>>(B, n_win, s->d_win_e0);
         // the step buffer is taken before the passes, for the batch's whole
         // output (the sealed part is at most that), so one kernel can fill
         // it and one synchronisation ends the step
         ob = take_outbuf(s, view.n_edges, (uint64_t)n_pass * n_win, view.n_det_entries);
         if (!ob) cst = sfail(GP_ERR_CUDA, "cudaMallocHost of a result buffer failed");
         if (cst == GP_OK) {
-            uint32_t launches = 0;
-            for (uint32_t r = 0; r < n_pass; r++) {
-                seal_flags_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->d_cyc_tab, s->W + 1u, r);
-                launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, driver_sms(s->drv), st, &launches);
-                slot_starts_kernel<<<1, 256, 0, st>>>(B, n_win, s->d_win_e0, r, s->d_starts, s->out.doff);
-                seal_write_kernel<<<grid, 256, 0, st>>>(B, s->d_seal, s->out, s->d_starts + (size_t)r * rs, r, n_win);
-            }
-            const SealOut host{ob->doff, ob->det, ob->prob, ob->logodds, ob->obs};
-            seal_copy_kernel<<<grid, 256, 0, st>>>(s->out, host, s->d_starts + (size_t)(n_pass - 1u) * rs + n_win,
-                                                    n_pass * n_win, ob->edges_cap, ob->det_cap);
-            SV_CUDA(cudaGetLastError());
-            SV_CUDA(cudaMemcpyAsync(s->h_starts, s->d_starts, (size_t)n_pass * rs * sizeof(uint2), cudaMemcpyDeviceToHost, st));
-            SV_CUDA(cudaMemcpyAsync(s->h_horizon, s->d_horizon, n_win * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            *s->h_sel = SelParams{n_win, n_pass, ob->edges_cap, ob->det_cap,
+                                  SealOut{ob->doff, ob->det, ob->prob, ob->logodds, ob->obs}};
+            const gp_status gs = ensure_select_graph(s, n_pass);
+            if (gs != GP_OK) cst = gs;
+        }
+        if (cst == GP_OK) {
+            SV_CUDA(cudaGraphLaunch(s->sel_exec[n_pass], st));
             SV_CUDA(cudaStreamSynchronize(st));
             const uint2 tot = s->h_starts[(size_t)(n_pass - 1u) * rs + n_win];
             if (tot.x + (uint64_t)n_pass * n_win > ob->edges_cap || tot.y > ob->det_cap)
