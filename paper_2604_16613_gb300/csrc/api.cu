@@ -194,7 +194,7 @@ struct gp_driver {
     gp_tuning exec_tuning{0, 0, 0, 0};
     uint32_t graph_kernels = 0;
     // tuning / instrumentation / test knobs
-    gp_tuning tuning{512, 0, 256, 8};
+    gp_tuning tuning{512, 0, 512, 8};
     gp_debug debug{0, 0, 0, 0};
     bool timing = false;
     cudaEvent_t ev[5] = {};

@@ -20,7 +20,7 @@ constexpr int kInlineWords = 4;         // mask words kept beside each mechanism
                                         // the rest go to the overflow list
 constexpr int kMechPerBlockScan = 1024; // mechanisms per compaction block
 constexpr uint64_t kPoolSlack = 1ull << 22;  // record-pool slack for unused chunk tails
-constexpr int kPackThreads = 256;       // layer packing block size
+constexpr int kPackThreads = 1024;      // layer index block size
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
 // stage-1 work item: column id | segment << kSegShift (segments of a long

@@ -462,10 +462,20 @@ __global__ void __launch_bounds__(256) gather_host_kernel(const CopyJob *jobs, u
     const bool wide = ((reinterpret_cast<uintptr_t>(job.src) | reinterpret_cast<uintptr_t>(job.dst)) & 15u) == 0u;
     uint64_t done = 0;
     if (wide) {
+        // four independent 16-byte loads in flight per thread (the link's
+        // latency, not its bandwidth, limits one load at a time)
         const uint64_t n16 = job.bytes / 16u;
-        const uint4 *src = static_cast<const uint4 *>(job.src);
-        uint4 *dst = static_cast<uint4 *>(job.dst);
-        for (uint64_t i = tid; i < n16; i += stride) dst[i] = src[i];
+        const uint4 *__restrict__ src = static_cast<const uint4 *>(job.src);
+        uint4 *__restrict__ dst = static_cast<uint4 *>(job.dst);
+        uint64_t i = tid;
+        for (; i + 3u * stride < n16; i += 4u * stride) {
+            const uint4 a = src[i], b = src[i + stride], c = src[i + 2u * stride], d = src[i + 3u * stride];
+            dst[i] = a;
+            dst[i + stride] = b;
+            dst[i + 2u * stride] = c;
+            dst[i + 3u * stride] = d;
+        }
+        for (; i < n16; i += stride) dst[i] = src[i];
         done = n16 * 16u;
     }
     const uint64_t n4 = (job.bytes - done) / 4u;
@@ -478,9 +488,10 @@ __global__ void __launch_bounds__(256) gather_host_kernel(const CopyJob *jobs, u
 
 void launch_gather_host(const CopyJob *jobs, uint32_t n_jobs, uint64_t max_bytes, uint32_t n_sms, cudaStream_t s) {
     if (!n_jobs) return;
-    // enough blocks that the largest job is spread over the whole GPU
+    // enough blocks that the largest job is spread over the whole GPU (each
+    // thread moves four 16-byte words per round)
     const uint64_t per_block = 256ull * 16u * 4u;
-    uint32_t gx = (uint32_t)std::min<uint64_t>((max_bytes + per_block - 1) / per_block, 4ull * n_sms);
+    uint32_t gx = (uint32_t)std::min<uint64_t>((max_bytes + per_block - 1) / per_block, 8ull * n_sms);
     if (gx == 0) gx = 1;
     gather_host_kernel<<<dim3(gx, n_jobs), 256, 0, s>>>(jobs, n_jobs);
 }

@@ -289,7 +289,7 @@ class Driver:
         return g[:self._last_noise_len]
 
     # -- knobs -------------------------------------------------------------------
-    def set_tuning(self, stage1_threads=512, stage1_blocks_per_sm=0, stage2_threads=256, stage2_blocks_per_sm=8):
+    def set_tuning(self, stage1_threads=512, stage1_blocks_per_sm=0, stage2_threads=512, stage2_blocks_per_sm=8):
         t = native.GpTuning(stage1_threads, stage1_blocks_per_sm, stage2_threads, stage2_blocks_per_sm)
         native.check(self.lib.gp_set_tuning(self.handle, ctypes.byref(t)))
 
