@@ -219,12 +219,22 @@ gp_status gp_result_view(const gp_driver *drv, gp_dem_view *out);
 gp_status gp_result_to_host(gp_driver *drv, uint32_t *det_offsets, uint32_t *det_idx,
                             uint64_t *obs_mask, float *prob, float *logodds, void *stream);
 
-/* Tunable launch parameters (picked by the package's autotuner). */
+/* Tunable launch and work-split parameters (picked by the package's
+ * autotuner; not in the paper).  None changes a compile's result.
+ *   obs_words     the observables of a circuit are split evenly over
+ *                 min(n_observables, obs_words) word columns, each walked on
+ *                 its own (Sec. 3.1 walks one observable word); a mechanism
+ *                 then carries one mask word per column it flips, so
+ *                 bounds.max_mask_words counts these words.
+ *   obs_segments  the most work items one observable column's walk is split
+ *                 over in time (each fast-forwards to its own part). */
 typedef struct {
     uint32_t stage1_threads;      /* 128, 256, 512 or 1024                    */
     uint32_t stage1_blocks_per_sm;/* resident blocks per SM for stage 1 (0 = max) */
     uint32_t stage2_threads;      /* 128, 256 or 512                          */
     uint32_t stage2_blocks_per_sm;/* grid = SMs x this for grid-stride kernels */
+    uint32_t obs_words;           /* 1..8                                     */
+    uint32_t obs_segments;        /* 1..3                                     */
 } gp_tuning;
 gp_status gp_set_tuning(gp_driver *drv, const gp_tuning *t);
 gp_status gp_get_tuning(const gp_driver *drv, gp_tuning *t);

@@ -1,11 +1,13 @@
 """Autotuner for the compile pipeline's launch shapes.
 
 The tunables are those of ``gp_tuning``: threads and resident blocks per SM
-for the stage-1 walk, and threads and blocks per SM for the grid-stride
-stage-2 kernels.  The tuner times candidate shapes on the caller's own
-workload (device-resident inputs, CUDA events on the compile stream, median
-of a few compiles after a warm-up) by coordinate search: stage 1 first with
-stage 2 fixed, then stage 2 with the chosen stage 1.  Results are cached per
+for the stage-1 walk, threads and blocks per SM for the grid-stride stage-2
+kernels, and how the observable walk is split (observable word columns, and
+the most time segments of one observable walk).  The tuner times candidate
+shapes on the caller's own workload (device-resident inputs, CUDA events on
+the compile stream, median of a few compiles after a warm-up) by coordinate
+search: stage 1 first with the rest fixed, then stage 2, then the observable
+split, each with the choices made before it.  Results are cached per
 workload signature.  Tuning changes only speed: the compile's outputs are
 identical under every shape (classes are numbered by their smallest member
 and class sums are exact integers).
@@ -22,6 +24,10 @@ from . import native
 
 STAGE1 = [(256, 0), (512, 0), (1024, 0), (512, 1), (256, 1)]
 STAGE2 = [(256, 8), (128, 16), (512, 4), (256, 4), (256, 16), (512, 8)]
+# (observable word columns, most time segments of one observable walk)
+OBS_SPLIT = [(4, 3), (1, 3), (2, 3), (8, 3), (4, 2), (4, 1)]
+FIELDS = ("stage1_threads", "stage1_blocks_per_sm", "stage2_threads", "stage2_blocks_per_sm", "obs_words",
+          "obs_segments")
 
 _cache: dict = {}
 
@@ -60,32 +66,34 @@ def autotune(driver, circuits, noise, level="L2", repeats: int = 5, cache_file: 
             pass
     if key in _cache:
         t = _cache[key]
-        driver.set_tuning(t["stage1_threads"], t["stage1_blocks_per_sm"], t["stage2_threads"],
-                          t["stage2_blocks_per_sm"])
+        driver.set_tuning(**{f: t[f] for f in FIELDS if f in t})
         return dict(t)
     best = driver.get_tuning()
     best_ms = float("inf")
     trials = []
+    n_obs = max(c.n_observables for c in (circuits if isinstance(circuits, (list, tuple)) else [circuits]))
+
+    def trial(**change):
+        nonlocal best, best_ms
+        shape = dict(best, **change)
+        try:
+            driver.set_tuning(**shape)
+            ms = _time(driver, circuits, noise, level, repeats)
+        except native.GpError:
+            return
+        trials.append((tuple(shape[f] for f in FIELDS), ms))
+        if ms < best_ms:
+            best_ms, best = ms, driver.get_tuning()
+
     for s1t, s1b in STAGE1:
-        try:
-            driver.set_tuning(s1t, s1b, best["stage2_threads"], best["stage2_blocks_per_sm"])
-            ms = _time(driver, circuits, noise, level, repeats)
-        except native.GpError:
-            continue
-        trials.append(((s1t, s1b, best["stage2_threads"], best["stage2_blocks_per_sm"]), ms))
-        if ms < best_ms:
-            best_ms, best = ms, driver.get_tuning()
+        trial(stage1_threads=s1t, stage1_blocks_per_sm=s1b)
     for s2t, s2b in STAGE2:
-        try:
-            driver.set_tuning(best["stage1_threads"], best["stage1_blocks_per_sm"], s2t, s2b)
-            ms = _time(driver, circuits, noise, level, repeats)
-        except native.GpError:
-            continue
-        trials.append(((best["stage1_threads"], best["stage1_blocks_per_sm"], s2t, s2b), ms))
-        if ms < best_ms:
-            best_ms, best = ms, driver.get_tuning()
-    driver.set_tuning(best["stage1_threads"], best["stage1_blocks_per_sm"], best["stage2_threads"],
-                      best["stage2_blocks_per_sm"])
+        trial(stage2_threads=s2t, stage2_blocks_per_sm=s2b)
+    if n_obs:
+        for ow, osg in OBS_SPLIT:
+            if ow <= max(n_obs, 1):
+                trial(obs_words=ow, obs_segments=osg)
+    driver.set_tuning(**best)
     if verbose:
         for shape, ms in trials:
             print(f"  tune {shape}: {ms:.3f} ms")

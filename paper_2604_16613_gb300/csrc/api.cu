@@ -74,7 +74,7 @@ bool bounds_ok(const gp_bounds &b, std::string &why) {
 Layout make_layout(const gp_bounds &b) {
     Layout L;
     L.max_tiles = (uint32_t)((b.max_ops + kRowTile - 1) / kRowTile) + b.max_circuits;
-    L.max_cols = b.max_detectors / 64u + 2u * b.max_circuits + 1u;
+    L.max_cols = b.max_detectors / 64u + (1u + kMaxObsWords) * b.max_circuits + 1u;
     L.max_layer_slots = b.max_layers + 2u * b.max_circuits;
     L.S = b.max_mask_words ? b.max_mask_words : (uint32_t)kMaxMaskWords;
     // classes never outnumber mechanisms: at least 1.5 slots per mechanism
@@ -106,7 +106,7 @@ Buffers carve_buffers(const gp_bounds &bd, const Layout &L, unsigned char *base,
     B.status = c.take<Status>(1);
     B.circ = c.take<CircuitDev>(bd.max_circuits);
     B.tiles = c.take<uint2>(L.max_tiles);
-    B.items = c.take<uint32_t>(L.max_cols + (kMaxSegments - 1u) * bd.max_circuits);   // + segment items
+    B.items = c.take<uint32_t>(L.max_cols + (kMaxSegments - 1u) * kMaxObsWords * bd.max_circuits);   // + segment items
     B.col_circ = c.take<uint32_t>(L.max_cols);
     if (params_bytes) *params_bytes = align_up(c.off, 256);
     B.ops_arena = c.take<uint4>(bd.max_ops);
@@ -191,10 +191,10 @@ struct gp_driver {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool exec_timing = false;
-    gp_tuning exec_tuning{0, 0, 0, 0};
+    gp_tuning exec_tuning{0, 0, 0, 0, 0, 0};
     uint32_t graph_kernels = 0;
     // tuning / instrumentation / test knobs
-    gp_tuning tuning{512, 0, 512, 8};
+    gp_tuning tuning{512, 0, 512, 8, 4, kMaxSegments};
     gp_debug debug{0, 0, 0, 0};
     bool timing = false;
     cudaEvent_t ev[5] = {};
@@ -307,6 +307,8 @@ gp_status enqueue_pipeline(gp_driver *d, cudaStream_t s, uint32_t *kernels) {
     return GP_OK;
 }
 
+// the launch shapes (the observable split only changes the work order the
+// host writes per compile)
 bool same_tuning(const gp_tuning &a, const gp_tuning &b) {
     return a.stage1_threads == b.stage1_threads && a.stage1_blocks_per_sm == b.stage1_blocks_per_sm &&
            a.stage2_threads == b.stage2_threads && a.stage2_blocks_per_sm == b.stage2_blocks_per_sm;
@@ -450,8 +452,10 @@ gp_status gp_set_tuning(gp_driver *d, const gp_tuning *t) {
     auto ok_threads = [](uint32_t x) { return x == 128 || x == 256 || x == 512; };
     if (!(ok_threads(t->stage1_threads) || t->stage1_threads == 1024) || !ok_threads(t->stage2_threads) ||
         t->stage2_blocks_per_sm == 0 ||
-        t->stage2_blocks_per_sm > 64 || t->stage1_blocks_per_sm > 64)
-        return fail(GP_ERR_INVALID, "tuning: stage-1 threads 128..1024, stage-2 threads 128..512 (powers of two); blocks per SM 1..64");
+        t->stage2_blocks_per_sm > 64 || t->stage1_blocks_per_sm > 64 || t->obs_words == 0 ||
+        t->obs_words > kMaxObsWords || t->obs_segments == 0 || t->obs_segments > kMaxSegments)
+        return fail(GP_ERR_INVALID, "tuning: stage-1 threads 128..1024, stage-2 threads 128..512 (powers of two); "
+                                    "blocks per SM 1..64; observable words 1..8; observable segments 1..3");
     d->tuning = *t;
     return GP_OK;
 }
@@ -581,7 +585,11 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
         C.det_base = (uint32_t)det_total;
         C.loc_base = (uint32_t)loc_total;
         C.col_base = cols_total;
-        C.n_cols = (c.n_detectors + 63u) / 64u + (c.n_observables ? 1u : 0u);
+        // the observables split evenly over up to obs_words word columns
+        C.n_ocols = std::min(c.n_observables, d->tuning.obs_words);
+        C.obs_per = C.n_ocols ? (c.n_observables + C.n_ocols - 1u) / C.n_ocols : 0u;
+        if (C.n_ocols) C.n_ocols = (c.n_observables + C.obs_per - 1u) / C.obs_per;
+        C.n_cols = (c.n_detectors + 63u) / 64u + C.n_ocols;
         C.tile_first = tiles_total;
         C.n_tiles = (uint32_t)((c.n_ops + kRowTile - 1) / kRowTile);
         ops_total += c.n_ops;
@@ -598,7 +606,7 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
             return fail(GP_ERR_CAPACITY, "batch too large for the driver");
     }
     // stage-1 work order: observable words first (they span whole circuits;
-    // with the role-split walk each is kMaxSegments items, one per segment,
+    // with the role-split walk each is obs_segments items, one per segment,
     // the latest-starting first), then detector words in order
     const uint32_t want1 = d->tuning.stage1_blocks_per_sm ? d->tuning.stage1_blocks_per_sm : 1u;
     const bool split_walk = stage1_shape(bd.max_qubits, want1, d->smem_limit).split != 0u;
@@ -607,14 +615,15 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
         const CircuitDev &C = hc[b];
         for (uint32_t k = 0; k < C.n_cols; k++) hcolc[C.col_base + k] = b;
     }
-    for (uint32_t k = split_walk ? kMaxSegments : 1u; k-- > 0;)
+    const uint32_t n_seg = split_walk ? d->tuning.obs_segments : 1u;
+    for (uint32_t k = n_seg; k-- > 0;)
         for (uint32_t b = 0; b < n_circuits; b++) {
             const CircuitDev &C = hc[b];
-            if (C.n_obs) hitems[ni++] = (C.col_base + C.n_cols - 1) | (k << kSegShift);
+            for (uint32_t o = C.n_cols - C.n_ocols; o < C.n_cols; o++) hitems[ni++] = (C.col_base + o) | (k << kSegShift);
         }
     for (uint32_t b = 0; b < n_circuits; b++) {
         const CircuitDev &C = hc[b];
-        const uint32_t nd = C.n_cols - (C.n_obs ? 1u : 0u);
+        const uint32_t nd = C.n_cols - C.n_ocols;
         for (uint32_t k = 0; k < nd; k++) hitems[ni++] = C.col_base + k;
     }
     for (uint32_t b = 0, t = 0; b < n_circuits; b++)
@@ -694,6 +703,7 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     P->wait_limit = d->debug.wait_limit ? d->debug.wait_limit : kWaitPolls;
     P->stall_windows = d->debug.stall_windows;
     P->ov_cap = L.ov_cap;
+    P->obs_segments = n_seg;
     // ---- pipeline: one graph launch ----------------------------------------------
     {
         const gp_status gs = ensure_graph(d);

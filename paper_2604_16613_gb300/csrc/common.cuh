@@ -28,6 +28,7 @@ constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint32_t kSegShift = 30;
 constexpr uint32_t kColMask = (1u << kSegShift) - 1u;
 constexpr uint32_t kMaxSegments = 3;
+constexpr uint32_t kMaxObsWords = 8;      // observable word columns per circuit
 constexpr uint32_t kObsColFlag = 0x80000000u;   // set on the column id of an
                                                 // observable word in a mask
 
@@ -40,7 +41,10 @@ struct CircuitDev {
     uint32_t n_ops, n_recs;
     uint32_t n_qubits, n_det, n_obs, n_loc;
     uint32_t col_base, n_cols; // global word columns: detector words, then
-                               // the observable word when n_obs > 0
+                               // n_ocols observable words
+    uint32_t n_ocols, obs_per; // observable words; observables per word
+                               // (word k holds observables k*obs_per ..)
+    uint32_t pad0, pad1;
     uint32_t det_base, loc_base, op_base, tile_first;
     uint32_t n_tiles;
     // filled by the lowering kernels
@@ -76,6 +80,7 @@ struct Params {
     uint32_t wait_limit;        // polls of a bounded wait (never 0 on the device)
     uint32_t stall_windows;     // 1: stage 1 stages no window
     uint32_t ov_cap;            // capacity of the overflow word list
+    uint32_t obs_segments;      // most work items of one observable walk
 };
 
 // device status block (read back by the host after every compile)

@@ -155,8 +155,8 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
 }
 
 // The (measurement, word) entries of one word column (Eq. init-slp): each
-// measurement a detector of the column (or the observable) reads, with the
-// column bit it sets, sorted by measurement, each run merged into its first
+// measurement a detector of the column (or an observable of an observable
+// word) reads, with the column bit it sets, sorted by measurement, each run merged into its first
 // entry, and each entry's layer and qubit.  Every thread of the block calls
 // it, with nent_sh and lmax_sh zeroed.  Returns the entry count, or 0 when
 // the column has nothing to walk (no entries, every word cancelled, or over
@@ -182,10 +182,13 @@ __device__ uint32_t column_entries(const Buffers &B, const CircuitDev &C, uint32
             }
         }
     } else {
+        // observable word k holds observables k * obs_per .. (bit = observable)
+        const uint32_t o0 = (local - (C.n_cols - C.n_ocols)) * C.obs_per, o1 = o0 + C.obs_per;
         const uint32_t n_rows = B.obs_count[cidx];
         for (uint32_t i0 = threadIdx.x; i0 < n_rows; i0 += NT) {
             const uint32_t row = B.obs_rows[C.op_base + i0];
             const uint4 op = C.ops[row];
+            if (op.w < o0 || op.w >= o1) continue;
             const uint32_t mb = B.aux[C.op_base + row];
             for (uint32_t i = 0; i < op.z; i++) {
                 const uint32_t e = atomicAdd(&nent_sh, 1u);
@@ -358,7 +361,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_kernel(Buffers B, uint32_t maxq,
         const uint32_t b = B.col_circ[gcol];
         const CircuitDev &C = B.circ[b];
         const uint32_t local = gcol - C.col_base;
-        const bool is_obs = (C.n_obs > 0u) && (local == C.n_cols - 1u);
+        const bool is_obs = local >= C.n_cols - C.n_ocols;
         const uint32_t col_tag = gcol | (is_obs ? kObsColFlag : 0u);
         const uint32_t nq = C.n_qubits;
         const uint32_t mech_base = C.mech_base;
@@ -920,7 +923,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         const uint32_t cidx = B.col_circ[gcol];
         const CircuitDev &C = B.circ[cidx];
         const uint32_t local = gcol - C.col_base;
-        const bool is_obs = (C.n_obs > 0u) && (local == C.n_cols - 1u);
+        const bool is_obs = local >= C.n_cols - C.n_ocols;
         const uint32_t col_tag = gcol | (is_obs ? kObsColFlag : 0u);
         const uint32_t nq = C.n_qubits;
         const uint32_t mech_base = C.mech_base;
@@ -941,7 +944,9 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         // 0.73 of an emitting one, so segments of equal time emit, from the
         // top: 79 % / 21 % of the walk (two segments), 74.5 % / 20 % / 5.5 %
         // (three).
-        const uint32_t n_seg = !is_obs ? 1u : (lmax >= 2u * kSplitMinLayers ? 3u : (lmax >= kSplitMinLayers ? 2u : 1u));
+        const uint32_t n_seg = !is_obs ? 1u
+                                       : min(P.obs_segments,
+                                             lmax >= 2u * kSplitMinLayers ? 3u : (lmax >= kSplitMinLayers ? 2u : 1u));
         if (seg >= n_seg) { __syncthreads(); continue; }
         int b1 = -1, b2 = -1;                             // segment boundaries
         if (n_seg == 2u) b1 = max(1, (int)(3u * lmax / 14u));

@@ -289,8 +289,10 @@ class Driver:
         return g[:self._last_noise_len]
 
     # -- knobs -------------------------------------------------------------------
-    def set_tuning(self, stage1_threads=512, stage1_blocks_per_sm=0, stage2_threads=512, stage2_blocks_per_sm=8):
-        t = native.GpTuning(stage1_threads, stage1_blocks_per_sm, stage2_threads, stage2_blocks_per_sm)
+    def set_tuning(self, stage1_threads=512, stage1_blocks_per_sm=0, stage2_threads=512, stage2_blocks_per_sm=8,
+                   obs_words=4, obs_segments=3):
+        t = native.GpTuning(stage1_threads, stage1_blocks_per_sm, stage2_threads, stage2_blocks_per_sm, obs_words,
+                            obs_segments)
         native.check(self.lib.gp_set_tuning(self.handle, ctypes.byref(t)))
 
     def get_tuning(self) -> dict:

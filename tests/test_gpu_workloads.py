@@ -15,6 +15,7 @@ import oracle
 from paper_2604_16613_gb300 import circuits as C
 from paper_2604_16613_gb300.autotune import autotune
 from paper_2604_16613_gb300.dem import Bounds, DemFunction, DeviceCircuit, Driver
+from paper_2604_16613_gb300.native import GpError
 
 from parity import compare_arrays, compare_edges, oracle_arrays, oracle_edges
 
@@ -150,6 +151,31 @@ def test_autotune_does_not_change_results():
             assert np.array_equal(base[k], other[k]), (shape, k)
 
 
+def test_observable_split_does_not_change_results():
+    """The observables of a circuit may be walked as 1 to 8 word columns,
+    each in 1 to 3 time segments: the compile is the same bit for bit, and
+    equal to the oracle.  The [[144,12,12]] code has 12 logicals (uneven
+    splits at 5 and 8 columns); the random circuits have one or two."""
+    circs = [C.bb_memory(3, C.NoiseModel.uniform(1e-3), seed=3),
+             C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))]
+    circs += [C.random_circuit(s) for s in range(6)]
+    noises = [f32(c.default_noise) for c in circs]
+    noise = torch.tensor(np.concatenate(noises), device="cuda")
+    dcs = [DeviceCircuit(c) for c in circs]
+    drv = Driver.for_circuits(circs)
+    base = drv.compile(dcs, noise).to_host()
+    for i, (c, nz) in enumerate(zip(circs, noises)):
+        compare_arrays(base, i, oracle_arrays((c.ops, c.recs, c.n_qubits, nz.astype(np.float64), "L2")), f"circuit {i}")
+    for ow, osg in [(1, 3), (2, 1), (5, 2), (8, 3), (3, 1)]:
+        drv.set_tuning(obs_words=ow, obs_segments=osg)
+        got = drv.compile(dcs, noise).to_host()
+        for k in base:
+            assert np.array_equal(base[k], got[k]), (ow, osg, k)
+    for bad in [dict(obs_words=0), dict(obs_words=9), dict(obs_segments=0), dict(obs_segments=4)]:
+        with pytest.raises(GpError):
+            drv.set_tuning(**bad)
+
+
 def test_block_wide_walk_equals_role_split_walk():
     """Stage 1 has two walks: the role-split one (a walker warp and emitter
     warps, used when its per-qubit tables fit in shared memory) and the
@@ -164,7 +190,7 @@ def test_block_wide_walk_equals_role_split_walk():
     bd = Bounds.for_circuits(circs)
     bd.max_qubits = 4096
     wide = Driver(bd)
-    for shape in [(512, 1, 256, 16), (256, 2, 256, 16), (128, 1, 256, 16)]:
+    for shape in [(512, 1, 256, 16), (256, 2, 256, 16, 1, 3), (128, 1, 256, 16, 8, 2)]:
         wide.set_tuning(*shape)
         got = wide.compile(dcs, noise).to_host()
         for k in split:
