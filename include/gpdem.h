@@ -70,6 +70,8 @@ typedef enum { GP_L0 = 0, GP_L1 = 1, GP_L2 = 2 } gp_level;
  *   X_ERROR, Z_ERROR,
  *   DEPOLARIZE1               a = qubit, c = noise location
  *   DEPOLARIZE2               a, b = qubits, c = noise location
+ *   NOP                       no operation (the row is ignored; the server
+ *                             blanks the noise rows it leaves out with it)
  * recs[] holds measurement-record lookbacks k >= 1 (k-th most recent
  * measurement before the annotation).  Between two TICKs a qubit takes part
  * in at most one gate; a noise row on a qubit that still has a gate later in
@@ -77,7 +79,7 @@ typedef enum { GP_L0 = 0, GP_L1 = 1, GP_L2 = 2 } gp_level;
  * row must be on the same side for both qubits).  Violations give
  * GP_ERR_INVALID. */
 enum {
-    GP_TICK = 0, GP_R = 1, GP_M = 2, GP_MR = 3, GP_RX = 4, GP_MX = 5, GP_MRX = 6,
+    GP_TICK = 0, GP_R = 1, GP_M = 2, GP_MR = 3, GP_RX = 4, GP_MX = 5, GP_MRX = 6, GP_NOP = 7,
     GP_H = 8, GP_S = 9, GP_CX = 10, GP_CZ = 11,
     GP_DETECTOR = 16, GP_OBSERVABLE_INCLUDE = 17,
     GP_X_ERROR = 32, GP_Z_ERROR = 33, GP_DEPOLARIZE1 = 34, GP_DEPOLARIZE2 = 35

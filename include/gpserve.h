@@ -16,7 +16,9 @@
  *     are emptied), and, unless t_b is the patch's final cycle, the window
  *     is closed by a Z measurement of every qubit of the declared logicals
  *     and one observable per logical, so observable bits are those of the
- *     logical frame at the cycle boundary;
+ *     logical frame at the cycle boundary; the noise of its last H cycles
+ *     is then left out (their mechanisms only flip detectors after every
+ *     cycle the window seals, so no delivered hyperedge holds one);
  *   - all windows of a step are compiled in one batched launch
  *     (gp_compile_batch), and a hyperedge is delivered with request t when
  *     its smallest detector lies in cycle t - H (the final request of a
@@ -148,6 +150,10 @@ gp_status gp_server_step(gp_server *srv, gp_level level, void *stream, uint32_t 
  * requests; then the compile's device stages (lowering, stage 1, grouping,
  * compaction) as gp_last_timing reports them. */
 gp_status gp_server_last_timing(const gp_server *srv, float times_us[8]);
+
+/* Launch and work-split parameters of the server's compiles (gp_tuning,
+ * gp_set_tuning's checks); none changes a result.  Not in the paper. */
+gp_status gp_server_set_tuning(gp_server *srv, const gp_tuning *t);
 
 /* Ids of requests finished since the last call (at most cap; *n receives
  * the count). */

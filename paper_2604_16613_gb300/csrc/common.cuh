@@ -165,7 +165,7 @@ struct Buffers {
 // row kinds (flat format)
 // ---------------------------------------------------------------------------
 enum Kind : uint32_t {
-    K_TICK = 0, K_R = 1, K_M = 2, K_MR = 3, K_RX = 4, K_MX = 5, K_MRX = 6,
+    K_TICK = 0, K_R = 1, K_M = 2, K_MR = 3, K_RX = 4, K_MX = 5, K_MRX = 6, K_NOP = 7,
     K_H = 8, K_S = 9, K_CX = 10, K_CZ = 11, K_DET = 16, K_OBS = 17,
     K_XERR = 32, K_ZERR = 33, K_DEP1 = 34, K_DEP2 = 35
 };

@@ -244,6 +244,8 @@ __device__ __forceinline__ void tile_lower_one(const Buffers &B, const Params &P
         case K_TICK:
             B.layer_start[C.layer_base + ticks + 1] = r + 1;
             break;
+        case K_NOP:
+            break;
         case K_R: case K_RX: case K_H: case K_S:
             bad = op.y >= C.n_qubits;
             break;

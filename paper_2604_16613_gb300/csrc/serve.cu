@@ -8,16 +8,20 @@
 //     the batch arena, shifting record and location indices to the window,
 //     emptying the detectors of records-only cycles (and zeroing their noise
 //     in a final window) and appending the rows that close a window with the
-//     declared logicals;
+//     declared logicals; the noise rows of a window's last H cycles are
+//     left out unless the window ends its patch (no hyperedge it delivers
+//     can hold one of their mechanisms);
 //   - the windows are compiled as one batch (gp_compile_batch);
-//   - seal: a horizon test per window (no mechanism of a records-only cycle
-//     c flips a detector after cycle c + H: those detectors all lie in the
-//     window, so a violation shows); then, for each request slot r of the
-//     windows (their r-th merged cycle), a flag per hyperedge (sealed, and
-//     its smallest detector lies in the cycle that request seals), a scan
-//     and a compaction of those hyperedges with patch-global detector ids.
-//     Every request's hyperedges thus come out contiguous and are copied to
-//     the host in slices.
+//   - seal (one captured graph of four kernels): a horizon test per window
+//     (no mechanism of a records-only cycle c flips a detector after cycle
+//     c + H: those detectors all lie in the window, so a violation shows);
+//     the request slot of every hyperedge (the request whose cycle holds its
+//     smallest detector; none when that cycle is not sealed yet), counted
+//     per chunk of a window's hyperedges; the request starts (slot, then
+//     window order); and every delivered hyperedge written, with
+//     patch-global detector ids, straight into a pinned host buffer.  Every
+//     request's hyperedges thus come out contiguous, and the host hands out
+//     slices.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -64,10 +68,11 @@ struct SegDesc {
     uint32_t n_ops, n_recs, n_loc;
     uint32_t dst_ops, dst_recs, dst_loc;
     uint32_t rec_shift, loc_shift;
-    uint32_t flags;             // kSegRecordsOnly | kSegZeroNoise
+    uint32_t flags;             // kSegRecordsOnly | kSegZeroNoise | kSegNoNoise
     uint32_t pad;
 };
-constexpr uint32_t kSegRecordsOnly = 1u, kSegZeroNoise = 2u;
+// kSegNoNoise: the cycle's noise rows become NOP rows (no mechanisms)
+constexpr uint32_t kSegRecordsOnly = 1u, kSegZeroNoise = 2u, kSegNoNoise = 4u;
 
 // what a window seals
 struct SealDesc {
@@ -99,7 +104,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(const SegDesc *seg, uint3
             op.y += d.rec_shift;
             if ((d.flags & kSegRecordsOnly) && k == K_DET) op.z = 0u;
         } else if (is_noise(k)) {
-            op.w += d.loc_shift;
+            if (d.flags & kSegNoNoise) op = make_uint4(K_NOP, 0u, 0u, 0u);
+            else op.w += d.loc_shift;
         }
         ops[d.dst_ops + i] = op;
     }
@@ -108,87 +114,115 @@ __global__ void __launch_bounds__(256) assemble_kernel(const SegDesc *seg, uint3
         noise[d.dst_loc + i] = (d.flags & kSegZeroNoise) ? 0.0f : d.noise[i];
 }
 
-// scan input per hyperedge: (delivered with request slot r, detector count)
-__global__ void seal_flags_kernel(Buffers B, const SealDesc *seal, const uint32_t *cyc_tab, uint32_t tab_stride,
-                                  uint32_t r) {
-    const uint32_t E = B.status->n_edges;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        const uint32_t w = B.edge_circ[e];
-        const SealDesc &sd = seal[w];
-        const uint32_t o0 = B.det_off[e], o1 = B.det_off[e + 1];
-        bool take;
-        if (o1 > o0) {
-            const uint32_t d0 = B.det_idx[o0];          // detector lists are ascending
-            take = d0 >= sd.det_lo && d0 < sd.det_hi;
-            if (take) {
-                // cycle of d0 within the window: last j with tab[j] <= d0
-                const uint32_t *tab = cyc_tab + (size_t)w * tab_stride;
-                uint32_t lo = 0, hi = sd.n_cyc;
-                while (hi - lo > 1u) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (tab[mid] <= d0) lo = mid; else hi = mid;
-                }
-                const int32_t slot = min((int32_t)lo + sd.r_off, (int32_t)sd.r_max);
-                take = slot == (int32_t)r;
-            }
-        } else {
-            take = sd.take_no_det != 0u && sd.r_max == r;
-        }
-        B.scan_val[e] = take ? make_uint2(1u, o1 - o0) : make_uint2(0u, 0u);
-    }
-}
-
 // What the select phase of a step needs beyond the compile: the windows,
-// the request slots (passes) and the pinned step buffer.  The host fills a
-// pinned copy before each step; a copy inside the captured select graph
-// brings it to the device, so the graph's kernels never change.
+// the request slots and the pinned step buffer.  The host fills a pinned
+// copy before each step; a copy inside the captured select graph brings it
+// to the device, so the graph's kernels never change.
 struct SealOut {
     uint32_t *doff, *det;
     float *prob, *logodds;
     unsigned long long *obs;
 };
 struct SelParams {
-    uint32_t n_win, n_pass;
-    uint64_t edges_cap, det_cap;
-    SealOut host;
+    uint32_t n_win, n_slots;        // windows; request slots (most requests of a window)
+    uint64_t edges_cap, det_cap;    // of the pinned step buffer
+    SealOut host;                   // the pinned step buffer
 };
 
-// first hyperedge of every window (from the compile's per-circuit counts)
-__global__ void win_edges_kernel(Buffers B, const SelParams *sp, uint32_t *win_e0) {
+// The select phase reads a window's hyperedges in chunks of kSelChunk, one
+// per thread of a block; a chunk never spans two windows.
+constexpr uint32_t kSelChunk = 1024;
+constexpr uint32_t kSelThreads = kSelChunk;
+constexpr uint32_t kMaxSlots = 512;     // request slots: max_cycles_per_step at most
+
+// device scratch of the select phase
+struct SelScratch {
+    uint32_t *win_e0;               // n_win + 1: first hyperedge of each window
+    uint32_t *chunk0;               // n_win + 1: first chunk of each window
+    uint2 *chunk_tot;               // per chunk and slot: delivered (edges, detector ids), then their output base
+    unsigned long long *tot;        // per slot and window: packed totals (edges << 32 | ids), then starts
+    uint2 *starts;                  // per slot: n_win + 1 output starts (device copy)
+};
+
+// the window holding chunk c: the last w < n_win with chunk0[w] <= c
+__device__ __forceinline__ uint32_t chunk_window(const uint32_t *chunk0, uint32_t n_win, uint32_t c) {
+    uint32_t lo = 0, hi = n_win;
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (chunk0[mid] <= c) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// first hyperedge and first chunk of every window (from the compile's
+// per-circuit counts); clears the horizon flags
+__global__ void sel_prep_kernel(Buffers B, const SelParams *sp, SelScratch sc, uint32_t *horizon) {
     const uint32_t n_win = sp->n_win;
     if (threadIdx.x == 0) {
-        uint32_t run = 0;
+        uint32_t e = 0, c = 0;
         for (uint32_t w = 0; w < n_win; w++) {
-            win_e0[w] = run;
-            run += B.circ_edges[w];
+            sc.win_e0[w] = e;
+            sc.chunk0[w] = c;
+            const uint32_t n = B.circ_edges[w];
+            e += n;
+            c += (n + kSelChunk - 1u) / kSelChunk;
         }
-        win_e0[n_win] = run;
+        sc.win_e0[n_win] = e;
+        sc.chunk0[n_win] = c;
     }
+    for (uint32_t w = threadIdx.x; w < n_win; w += blockDim.x) horizon[w] = 0u;
 }
 
-// after the scan of slot r: where its hyperedges and detector ids start for
-// every window (after those of slots 0 .. r-1); the last detector offset of
-// every request (r, w) -- offsets are per request, and request (r, w) is the
-// (r n_win + w)-th, so its offsets sit r n_win + w entries after its edges
-__global__ void slot_starts_kernel(Buffers B, const SelParams *sp, const uint32_t *win_e0, uint32_t r, uint2 *starts,
-                                   uint32_t *doff) {
-    const uint32_t E = B.status->n_edges, n_win = sp->n_win;
-    const uint2 base = r ? starts[(size_t)(r - 1u) * (n_win + 1u) + n_win] : make_uint2(0u, 0u);
-    uint2 *row = starts + (size_t)r * (n_win + 1u);
-    for (uint32_t w = threadIdx.x; w <= n_win; w += blockDim.x) {
-        const uint2 c = B.comp_off[w < n_win ? win_e0[w] : E];
-        row[w] = make_uint2(base.x + c.x, base.y + c.y);
+// Per hyperedge: the request slot that delivers it (its smallest detector
+// lies in the cycle that request seals), stored with its detector count;
+// per chunk: the delivered hyperedges and detector ids of every slot.
+// Then the horizon test: a mechanism of records-only cycle c flipping a
+// detector after cycle c + H means the window's horizon was too short.
+__global__ void __launch_bounds__(kSelThreads) sel_count_kernel(Buffers B, const SealDesc *seal, const uint32_t *cyc_tab,
+                                                                uint32_t tab_stride, const uint2 *rec_tab,
+                                                                uint32_t max_h, const SelParams *sp, SelScratch sc,
+                                                                uint32_t *horizon) {
+    extern __shared__ uint2 slot_cnt[];   // n_slots
+    const uint32_t n_win = sp->n_win, R = sp->n_slots, n_chunks = sc.chunk0[n_win];
+    for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const uint32_t w = chunk_window(sc.chunk0, n_win, c);
+        for (uint32_t i = threadIdx.x; i < R; i += blockDim.x) slot_cnt[i] = make_uint2(0u, 0u);
+        __syncthreads();
+        const uint32_t e = sc.win_e0[w] + (c - sc.chunk0[w]) * kSelChunk + threadIdx.x;
+        uint32_t key = 0u, nd = 0u;            // key: slot + 1, or 0 (not delivered this step)
+        if (e < sc.win_e0[w + 1]) {
+            const SealDesc &sd = seal[w];
+            const uint32_t o0 = B.det_off[e], o1 = B.det_off[e + 1];
+            nd = o1 - o0;
+            if (o1 > o0) {
+                const uint32_t d0 = B.det_idx[o0];          // detector lists are ascending
+                if (d0 >= sd.det_lo && d0 < sd.det_hi) {
+                    // cycle of d0 within the window: last j with tab[j] <= d0
+                    const uint32_t *tab = cyc_tab + (size_t)w * tab_stride;
+                    uint32_t lo = 0, hi = sd.n_cyc;
+                    while (hi - lo > 1u) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (tab[mid] <= d0) lo = mid; else hi = mid;
+                    }
+                    key = (uint32_t)min((int32_t)lo + sd.r_off, (int32_t)sd.r_max) + 1u;
+                }
+            } else if (sd.take_no_det) {
+                key = sd.r_max + 1u;
+            }
+            B.scan_val[e] = make_uint2(key, nd);
+        }
+        // one shared add per slot and warp
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+        const uint32_t sum = __reduce_add_sync(peers, nd);
+        if (key != 0u && (threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1)) {
+            atomicAdd(&slot_cnt[key - 1u].x, (uint32_t)__popc(peers));
+            atomicAdd(&slot_cnt[key - 1u].y, sum);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < R; i += blockDim.x) sc.chunk_tot[(size_t)c * R + i] = slot_cnt[i];
+        __syncthreads();
     }
-    __syncthreads();
-    for (uint32_t w = threadIdx.x; w < n_win; w += blockDim.x)
-        doff[row[w + 1].x + r * n_win + w] = row[w + 1].y - row[w].y;
-}
-
-// a mechanism of records-only cycle c flipping a detector after cycle c + H:
-// the window's horizon was too short
-__global__ void seal_horizon_kernel(Buffers B, const SealDesc *seal, const uint2 *rec_tab, uint32_t max_h,
-                                    const SelParams *sp, uint32_t *horizon) {
-    for (uint32_t w = blockIdx.x; w < sp->n_win; w += gridDim.x) {
+    for (uint32_t w = blockIdx.x; w < n_win; w += gridDim.x) {
         const uint32_t m0 = B.circ[w].mech_base, n = seal[w].n_mech_rec, nr = seal[w].n_rec;
         const uint2 *tab = rec_tab + (size_t)w * max_h;
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -203,52 +237,138 @@ __global__ void seal_horizon_kernel(Buffers B, const SealDesc *seal, const uint2
     }
 }
 
-__global__ void seal_write_kernel(Buffers B, const SealDesc *seal, SealOut out, const uint2 *starts, uint32_t r,
-                                  const SelParams *sp) {
-    const uint32_t E = B.status->n_edges, n_win = sp->n_win;
-    const uint2 *row = starts + (size_t)r * (n_win + 1u);
-    const uint2 base = row[0];
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        if (B.scan_val[e].x == 0u) continue;
-        const uint2 off = B.comp_off[e];
-        const uint32_t w = B.edge_circ[e], pos = base.x + off.x, dpos = base.y + off.y;
-        out.prob[pos] = B.prob[e];
-        out.logodds[pos] = B.logodds[e];
-        out.obs[pos] = B.obs_mask[e];
-        out.doff[pos + r * n_win + w] = dpos - row[w].y;
-        const uint32_t o0 = B.det_off[e], o1 = B.det_off[e + 1], db = seal[w].det_base;
-        for (uint32_t i = o0; i < o1; i++) out.det[dpos + (i - o0)] = B.det_idx[i] + db;
+// Output order: request slot, then window, then hyperedge.  Totals per
+// (slot, window), their exclusive scan (the request starts, also written to
+// the host), each chunk's base within its request, and the last detector
+// offset of every request (offsets are per request, and request (r, w) is
+// the (r n_win + w)-th, so its offsets sit r n_win + w entries after its
+// hyperedges).  One block.
+__global__ void __launch_bounds__(kSelThreads) sel_starts_kernel(const SelParams *sp, SelScratch sc, uint2 *starts_host) {
+    __shared__ unsigned long long warp_tot[kSelThreads / 32];
+    const uint32_t n_win = sp->n_win, R = sp->n_slots, P = R * n_win;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t r = i / n_win, w = i % n_win;
+        unsigned long long t = 0ull;
+        for (uint32_t c = sc.chunk0[w]; c < sc.chunk0[w + 1]; c++) {
+            const uint2 v = sc.chunk_tot[(size_t)c * R + r];
+            t += ((unsigned long long)v.x << 32) + v.y;
+        }
+        sc.tot[i] = t;
+    }
+    __syncthreads();
+    unsigned long long run = 0ull;
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const unsigned long long v = i < P ? sc.tot[i] : 0ull;
+        unsigned long long x = v;
+        for (uint32_t o = 1; o < 32u; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31u) warp_tot[warp] = x;
+        __syncthreads();
+        unsigned long long before = 0ull, all = 0ull;
+        for (uint32_t k = 0; k < blockDim.x / 32u; k++) {
+            if (k < warp) before += warp_tot[k];
+            all += warp_tot[k];
+        }
+        if (i < P) sc.tot[i] = run + before + x - v;
+        run += all;
+        __syncthreads();
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < R * (n_win + 1u); i += blockDim.x) {
+        const uint32_t r = i / (n_win + 1u), w = i % (n_win + 1u);
+        const unsigned long long v = w < n_win ? sc.tot[r * n_win + w] : (r + 1u < R ? sc.tot[(r + 1u) * n_win] : run);
+        const uint2 st = make_uint2((uint32_t)(v >> 32), (uint32_t)v);
+        sc.starts[i] = st;
+        starts_host[i] = st;
+    }
+    const SealOut out = sp->host;
+    const uint64_t edges_cap = sp->edges_cap;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t r = i / n_win, w = i % n_win;
+        const unsigned long long b0 = sc.tot[i];
+        unsigned long long b = b0;
+        for (uint32_t c = sc.chunk0[w]; c < sc.chunk0[w + 1]; c++) {
+            const uint2 v = sc.chunk_tot[(size_t)c * R + r];
+            sc.chunk_tot[(size_t)c * R + r] = make_uint2((uint32_t)(b >> 32), (uint32_t)b);
+            b += ((unsigned long long)v.x << 32) + v.y;
+        }
+        const uint64_t at = (b >> 32) + (uint64_t)r * n_win + w;
+        if (at < edges_cap) out.doff[at] = (uint32_t)b - (uint32_t)b0;
     }
 }
 
-// n 4-byte words from device memory into pinned host memory (both ends
-// 16-byte aligned: whole 16-byte moves, then the tail)
-__device__ __forceinline__ void copy_words(uint32_t *dst, const uint32_t *src, uint64_t n, uint64_t t, uint64_t nt) {
-    const uint64_t n4 = n / 4;
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-    for (uint64_t i = t; i < n4; i += nt) d4[i] = s4[i];
-    for (uint64_t i = 4 * n4 + t; i < n; i += nt) dst[i] = src[i];
-}
-
-// after the last slot's pass: the step's hyperedges, per-request detector
-// offsets and detector ids into the pinned step buffer, sized by the totals
-// on the device (tot = edges and detector ids over all slots)
-// (the counts are clamped to the buffer's capacity; the host checks them)
-__global__ void seal_copy_kernel(SealOut dev, const SelParams *sp, const uint2 *starts) {
-    const uint32_t n_win = sp->n_win, n_pass = sp->n_pass;
-    const SealOut host = sp->host;
+// Every delivered hyperedge written straight into the pinned step buffer at
+// its place: the chunk's base in its request, plus those of the same slot
+// before it in the chunk (per warp, then across warps).
+__global__ void __launch_bounds__(kSelThreads) sel_write_kernel(Buffers B, const SealDesc *seal, const SelParams *sp,
+                                                                SelScratch sc) {
+    extern __shared__ uint2 warp_cnt[];   // [warp][slot]
+    const uint32_t n_win = sp->n_win, R = sp->n_slots, n_chunks = sc.chunk0[n_win];
+    const SealOut out = sp->host;
     const uint64_t edges_cap = sp->edges_cap, det_cap = sp->det_cap;
-    const uint32_t n_offs_extra = n_pass * n_win;
-    const uint2 tot = starts[(size_t)(n_pass - 1u) * (n_win + 1u) + n_win];
-    const uint64_t ne = min((uint64_t)tot.x, edges_cap), no = min((uint64_t)tot.x + n_offs_extra, edges_cap);
-    const uint64_t nd = min((uint64_t)tot.y, det_cap);
-    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
-    copy_words(host.doff, dev.doff, no, t, nt);
-    copy_words(host.det, dev.det, nd, t, nt);
-    copy_words(reinterpret_cast<uint32_t *>(host.prob), reinterpret_cast<const uint32_t *>(dev.prob), ne, t, nt);
-    copy_words(reinterpret_cast<uint32_t *>(host.logodds), reinterpret_cast<const uint32_t *>(dev.logodds), ne, t, nt);
-    copy_words(reinterpret_cast<uint32_t *>(host.obs), reinterpret_cast<const uint32_t *>(dev.obs), 2 * ne, t, nt);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    constexpr uint32_t kWarps = kSelThreads / 32u;
+    for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const uint32_t w = chunk_window(sc.chunk0, n_win, c);
+        for (uint32_t i = threadIdx.x; i < kWarps * R; i += blockDim.x) warp_cnt[i] = make_uint2(0u, 0u);
+        __syncthreads();
+        const uint32_t e = sc.win_e0[w] + (c - sc.chunk0[w]) * kSelChunk + threadIdx.x;
+        const uint2 kv = e < sc.win_e0[w + 1] ? B.scan_val[e] : make_uint2(0u, 0u);
+        const uint32_t key = kv.x, nd = kv.y;
+        // rank and detector-id prefix among this warp's hyperedges of the same slot
+        uint32_t rank = 0, dpre = 0;
+        unsigned todo = __ballot_sync(0xFFFFFFFFu, key != 0u);
+        while (todo) {
+            const uint32_t k = __shfl_sync(0xFFFFFFFFu, key, __ffs(todo) - 1);
+            const bool mine = key == k;
+            uint32_t x = mine ? nd : 0u;
+            for (uint32_t o = 1; o < 32u; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= o) x += y;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+            if (mine) {
+                rank = (uint32_t)__popc(m & lt);
+                dpre = x - nd;
+            }
+            if (lane == 0u) warp_cnt[warp * R + (k - 1u)] = make_uint2((uint32_t)__popc(m), total);
+            todo &= ~m;
+        }
+        __syncthreads();
+        for (uint32_t r = threadIdx.x; r < R; r += blockDim.x) {
+            uint2 run = make_uint2(0u, 0u);
+            for (uint32_t k = 0; k < kWarps; k++) {
+                const uint2 t = warp_cnt[k * R + r];
+                warp_cnt[k * R + r] = run;
+                run.x += t.x;
+                run.y += t.y;
+            }
+        }
+        __syncthreads();
+        if (key != 0u) {
+            const uint32_t r = key - 1u;
+            const uint2 base = sc.chunk_tot[(size_t)c * R + r], wb = warp_cnt[warp * R + r];
+            const uint64_t pos = (uint64_t)base.x + wb.x + rank, dpos = (uint64_t)base.y + wb.y + dpre;
+            if (pos < edges_cap) {
+                out.prob[pos] = B.prob[e];
+                out.logodds[pos] = B.logodds[e];
+                out.obs[pos] = B.obs_mask[e];
+            }
+            const uint64_t at = pos + (uint64_t)r * n_win + w;
+            if (at < edges_cap) out.doff[at] = (uint32_t)(dpos - sc.starts[r * (n_win + 1u) + w].y);
+            if (dpos + nd <= det_cap) {
+                const uint32_t o0 = B.det_off[e], db = seal[w].det_base;
+                for (uint32_t i = 0; i < nd; i++) out.det[dpos + i] = B.det_idx[o0 + i] + db;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 uint32_t n_comp_host(uint32_t kind, uint32_t level) {
@@ -351,17 +471,14 @@ struct gp_server {
     uint2 *d_rec_tab = nullptr;
     uint4 *d_extra_ops = nullptr;
     uint32_t *d_extra_recs = nullptr;
-    uint32_t *d_horizon = nullptr;
     uint32_t *d_cyc_tab = nullptr;       // per window: detector offset of each cycle
-    uint32_t *d_win_e0 = nullptr;        // per window: first hyperedge
-    uint2 *d_starts = nullptr;           // per request slot and window: output starts
+    SelScratch sel{};                    // select-phase scratch
     SelParams *d_sel = nullptr;          // the select phase's per-step parameters
     SelParams *h_sel = nullptr;          // ... their pinned host copy
-    cudaStream_t cap_stream = nullptr;   // captures the select graphs
-    std::vector<cudaGraphExec_t> sel_exec;   // select phase, one graph per pass count
+    cudaStream_t cap_stream = nullptr;   // captures the select graph
+    cudaGraphExec_t sel_exec = nullptr;  // the select phase
     float times[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // last step: build, compile, select, hand-out,
                                                  // then the compile's device stages (us)
-    SealOut out{};
     uint64_t out_edges_cap = 0, out_det_cap = 0;
     // pinned host memory
     unsigned char *h_desc = nullptr;     // segs | seals | extra ops | extra recs
@@ -370,8 +487,8 @@ struct gp_server {
     uint32_t *h_stage_recs = nullptr;
     float *h_stage_noise = nullptr;
     std::vector<uint32_t> free_stage;
-    uint32_t *h_horizon = nullptr;
-    uint2 *h_starts = nullptr;           // per request slot and window: output starts
+    uint32_t *h_horizon = nullptr;       // per window: horizon too short (written by the device)
+    uint2 *h_starts = nullptr;           // per request slot and window: output starts (ditto)
     std::vector<OutBuf *> out_pool;
     // state
     std::vector<Patch> patches;
@@ -474,6 +591,7 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
                                      "detectors, mechanisms and logical qubits may be zero)");
     if (c.max_qubits > 8192) return sfail(GP_ERR_INVALID, "server config: max_qubits above 8192");
     if (c.max_batch > c.max_patches) return sfail(GP_ERR_INVALID, "server config: max_batch above max_patches");
+    if (c.max_cycles_per_step > kMaxSlots) return sfail(GP_ERR_INVALID, "server config: max_cycles_per_step above 512");
     gp_server *s = new (std::nothrow) gp_server();
     if (!s) return sfail(GP_ERR_CAPACITY, "out of host memory");
     auto cleanup = [&](gp_status st) { gp_server_destroy(s); return st; };
@@ -538,16 +656,16 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
         s->d_rec_tab = carve_dev<uint2>(base, off, Bt * c.max_horizon);
         s->d_extra_ops = carve_dev<uint4>(base, off, Bt * s->extra_ops);
         s->d_extra_recs = carve_dev<uint32_t>(base, off, std::max<uint64_t>(Bt * s->extra_recs, 1));
-        s->d_horizon = carve_dev<uint32_t>(base, off, Bt);
-        s->out.doff = carve_dev<uint32_t>(base, off, s->out_edges_cap + (uint64_t)c.max_cycles_per_step * (Bt + 1));
-        s->out.det = carve_dev<uint32_t>(base, off, std::max<uint64_t>(s->out_det_cap, 1));
         s->d_cyc_tab = carve_dev<uint32_t>(base, off, Bt * (W + 1));
-        s->d_win_e0 = carve_dev<uint32_t>(base, off, Bt + 1);
-        s->d_starts = carve_dev<uint2>(base, off, (uint64_t)c.max_cycles_per_step * (Bt + 1));
+        const uint64_t K = c.max_cycles_per_step, max_chunks = s->out_edges_cap / kSelChunk + Bt + 1;
+        SelScratch sc{};
+        sc.win_e0 = carve_dev<uint32_t>(base, off, Bt + 1);
+        sc.chunk0 = carve_dev<uint32_t>(base, off, Bt + 1);
+        sc.chunk_tot = carve_dev<uint2>(base, off, max_chunks * K);
+        sc.tot = carve_dev<unsigned long long>(base, off, K * Bt);
+        sc.starts = carve_dev<uint2>(base, off, K * (Bt + 1));
+        if (base) s->sel = sc;
         s->d_sel = carve_dev<SelParams>(base, off, 1);
-        s->out.prob = carve_dev<float>(base, off, s->out_edges_cap);
-        s->out.logodds = carve_dev<float>(base, off, s->out_edges_cap);
-        s->out.obs = carve_dev<unsigned long long>(base, off, s->out_edges_cap);
         return off;
     };
     s->patches.resize(c.max_patches);
@@ -579,7 +697,6 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
         return cleanup(sfail(GP_ERR_CUDA, "cudaMallocHost of the server staging failed"));
     if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup(sfail(GP_ERR_CUDA, "cudaStreamCreate failed"));
-    s->sel_exec.assign(c.max_cycles_per_step + 1u, nullptr);
     for (uint32_t i = 0; i < c.max_pending; i++) s->free_stage.push_back(c.max_pending - 1 - i);
     *out = s;
     return GP_OK;
@@ -587,8 +704,7 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
 
 void gp_server_destroy(gp_server *s) {
     if (!s) return;
-    for (cudaGraphExec_t g : s->sel_exec)
-        if (g) cudaGraphExecDestroy(g);
+    if (s->sel_exec) cudaGraphExecDestroy(s->sel_exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->drv) gp_driver_destroy(s->drv);
     if (s->dmem) cudaFree(s->dmem);
@@ -659,38 +775,33 @@ gp_status gp_server_close_patch(gp_server *s, uint32_t patch) {
 
 namespace {
 
-// The select phase of a step with n_pass request slots, captured once as a
-// graph on the server's own stream and replayed on the caller's: clear the
-// horizon flags, bring the step's parameters to the device, the horizon
-// check, each window's first hyperedge, and per request slot the flags, the
-// scan, the starts and the write; then the copy into the pinned step buffer
-// and the read-back of the starts and the horizon flags.  Every size and
-// pointer that changes from step to step is read on the device from the
-// parameter block, so one graph per pass count serves every step.
-gp_status ensure_select_graph(gp_server *s, uint32_t n_pass) {
-    if (s->sel_exec[n_pass]) return GP_OK;
+// The select phase, captured once as a graph on the server's own stream and
+// replayed on the caller's: bring the step's parameters to the device, then
+// four kernels (windows' first hyperedges and chunks; per-chunk slot counts
+// and the horizon test; request starts; the writes into the pinned step
+// buffer).  The starts and horizon flags are written to pinned host memory
+// by the kernels themselves.  Every size and pointer that changes from step
+// to step is read on the device from the parameter block, so one graph
+// serves every step.
+gp_status ensure_select_graph(gp_server *s) {
+    if (s->sel_exec) return GP_OK;
     const gp_server_config &c = s->cfg;
-    const uint32_t Bt = c.max_batch;
     const Buffers &B = driver_buffers(s->drv);
-    const uint32_t grid = 4u * s->n_sms;
-    const uint32_t grid_h = std::max(1u, std::min<uint32_t>(Bt, 8u * s->n_sms));
+    const uint32_t grid = 2u * s->n_sms;
+    const size_t smem_count = (size_t)c.max_cycles_per_step * sizeof(uint2);
+    const size_t smem_write = (size_t)(kSelThreads / 32u) * c.max_cycles_per_step * sizeof(uint2);
+    if (smem_write > 48u * 1024u &&
+        cudaFuncSetAttribute(sel_write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_write) != cudaSuccess)
+        return sfail(GP_ERR_CUDA, "select graph: shared memory of the write kernel");
     cudaStream_t cs = s->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return sfail(GP_ERR_CUDA, std::string("select graph capture: ") + cudaGetErrorString(e));
-    uint32_t launches = 0;
-    cudaMemsetAsync(s->d_horizon, 0, Bt * sizeof(uint32_t), cs);
     cudaMemcpyAsync(s->d_sel, s->h_sel, sizeof(SelParams), cudaMemcpyHostToDevice, cs);
-    seal_horizon_kernel<<<grid_h, 256, 0, cs>>>(B, s->d_seal, s->d_rec_tab, c.max_horizon, s->d_sel, s->d_horizon);
-    win_edges_kernel<<<1, 32, 0, cs>>>(B, s->d_sel, s->d_win_e0);
-    for (uint32_t r = 0; r < n_pass; r++) {
-        seal_flags_kernel<<<grid, 256, 0, cs>>>(B, s->d_seal, s->d_cyc_tab, s->W + 1u, r);
-        launch_scan(B, B.scan_val, &B.status->n_edges, B.comp_off, s->out_edges_cap, driver_sms(s->drv), cs, &launches);
-        slot_starts_kernel<<<1, 256, 0, cs>>>(B, s->d_sel, s->d_win_e0, r, s->d_starts, s->out.doff);
-        seal_write_kernel<<<grid, 256, 0, cs>>>(B, s->d_seal, s->out, s->d_starts, r, s->d_sel);
-    }
-    seal_copy_kernel<<<grid, 256, 0, cs>>>(s->out, s->d_sel, s->d_starts);
-    cudaMemcpyAsync(s->h_starts, s->d_starts, (size_t)n_pass * (Bt + 1u) * sizeof(uint2), cudaMemcpyDeviceToHost, cs);
-    cudaMemcpyAsync(s->h_horizon, s->d_horizon, Bt * sizeof(uint32_t), cudaMemcpyDeviceToHost, cs);
+    sel_prep_kernel<<<1, 256, 0, cs>>>(B, s->d_sel, s->sel, s->h_horizon);
+    sel_count_kernel<<<grid, kSelThreads, smem_count, cs>>>(B, s->d_seal, s->d_cyc_tab, s->W + 1u, s->d_rec_tab,
+                                                            c.max_horizon, s->d_sel, s->sel, s->h_horizon);
+    sel_starts_kernel<<<1, kSelThreads, 0, cs>>>(s->d_sel, s->sel, s->h_starts);
+    sel_write_kernel<<<grid, kSelThreads, smem_write, cs>>>(B, s->d_seal, s->d_sel, s->sel);
     cudaGraph_t g = nullptr;
     const cudaError_t launch_err = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &g);
@@ -699,10 +810,10 @@ gp_status ensure_select_graph(gp_server *s, uint32_t n_pass) {
         return sfail(GP_ERR_CUDA, std::string("select graph capture: ") +
                                       cudaGetErrorString(launch_err != cudaSuccess ? launch_err : e));
     }
-    e = cudaGraphInstantiate(&s->sel_exec[n_pass], g, 0);
+    e = cudaGraphInstantiate(&s->sel_exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        s->sel_exec[n_pass] = nullptr;
+        s->sel_exec = nullptr;
         return sfail(GP_ERR_CUDA, std::string("select graph instantiate: ") + cudaGetErrorString(e));
     }
     return GP_OK;
@@ -969,7 +1080,13 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
             d.rec_shift = (uint32_t)(a_recs - recs0);
             d.loc_shift = (uint32_t)(a_loc - loc0);
             const bool rec_only = k < w.c0 + w.n_rec;
-            d.flags = (rec_only ? kSegRecordsOnly : 0u) | (rec_only && w.final ? kSegZeroNoise : 0u);
+            // a mechanism of the last H cycles of a window that does not end
+            // the patch only flips detectors of those cycles or later, after
+            // every cycle the window seals: its hyperedge is not delivered,
+            // and no delivered hyperedge has its mask, so it is left out
+            const bool unsealed = !w.final && k + P.H > w.t_b;
+            d.flags = (rec_only ? kSegRecordsOnly : 0u) | (rec_only && w.final ? kSegZeroNoise : 0u) |
+                      (unsealed ? kSegNoNoise : 0u);
             d.pad = 0;
             if (rec_only) mech_rec += ci.mech[(int)level];
             a_ops += ci.n_ops;
@@ -1063,19 +1180,23 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     const uint32_t rs = n_win + 1u;             // entries of one slot's row of starts
     OutBuf *ob = nullptr;
     if (cst == GP_OK && view.n_edges) {
-        // the step buffer is taken before the passes, for the batch's whole
-        // output (the sealed part is at most that), so one kernel can fill
-        // it and one synchronisation ends the step
-        ob = take_outbuf(s, view.n_edges, (uint64_t)n_pass * n_win, view.n_det_entries);
-        if (!ob) cst = sfail(GP_ERR_CUDA, "cudaMallocHost of a result buffer failed");
+        // the step buffer is taken before the select phase, for the batch's
+        // whole output (the sealed part is at most that), so the kernels can
+        // fill it and one synchronisation ends the step
+        if (view.n_det_entries > 0xFFFFFFFFull)
+            cst = sfail(GP_ERR_CAPACITY, "a step's detector ids exceed 32 bits");
+        if (cst == GP_OK) {
+            ob = take_outbuf(s, view.n_edges, (uint64_t)n_pass * n_win, view.n_det_entries);
+            if (!ob) cst = sfail(GP_ERR_CUDA, "cudaMallocHost of a result buffer failed");
+        }
         if (cst == GP_OK) {
             *s->h_sel = SelParams{n_win, n_pass, ob->edges_cap, ob->det_cap,
                                   SealOut{ob->doff, ob->det, ob->prob, ob->logodds, ob->obs}};
-            const gp_status gs = ensure_select_graph(s, n_pass);
+            const gp_status gs = ensure_select_graph(s);
             if (gs != GP_OK) cst = gs;
         }
         if (cst == GP_OK) {
-            SV_CUDA(cudaGraphLaunch(s->sel_exec[n_pass], st));
+            SV_CUDA(cudaGraphLaunch(s->sel_exec, st));
             SV_CUDA(cudaStreamSynchronize(st));
             const uint2 tot = s->h_starts[(size_t)(n_pass - 1u) * rs + n_win];
             if (tot.x + (uint64_t)n_pass * n_win > ob->edges_cap || tot.y > ob->det_cap)
@@ -1127,6 +1248,11 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     s->times[3] = (float)(t_done - t_selected) * 1e-3f;
     gp_last_timing(s->drv, s->times + 4);
     return cst;
+}
+
+gp_status gp_server_set_tuning(gp_server *s, const gp_tuning *t) {
+    if (!s || !t) return sfail(GP_ERR_INVALID, "null argument");
+    return gp_set_tuning(s->drv, t);
 }
 
 gp_status gp_server_last_timing(const gp_server *s, float times_us[8]) {

@@ -26,7 +26,7 @@ EXPORTED = [
     "gp_server_create", "gp_server_destroy", "gp_server_open_patch", "gp_server_close_patch",
     "gp_server_submit", "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release",
     "gp_server_register_cycle", "gp_server_submit_registered", "gp_server_submit_registered_many",
-    "gp_server_drain", "gp_server_last_timing",
+    "gp_server_drain", "gp_server_last_timing", "gp_server_set_tuning",
 ]
 
 
@@ -145,10 +145,12 @@ def load(path: str = LIB_PATH):
         lib.gp_server_submit_registered_many.argtypes = [vp, u32, vp, vp, vp, vp, vp, ctypes.POINTER(u32)]
         lib.gp_server_drain.argtypes = [vp, u32, vp, vp, vp, vp, vp, ctypes.POINTER(u32)]
         lib.gp_server_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        lib.gp_server_set_tuning.argtypes = [vp, ctypes.POINTER(GpTuning)]
         for name in ("gp_server_create", "gp_server_open_patch", "gp_server_close_patch", "gp_server_submit",
                      "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release",
                      "gp_server_register_cycle", "gp_server_submit_registered",
-                     "gp_server_submit_registered_many", "gp_server_drain", "gp_server_last_timing"):
+                     "gp_server_submit_registered_many", "gp_server_drain", "gp_server_last_timing",
+                     "gp_server_set_tuning"):
             getattr(lib, name).restype = i32
         lib.gp_last_error.argtypes = []
         lib.gp_last_error.restype = ctypes.c_char_p

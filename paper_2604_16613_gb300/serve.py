@@ -171,6 +171,14 @@ class Server:
         native.check(self.lib.gp_server_step(self.handle, native.LEVELS[level], s, ctypes.byref(n)))
         return n.value
 
+    def set_tuning(self, stage1_threads=512, stage1_blocks_per_sm=0, stage2_threads=512, stage2_blocks_per_sm=8,
+                   obs_words=4, obs_segments=3):
+        """Launch and work-split parameters of the server's compiles (as
+        ``Driver.set_tuning``); results do not change."""
+        t = native.GpTuning(stage1_threads, stage1_blocks_per_sm, stage2_threads, stage2_blocks_per_sm, obs_words,
+                            obs_segments)
+        native.check(self.lib.gp_server_set_tuning(self.handle, ctypes.byref(t)))
+
     def last_timing(self) -> list[float]:
         """Microseconds of the last step: host build, compile, select,
         hand-out, then the compile's device stages (lowering, stage 1,

@@ -235,6 +235,25 @@ def test_zero_probability_locations_are_dropped():
     compare_edges(dem.edges(), oracle_edges(circ, noise).edges(), "p=0")
 
 
+def test_nop_rows_equal_zero_probability_locations():
+    """A NOP row is ignored: noise rows turned into NOP rows give the model of
+    the same circuit with those locations at p = 0 (which contribute no
+    mechanism, Sec. 2.1.4), against the oracle."""
+    import copy
+    circ = C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))
+    noise = C.log_uniform_noise(circ.n_locations, seed=8)
+    ops = np.array(circ.ops, dtype=np.uint32).reshape(-1, 4).copy()
+    rows = np.flatnonzero(ops[:, 0] >= 32)[1::3]
+    zero = noise.copy()
+    zero[ops[rows, 3]] = 0.0
+    ops[rows] = [7, 0, 0, 0]
+    nop = copy.copy(circ)
+    nop._ops, nop._frozen = [ops], None
+    assert np.array_equal(nop.recs, circ.recs)
+    _, dem = run(nop, noise)
+    compare_edges(dem.edges(), oracle_edges(circ, zero).edges(), "nop")
+
+
 def test_saturated_x_error():
     c = C.Circuit(1)
     c.gate1(C.R, [0]); c.tick()

@@ -90,6 +90,20 @@ def test_mix_equals_alone(wl):
         assert got == alone, n
 
 
+def test_tuning_does_not_change_stream(wl):
+    """The server's compile tuning (launch shapes, observable split) changes
+    no delivered hyperedge."""
+    names = ["surface5", "bb", "adaptive"]
+    circs = [wl[n][0] for n in names]
+    hs = [wl[n][1] for n in names]
+    base = Server.for_circuits(circs, max_cycles_per_step=2, max_horizon=max(hs)).stream(circs, hs)
+    srv = Server.for_circuits(circs, max_cycles_per_step=2, max_horizon=max(hs))
+    srv.set_tuning(1024, 0, 256, 4, 1, 1)
+    assert srv.stream(circs, hs) == base
+    with pytest.raises(native.GpError):
+        srv.set_tuning(obs_words=0)
+
+
 def test_record_horizon_refused_at_submit(wl):
     circ, _ = wl["adaptive"]          # outer detectors look two cycles back
     srv = Server.for_circuits([circ], max_horizon=2)
