@@ -178,7 +178,7 @@ __global__ void sel_prep_kernel(Buffers B, const SelParams *sp, SelScratch sc, u
 // per chunk: the delivered hyperedges and detector ids of every slot.
 // Then the horizon test: a mechanism of records-only cycle c flipping a
 // detector after cycle c + H means the window's horizon was too short.
-__global__ void __launch_bounds__(kSelThreads) sel_count_kernel(Buffers B, const SealDesc *seal, const uint32_t *cyc_tab,
+__global__ void __launch_bounds__(kSelThreads, 1) sel_count_kernel(Buffers B, const SealDesc *seal, const uint32_t *cyc_tab,
                                                                 uint32_t tab_stride, const uint2 *rec_tab,
                                                                 uint32_t max_h, const SelParams *sp, SelScratch sc,
                                                                 uint32_t *horizon) {
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kSelThreads) sel_starts_kernel(const SelParams
 // Every delivered hyperedge written straight into the pinned step buffer at
 // its place: the chunk's base in its request, plus those of the same slot
 // before it in the chunk (per warp, then across warps).
-__global__ void __launch_bounds__(kSelThreads) sel_write_kernel(Buffers B, const SealDesc *seal, const SelParams *sp,
+__global__ void __launch_bounds__(kSelThreads, 1) sel_write_kernel(Buffers B, const SealDesc *seal, const SelParams *sp,
                                                                 SelScratch sc) {
     extern __shared__ uint2 warp_cnt[];   // [warp][slot]
     const uint32_t n_win = sp->n_win, R = sp->n_slots, n_chunks = sc.chunk0[n_win];
@@ -362,10 +362,38 @@ __global__ void __launch_bounds__(kSelThreads) sel_write_kernel(Buffers B, const
             }
             const uint64_t at = pos + (uint64_t)r * n_win + w;
             if (at < edges_cap) out.doff[at] = (uint32_t)(dpos - sc.starts[r * (n_win + 1u) + w].y);
-            if (dpos + nd <= det_cap) {
-                const uint32_t o0 = B.det_off[e], db = seal[w].det_base;
-                for (uint32_t i = 0; i < nd; i++) out.det[dpos + i] = B.det_idx[o0 + i] + db;
+        }
+        // the detector ids of each slot's hyperedges in this warp form one
+        // contiguous range of the output: the warp writes it lane by lane
+        // (consecutive lanes, consecutive words), each lane finding the
+        // hyperedge of its word by a binary search over the running counts
+        const uint32_t o0 = key != 0u ? B.det_off[e] : 0u;
+        const uint32_t db = seal[w].det_base;
+        unsigned todo2 = __ballot_sync(0xFFFFFFFFu, key != 0u);
+        while (todo2) {
+            const uint32_t k = __shfl_sync(0xFFFFFFFFu, key, __ffs(todo2) - 1);
+            const bool mine = key == k;
+            uint32_t x = mine ? nd : 0u;
+            for (uint32_t o = 1; o < 32u; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= o) x += y;
             }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+            const uint32_t excl = x - (mine ? nd : 0u);
+            const uint2 base = sc.chunk_tot[(size_t)c * R + (k - 1u)], wb = warp_cnt[warp * R + (k - 1u)];
+            const uint64_t g0 = (uint64_t)base.y + wb.y;
+            for (uint32_t t0 = 0; t0 < total; t0 += 32u) {
+                const uint32_t t = t0 + lane;
+                uint32_t lo = 0;                       // first lane whose running count exceeds t
+                for (uint32_t h = 16; h; h >>= 1) {
+                    const uint32_t y = __shfl_sync(0xFFFFFFFFu, x, lo + h - 1u);
+                    if (y <= t) lo += h;
+                }
+                const uint32_t so0 = __shfl_sync(0xFFFFFFFFu, o0, lo);
+                const uint32_t sex = __shfl_sync(0xFFFFFFFFu, excl, lo);
+                if (t < total && g0 + t < det_cap) out.det[g0 + t] = B.det_idx[so0 + (t - sex)] + db;
+            }
+            todo2 &= ~__ballot_sync(0xFFFFFFFFu, mine);
         }
         __syncthreads();
     }

@@ -67,6 +67,29 @@ def test_stream_equals_full_compile(wl, name, K):
     compare_edges(got, orc.edges(), f"{name} K={K}")
 
 
+@pytest.mark.parametrize("name,K", [("surface5", 8), ("adaptive", 6)])
+def test_many_cycles_per_step(wl, name, K):
+    """Up to K cycles of a patch per step: a window's hyperedges go to up to K
+    request slots in one select pass."""
+    circ, H = wl[name]
+    got = Server.for_circuits([circ], max_cycles_per_step=K, max_horizon=H).stream([circ], [H])[0]
+    ref = gpu_full(circ)
+    assert got == ref
+
+
+def test_wide_windows_span_select_chunks():
+    """Windows of thousands of hyperedges (several select chunks of 1,024)
+    against the full compile and the oracle."""
+    circ = C.rotated_surface_code_memory(11, 6, C.NoiseModel.uniform(1e-3))
+    srv = Server.for_circuits([circ], max_cycles_per_step=2, max_horizon=1)
+    got = srv.stream([circ], [1])[0]
+    ref = gpu_full(circ)
+    assert got == ref
+    orc = oracle_edges(circ, f32(circ.default_noise))
+    assert len(got) == orc.n_classes
+    compare_edges(got, orc.edges(), "d=11 stream")
+
+
 def test_levels(wl):
     circ, H = wl["surface5"]
     srv = Server.for_circuits([circ], max_cycles_per_step=2, max_horizon=H)
