@@ -229,7 +229,11 @@ gp_status gp_result_to_host(gp_driver *drv, uint32_t *det_offsets, uint32_t *det
  *                 then carries one mask word per column it flips, so
  *                 bounds.max_mask_words counts these words.
  *   obs_segments  the most work items one observable column's walk is split
- *                 over in time (each fast-forwards to its own part). */
+ *                 over in time (each fast-forwards to its own part).
+ *   stage1_wide_emit  1: steps of many active qubits have their noise rows
+ *                 and Pauli components dealt out one per lane (faster wide
+ *                 detector columns, e.g. non-local codes; a slightly slower
+ *                 observable walk); 0: one active qubit per half-warp. */
 typedef struct {
     uint32_t stage1_threads;      /* 128, 256, 512 or 1024                    */
     uint32_t stage1_blocks_per_sm;/* resident blocks per SM for stage 1 (0 = max) */
@@ -237,6 +241,7 @@ typedef struct {
     uint32_t stage2_blocks_per_sm;/* grid = SMs x this for grid-stride kernels */
     uint32_t obs_words;           /* 1..8                                     */
     uint32_t obs_segments;        /* 1..3                                     */
+    uint32_t stage1_wide_emit;    /* 0 or 1                                   */
 } gp_tuning;
 gp_status gp_set_tuning(gp_driver *drv, const gp_tuning *t);
 gp_status gp_get_tuning(const gp_driver *drv, gp_tuning *t);

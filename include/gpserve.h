@@ -152,7 +152,9 @@ gp_status gp_server_step(gp_server *srv, gp_level level, void *stream, uint32_t 
 gp_status gp_server_last_timing(const gp_server *srv, float times_us[8]);
 
 /* Launch and work-split parameters of the server's compiles (gp_tuning,
- * gp_set_tuning's checks); none changes a result.  Not in the paper. */
+ * gp_set_tuning's checks); none changes a result.  A server starts with the
+ * driver's defaults and stage1_wide_emit = 1 (its windows are short, so
+ * detector columns set the walk's time).  Not in the paper. */
 gp_status gp_server_set_tuning(gp_server *srv, const gp_tuning *t);
 
 /* Ids of requests finished since the last call (at most cap; *n receives

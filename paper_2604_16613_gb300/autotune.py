@@ -1,13 +1,14 @@
 """Autotuner for the compile pipeline's launch shapes.
 
 The tunables are those of ``gp_tuning``: threads and resident blocks per SM
-for the stage-1 walk, threads and blocks per SM for the grid-stride stage-2
-kernels, and how the observable walk is split (observable word columns, and
-the most time segments of one observable walk).  The tuner times candidate
-shapes on the caller's own workload (device-resident inputs, CUDA events on
-the compile stream, median of a few compiles after a warm-up) by coordinate
-search: stage 1 first with the rest fixed, then stage 2, then the observable
-split, each with the choices made before it.  Results are cached per
+for the stage-1 walk and whether its emitters deal wide steps out lane by
+lane, threads and blocks per SM for the grid-stride stage-2 kernels, and how
+the observable walk is split (observable word columns, and the most time
+segments of one observable walk).  The tuner times candidate shapes on the
+caller's own workload (device-resident inputs, CUDA events on the compile
+stream, median of a few compiles after a warm-up) by coordinate search:
+stage 1 first with the rest fixed, then stage 2, then the observable split,
+each with the choices made before it.  Results are cached per
 workload signature.  Tuning changes only speed: the compile's outputs are
 identical under every shape (classes are numbered by their smallest member
 and class sums are exact integers).
@@ -27,7 +28,7 @@ STAGE2 = [(256, 8), (128, 16), (512, 4), (256, 4), (256, 16), (512, 8)]
 # (observable word columns, most time segments of one observable walk)
 OBS_SPLIT = [(4, 3), (1, 3), (2, 3), (8, 3), (4, 2), (4, 1)]
 FIELDS = ("stage1_threads", "stage1_blocks_per_sm", "stage2_threads", "stage2_blocks_per_sm", "obs_words",
-          "obs_segments")
+          "obs_segments", "stage1_wide_emit")
 
 _cache: dict = {}
 
@@ -87,6 +88,7 @@ def autotune(driver, circuits, noise, level="L2", repeats: int = 5, cache_file: 
 
     for s1t, s1b in STAGE1:
         trial(stage1_threads=s1t, stage1_blocks_per_sm=s1b)
+    trial(stage1_wide_emit=1 - best["stage1_wide_emit"])
     for s2t, s2b in STAGE2:
         trial(stage2_threads=s2t, stage2_blocks_per_sm=s2b)
     if n_obs:

@@ -191,10 +191,10 @@ struct gp_driver {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool exec_timing = false;
-    gp_tuning exec_tuning{0, 0, 0, 0, 0, 0};
+    gp_tuning exec_tuning{0, 0, 0, 0, 0, 0, 0};
     uint32_t graph_kernels = 0;
     // tuning / instrumentation / test knobs
-    gp_tuning tuning{512, 0, 512, 8, 4, kMaxSegments};
+    gp_tuning tuning{512, 0, 512, 8, 4, kMaxSegments, 0};
     gp_debug debug{0, 0, 0, 0};
     bool timing = false;
     cudaEvent_t ev[5] = {};
@@ -285,7 +285,8 @@ gp_status enqueue_pipeline(gp_driver *d, cudaStream_t s, uint32_t *kernels) {
     const Stage1Shape shape1 = stage1_shape(bd.max_qubits, want, d->smem_limit);
     if (shape1.smem > d->smem_limit) return fail(GP_ERR_CAPACITY, "stage 1 does not fit in shared memory with these bounds");
     int occ = 1;
-    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage1_kernel_ptr(d->tuning.stage1_threads, shape1.split),
+    const bool wide = shape1.split && d->tuning.stage1_wide_emit;
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage1_kernel_ptr(d->tuning.stage1_threads, wide ? 2u : shape1.split),
                                                           (int)d->tuning.stage1_threads, shape1.smem));
     if (occ < 1) return fail(GP_ERR_CAPACITY, "stage 1 does not fit on an SM with these bounds");
     const uint32_t bps = std::min<uint32_t>(want, (uint32_t)occ);
@@ -294,7 +295,7 @@ gp_status enqueue_pipeline(gp_driver *d, cudaStream_t s, uint32_t *kernels) {
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[0], s, cudaEventRecordExternal));
     launch_lowering(d->B, L.max_tiles, L.max_layer_slots, bd.max_qubits, (uint32_t)d->n_sms, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[1], s, cudaEventRecordExternal));
-    launch_stage1(d->B, grid1, d->tuning.stage1_threads, bd.max_qubits, shape1, s, kernels);
+    launch_stage1(d->B, grid1, d->tuning.stage1_threads, bd.max_qubits, shape1, wide, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[2], s, cudaEventRecordExternal));
     launch_group(d->B, grid2, d->tuning.stage2_threads, bd.max_mechanisms, s, kernels);
     if (d->timing) GP_CUDA(cudaEventRecordWithFlags(d->ev[3], s, cudaEventRecordExternal));
@@ -311,7 +312,8 @@ gp_status enqueue_pipeline(gp_driver *d, cudaStream_t s, uint32_t *kernels) {
 // host writes per compile)
 bool same_tuning(const gp_tuning &a, const gp_tuning &b) {
     return a.stage1_threads == b.stage1_threads && a.stage1_blocks_per_sm == b.stage1_blocks_per_sm &&
-           a.stage2_threads == b.stage2_threads && a.stage2_blocks_per_sm == b.stage2_blocks_per_sm;
+           a.stage2_threads == b.stage2_threads && a.stage2_blocks_per_sm == b.stage2_blocks_per_sm &&
+           a.stage1_wide_emit == b.stage1_wide_emit;
 }
 
 gp_status ensure_graph(gp_driver *d) {
@@ -418,7 +420,7 @@ gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace, uint64_t 
     // per-layer index kernel
     d->smem_limit = stage1_dynamic_smem_limit(d->device);
     if (d->smem_limit == 0) return cleanup(fail(GP_ERR_CUDA, "querying the shared-memory limit failed"));
-    for (uint32_t split : {0u, 1u})
+    for (uint32_t split : {0u, 1u, 2u})
         for (uint32_t t : {128u, 256u, 512u, 1024u}) {
             if (cudaFuncSetAttribute(stage1_kernel_ptr(t, split), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)d->smem_limit) != cudaSuccess)
@@ -453,9 +455,11 @@ gp_status gp_set_tuning(gp_driver *d, const gp_tuning *t) {
     if (!(ok_threads(t->stage1_threads) || t->stage1_threads == 1024) || !ok_threads(t->stage2_threads) ||
         t->stage2_blocks_per_sm == 0 ||
         t->stage2_blocks_per_sm > 64 || t->stage1_blocks_per_sm > 64 || t->obs_words == 0 ||
-        t->obs_words > kMaxObsWords || t->obs_segments == 0 || t->obs_segments > kMaxSegments)
+        t->obs_words > kMaxObsWords || t->obs_segments == 0 || t->obs_segments > kMaxSegments ||
+        t->stage1_wide_emit > 1)
         return fail(GP_ERR_INVALID, "tuning: stage-1 threads 128..1024, stage-2 threads 128..512 (powers of two); "
-                                    "blocks per SM 1..64; observable words 1..8; observable segments 1..3");
+                                    "blocks per SM 1..64; observable words 1..8; observable segments 1..3; "
+                                    "wide emission 0 or 1");
     d->tuning = *t;
     return GP_OK;
 }

@@ -463,8 +463,11 @@ struct Stage1Shape {
 // kernel's static shared memory)
 Stage1Shape stage1_shape(uint32_t max_qubits, uint32_t blocks_per_sm, size_t limit);
 size_t stage1_dynamic_smem_limit(int device);
+// wide: the role-split walk's emitters deal the rows of wide steps out
+// lane by lane (the kernel instance with that path)
 void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_qubits, const Stage1Shape &shape,
-                   cudaStream_t s, uint32_t *launches);
+                   bool wide, cudaStream_t s, uint32_t *launches);
+// split: 0 block-wide walk, 1 role-split walk, 2 role-split walk with wide emission
 const void *stage1_kernel_ptr(uint32_t threads, uint32_t split);
 void launch_group(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, cudaStream_t s, uint32_t *launches);
 void launch_compact(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t max_mech, uint32_t n_sms, cudaStream_t s,

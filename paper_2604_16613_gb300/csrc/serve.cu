@@ -710,6 +710,13 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
         const gp_status st = gp_driver_create(&b, nullptr, 0, &s->drv);
         if (st != GP_OK) return cleanup(st);
         gp_enable_timing(s->drv, 1);
+        // windows are a few cycles long, so their detector columns, not an
+        // observable's long walk, set stage 1: wide emission by default
+        gp_tuning t{};
+        gp_get_tuning(s->drv, &t);
+        t.stage1_wide_emit = 1;
+        const gp_status ts = gp_set_tuning(s->drv, &t);
+        if (ts != GP_OK) return cleanup(ts);
     }
     // pinned staging
     s->h_desc_bytes = nseg * sizeof(SegDesc) + Bt * sizeof(SealDesc) + Bt * s->extra_ops * sizeof(uint4) +

@@ -798,7 +798,7 @@ struct SplitShared {
     uint32_t wcnt[2];       // large step: {active, added}
 };
 
-template <int NT>
+template <int NT, bool WIDE>
 __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t maxq, uint32_t nbuf,
                                                              uint32_t list_cap, uint32_t wbytes, uint32_t wchunk) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1253,9 +1253,8 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
             }
             if (lane == 0u) *(volatile uint32_t *)&sh.walk_done = 1u;
         } else if (!producer) {
-            // ---- emitters: the noise rows of each published step; each
-            // half-warp takes one active qubit and evaluates its rows two at
-            // a time, one Pauli component per lane
+            // ---- emitters: the noise rows of each published step, one
+            // mask word per Pauli component (mechanism) of each row
             for (;;) {
                 const uint32_t b = st & 1u;
                 if (!wait_warp(&sh.tab_full[b], (tfull_par >> b) & 1u)) break;
@@ -1285,6 +1284,14 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     return t == stamp ? p : make_ulonglong2(0ull, 0ull);
                 };
                 warp_prefetch();
+                // A wide step's work is dealt out twice, so that every lane
+                // has work whatever the row kinds: each emitter warp takes a
+                // contiguous share of the active qubits, 32 at a time (one
+                // per lane); their (qubit, noise row) pairs go one per lane;
+                // then the Pauli components of those rows (one mechanism
+                // each), again one per lane.  A lane finds its pair or its
+                // component by a binary search over the lanes' running
+                // counts and fetches what it needs from the lane holding it.
                 auto row_word = [&](uint2 r, uint32_t q) -> unsigned long long {
                     const uint32_t kind = row_kind(r);
                     if (kind < K_XERR) return 0ull;
@@ -1301,33 +1308,121 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
                     return ((code & 1u) ? pa.x : 0ull) ^ ((code & 2u) ? pa.y : 0ull) ^
                            ((code & 4u) ? pb.x : 0ull) ^ ((code & 8u) ? pb.y : 0ull);
                 };
-                auto emit = [&](uint2 r, unsigned long long w) {
+                auto scan = [&](uint32_t x) -> uint32_t {     // inclusive, over the lanes
+#pragma unroll
+                    for (uint32_t o = 1; o < 32u; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    return x;
+                };
+                // the lane whose range of the running count holds j
+                auto lane_of = [&](uint32_t incl, uint32_t j) -> uint32_t {
+                    uint32_t lo = 0;
+#pragma unroll
+                    for (uint32_t h = 16; h; h >>= 1) {
+                        const uint32_t y = __shfl_sync(0xFFFFFFFFu, incl, lo + h - 1u);
+                        if (y <= j) lo += h;
+                    }
+                    return lo;
+                };
+                auto emit = [&](uint32_t mech, unsigned long long w) {
                     const unsigned m = __ballot_sync(0xFFFFFFFFu, w != 0ull);
                     if (m == 0u) return;
                     const uint32_t cnt = (uint32_t)__popc(m);
                     if (!warp_room(cnt)) return;
                     if (w != 0ull)
                         B.records[ck_pos + __popc(m & lt_mask)] =
-                            make_uint4(mech_base + r.y + l16, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
+                            make_uint4(mech_base + mech, col_tag, (uint32_t)w, (uint32_t)(w >> 32));
                     ck_pos += cnt;
                 };
-                for (uint32_t base = 2u * ew; base < n_act; base += 2u * NE) {
-                    const uint32_t c = base + half;
-                    const bool valid = c < n_act;
-                    const uint32_t q = valid ? ab[c] : 0u;
-                    uint32_t a0 = 0, a1 = 0;
-                    if (after) { a0 = v.aoff[q]; a1 = v.aoff[q + 1u]; }
-                    const uint32_t b0 = v.boff[q], b1 = v.boff[q + 1u];
-                    const uint32_t na = valid ? a1 - a0 : 0u;
-                    const uint32_t n = valid ? na + (b1 - b0) : 0u;
-                    const uint32_t nmax = max(n, __shfl_xor_sync(0xFFFFFFFFu, n, 16));
-                    for (uint32_t i = 0; i < nmax; i += 2u) {
-                        uint2 r0 = make_uint2(0u, 0u), r1 = make_uint2(0u, 0u);
-                        if (i < n) r0 = v.lists[i < na ? a0 + i : v.n_after + b0 + (i - na)];
-                        if (i + 1u < n) r1 = v.lists[i + 1u < na ? a0 + i + 1u : v.n_after + b0 + (i + 1u - na)];
-                        const unsigned long long w0 = row_word(r0, q), w1 = row_word(r1, q);
-                        emit(r0, w0);
-                        emit(r1, w1);
+                if (!WIDE || n_act <= 4u * NE) {
+                    // a narrow step (an observable's walk): each half-warp
+                    // takes one active qubit and evaluates its rows two at a
+                    // time, one Pauli component per lane -- the shortest
+                    // chain per step
+                    for (uint32_t base = 2u * ew; base < n_act; base += 2u * NE) {
+                        const uint32_t c = base + half;
+                        const bool valid = c < n_act;
+                        const uint32_t q = valid ? ab[c] : 0u;
+                        uint32_t a0 = 0, a1 = 0;
+                        if (after) { a0 = v.aoff[q]; a1 = v.aoff[q + 1u]; }
+                        const uint32_t b0 = v.boff[q], b1 = v.boff[q + 1u];
+                        const uint32_t na = valid ? a1 - a0 : 0u;
+                        const uint32_t n = valid ? na + (b1 - b0) : 0u;
+                        const uint32_t nmax = max(n, __shfl_xor_sync(0xFFFFFFFFu, n, 16));
+                        for (uint32_t i = 0; i < nmax; i += 2u) {
+                            uint2 r0 = make_uint2(0u, 0u), r1 = make_uint2(0u, 0u);
+                            if (i < n) r0 = v.lists[i < na ? a0 + i : v.n_after + b0 + (i - na)];
+                            if (i + 1u < n) r1 = v.lists[i + 1u < na ? a0 + i + 1u : v.n_after + b0 + (i + 1u - na)];
+                            const unsigned long long w0 = row_word(r0, q), w1 = row_word(r1, q);
+                            emit(r0.y + l16, w0);
+                            emit(r1.y + l16, w1);
+                        }
+                    }
+                } else {
+                    const uint32_t per = (n_act + NE - 1u) / NE;
+                    const uint32_t c_lo = min(ew * per, n_act), c_hi = min(c_lo + per, n_act);
+                    for (uint32_t c0 = c_lo; c0 < c_hi; c0 += 32u) {
+                        const uint32_t c = c0 + lane;
+                        const uint32_t q = c < c_hi ? ab[c] : 0u;
+                        uint32_t a0 = 0, na = 0, b0 = 0, nb = 0;
+                        if (c < c_hi) {
+                            if (after) {
+                                a0 = v.aoff[q];
+                                na = v.aoff[q + 1u] - a0;
+                            }
+                            b0 = v.boff[q];
+                            nb = v.boff[q + 1u] - b0;
+                        }
+                        const uint32_t rinc = scan(na + nb);
+                        const uint32_t n_rows = __shfl_sync(0xFFFFFFFFu, rinc, 31);
+                        for (uint32_t j0 = 0; j0 < n_rows; j0 += 32u) {
+                            // this lane's (qubit, row) pair
+                            const uint32_t j = j0 + lane;
+                            const uint32_t o = lane_of(rinc, j);
+                            const uint32_t oq = __shfl_sync(0xFFFFFFFFu, q, o);
+                            const uint32_t oa0 = __shfl_sync(0xFFFFFFFFu, a0, o);
+                            const uint32_t ona = __shfl_sync(0xFFFFFFFFu, na, o);
+                            const uint32_t ob0 = __shfl_sync(0xFFFFFFFFu, b0, o);
+                            const uint32_t k = j - __shfl_sync(0xFFFFFFFFu, rinc - na - nb, o);
+                            uint2 r = make_uint2(0u, 0u);
+                            if (j < n_rows) r = v.lists[k < ona ? oa0 + k : v.n_after + ob0 + (k - ona)];
+                            // the row's components (a two-qubit row listed
+                            // under both qubits is emitted from its first
+                            // qubit when that one is active)
+                            const uint32_t kind = row_kind(r);
+                            uint32_t nc = 0;
+                            if (j < n_rows && kind >= K_XERR) {
+                                const bool two = kind == K_DEP2;
+                                nc = two ? nc_dep2 : (kind == K_DEP1 ? nc_dep1 : 1u);
+                                if (two && oq == row_b(r) && tg[row_a(r)] == stamp) nc = 0u;
+                            }
+                            const uint32_t cinc = scan(nc);
+                            const uint32_t n_comp = __shfl_sync(0xFFFFFFFFu, cinc, 31);
+                            for (uint32_t i0 = 0; i0 < n_comp; i0 += 32u) {
+                                // this lane's component: its row from the lane
+                                // holding it, the planes from the snapshot
+                                const uint32_t i = i0 + lane;
+                                const uint32_t ro = lane_of(cinc, i);
+                                const uint32_t comp = i - __shfl_sync(0xFFFFFFFFu, cinc - nc, ro);
+                                const uint2 rr = make_uint2(__shfl_sync(0xFFFFFFFFu, r.x, ro), __shfl_sync(0xFFFFFFFFu, r.y, ro));
+                                const uint32_t rm = rr.y;
+                                unsigned long long w = 0ull;
+                                if (i < n_comp) {
+                                    const uint32_t rk = row_kind(rr);
+                                    const ulonglong2 pa = planes(row_a(rr));
+                                    const ulonglong2 pb = rk == K_DEP2 ? planes(row_b(rr)) : make_ulonglong2(0ull, 0ull);
+                                    const unsigned long long codes =
+                                        rk == K_DEP2 ? 0x0EBF7D639CA25184ull
+                                                     : (rk == K_DEP1 ? 0x321ull : (rk == K_XERR ? 1ull : 2ull));
+                                    const uint32_t code = (uint32_t)(codes >> (4u * comp)) & 0xFu;
+                                    w = ((code & 1u) ? pa.x : 0ull) ^ ((code & 2u) ? pa.y : 0ull) ^
+                                        ((code & 4u) ? pb.x : 0ull) ^ ((code & 8u) ? pb.y : 0ull);
+                                }
+                                emit(rm + comp, w);
+                            }
+                        }
                     }
                 }
                 __syncwarp();
@@ -1459,7 +1554,7 @@ size_t stage1_dynamic_smem_limit(int device) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
     cudaFuncAttributes fa{};
     size_t stat = 0;
-    for (uint32_t split : {0u, 1u})
+    for (uint32_t split : {0u, 1u, 2u})
         for (uint32_t t : {128u, 256u, 512u, 1024u}) {
             if (cudaFuncGetAttributes(&fa, stage1_kernel_ptr(t, split)) != cudaSuccess) return 0;
             stat = std::max(stat, fa.sharedSizeBytes);
@@ -1507,12 +1602,20 @@ Stage1Shape stage1_shape(uint32_t maxq, uint32_t blocks_per_sm, size_t limit) {
 }
 
 const void *stage1_kernel_ptr(uint32_t threads, uint32_t split) {
+    if (split == 2u) {
+        switch (threads) {
+        case 128: return (const void *)stage1_split_kernel<128, true>;
+        case 256: return (const void *)stage1_split_kernel<256, true>;
+        case 1024: return (const void *)stage1_split_kernel<1024, true>;
+        default: return (const void *)stage1_split_kernel<512, true>;
+        }
+    }
     if (split) {
         switch (threads) {
-        case 128: return (const void *)stage1_split_kernel<128>;
-        case 256: return (const void *)stage1_split_kernel<256>;
-        case 1024: return (const void *)stage1_split_kernel<1024>;
-        default: return (const void *)stage1_split_kernel<512>;
+        case 128: return (const void *)stage1_split_kernel<128, false>;
+        case 256: return (const void *)stage1_split_kernel<256, false>;
+        case 1024: return (const void *)stage1_split_kernel<1024, false>;
+        default: return (const void *)stage1_split_kernel<512, false>;
         }
     }
     switch (threads) {
@@ -1523,19 +1626,26 @@ const void *stage1_kernel_ptr(uint32_t threads, uint32_t split) {
     }
 }
 
-void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t maxq, const Stage1Shape &sh,
+void launch_stage1(const Buffers &b, uint32_t grid, uint32_t threads, uint32_t maxq, const Stage1Shape &sh, bool wide,
                    cudaStream_t s, uint32_t *launches) {
     // records per warp chunk: the chunk tails the warps may leave unused fit
     // the pool's slack (kPoolSlack records)
     const uint64_t warps = (uint64_t)grid * (threads / 32u - 1u);
     uint32_t wchunk = (uint32_t)std::min<uint64_t>(256, kPoolSlack / std::max<uint64_t>(warps, 1)) & ~31u;
     if (wchunk < 32u) wchunk = 32u;
-    if (sh.split) {
+    if (sh.split && wide) {
         switch (threads) {
-        case 128: stage1_split_kernel<128><<<grid, 128, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
-        case 256: stage1_split_kernel<256><<<grid, 256, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
-        case 1024: stage1_split_kernel<1024><<<grid, 1024, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
-        default: stage1_split_kernel<512><<<grid, 512, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 128: stage1_split_kernel<128, true><<<grid, 128, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 256: stage1_split_kernel<256, true><<<grid, 256, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 1024: stage1_split_kernel<1024, true><<<grid, 1024, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        default: stage1_split_kernel<512, true><<<grid, 512, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        }
+    } else if (sh.split) {
+        switch (threads) {
+        case 128: stage1_split_kernel<128, false><<<grid, 128, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 256: stage1_split_kernel<256, false><<<grid, 256, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        case 1024: stage1_split_kernel<1024, false><<<grid, 1024, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
+        default: stage1_split_kernel<512, false><<<grid, 512, sh.smem, s>>>(b, maxq, sh.nbuf, sh.list_cap, sh.wbytes, wchunk); break;
         }
     } else {
         switch (threads) {

@@ -290,9 +290,9 @@ class Driver:
 
     # -- knobs -------------------------------------------------------------------
     def set_tuning(self, stage1_threads=512, stage1_blocks_per_sm=0, stage2_threads=512, stage2_blocks_per_sm=8,
-                   obs_words=4, obs_segments=3):
+                   obs_words=4, obs_segments=3, stage1_wide_emit=0):
         t = native.GpTuning(stage1_threads, stage1_blocks_per_sm, stage2_threads, stage2_blocks_per_sm, obs_words,
-                            obs_segments)
+                            obs_segments, stage1_wide_emit)
         native.check(self.lib.gp_set_tuning(self.handle, ctypes.byref(t)))
 
     def get_tuning(self) -> dict:

@@ -59,7 +59,8 @@ class GpDemView(ctypes.Structure):
 class GpTuning(ctypes.Structure):
     _fields_ = [("stage1_threads", ctypes.c_uint32), ("stage1_blocks_per_sm", ctypes.c_uint32),
                 ("stage2_threads", ctypes.c_uint32), ("stage2_blocks_per_sm", ctypes.c_uint32),
-                ("obs_words", ctypes.c_uint32), ("obs_segments", ctypes.c_uint32)]
+                ("obs_words", ctypes.c_uint32), ("obs_segments", ctypes.c_uint32),
+                ("stage1_wide_emit", ctypes.c_uint32)]
 
 
 class GpDebug(ctypes.Structure):

@@ -172,11 +172,11 @@ class Server:
         return n.value
 
     def set_tuning(self, stage1_threads=512, stage1_blocks_per_sm=0, stage2_threads=512, stage2_blocks_per_sm=8,
-                   obs_words=4, obs_segments=3):
+                   obs_words=4, obs_segments=3, stage1_wide_emit=1):
         """Launch and work-split parameters of the server's compiles (as
         ``Driver.set_tuning``); results do not change."""
         t = native.GpTuning(stage1_threads, stage1_blocks_per_sm, stage2_threads, stage2_blocks_per_sm, obs_words,
-                            obs_segments)
+                            obs_segments, stage1_wide_emit)
         native.check(self.lib.gp_server_set_tuning(self.handle, ctypes.byref(t)))
 
     def last_timing(self) -> list[float]:

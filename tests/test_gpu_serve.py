@@ -121,7 +121,7 @@ def test_tuning_does_not_change_stream(wl):
     hs = [wl[n][1] for n in names]
     base = Server.for_circuits(circs, max_cycles_per_step=2, max_horizon=max(hs)).stream(circs, hs)
     srv = Server.for_circuits(circs, max_cycles_per_step=2, max_horizon=max(hs))
-    srv.set_tuning(1024, 0, 256, 4, 1, 1)
+    srv.set_tuning(1024, 0, 256, 4, 1, 1, 1)
     assert srv.stream(circs, hs) == base
     with pytest.raises(native.GpError):
         srv.set_tuning(obs_words=0)

@@ -153,8 +153,8 @@ def test_autotune_does_not_change_results():
 
 def test_observable_split_does_not_change_results():
     """The observables of a circuit may be walked as 1 to 8 word columns,
-    each in 1 to 3 time segments: the compile is the same bit for bit, and
-    equal to the oracle.  The [[144,12,12]] code has 12 logicals (uneven
+    each in 1 to 3 time segments, and stage 1 may deal wide steps out lane by
+    lane: the compile is the same bit for bit, and equal to the oracle.  The [[144,12,12]] code has 12 logicals (uneven
     splits at 5 and 8 columns); the random circuits have one or two."""
     circs = [C.bb_memory(3, C.NoiseModel.uniform(1e-3), seed=3),
              C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3))]
@@ -166,12 +166,13 @@ def test_observable_split_does_not_change_results():
     base = drv.compile(dcs, noise).to_host()
     for i, (c, nz) in enumerate(zip(circs, noises)):
         compare_arrays(base, i, oracle_arrays((c.ops, c.recs, c.n_qubits, nz.astype(np.float64), "L2")), f"circuit {i}")
-    for ow, osg in [(1, 3), (2, 1), (5, 2), (8, 3), (3, 1)]:
-        drv.set_tuning(obs_words=ow, obs_segments=osg)
+    for ow, osg, wide in [(1, 3, 0), (2, 1, 1), (5, 2, 0), (8, 3, 1), (3, 1, 0), (4, 3, 1)]:
+        drv.set_tuning(obs_words=ow, obs_segments=osg, stage1_wide_emit=wide)
         got = drv.compile(dcs, noise).to_host()
         for k in base:
-            assert np.array_equal(base[k], got[k]), (ow, osg, k)
-    for bad in [dict(obs_words=0), dict(obs_words=9), dict(obs_segments=0), dict(obs_segments=4)]:
+            assert np.array_equal(base[k], got[k]), (ow, osg, wide, k)
+    for bad in [dict(obs_words=0), dict(obs_words=9), dict(obs_segments=0), dict(obs_segments=4),
+                dict(stage1_wide_emit=2)]:
         with pytest.raises(GpError):
             drv.set_tuning(**bad)
 
@@ -190,7 +191,7 @@ def test_block_wide_walk_equals_role_split_walk():
     bd = Bounds.for_circuits(circs)
     bd.max_qubits = 4096
     wide = Driver(bd)
-    for shape in [(512, 1, 256, 16), (256, 2, 256, 16, 1, 3), (128, 1, 256, 16, 8, 2)]:
+    for shape in [(512, 1, 256, 16), (256, 2, 256, 16, 1, 3, 1), (128, 1, 256, 16, 8, 2)]:
         wide.set_tuning(*shape)
         got = wide.compile(dcs, noise).to_host()
         for k in split:
