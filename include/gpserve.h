@@ -18,7 +18,9 @@
  *     and one observable per logical, so observable bits are those of the
  *     logical frame at the cycle boundary; the noise of its last H cycles
  *     is then left out (their mechanisms only flip detectors after every
- *     cycle the window seals, so no delivered hyperedge holds one);
+ *     cycle the window seals, so no delivered hyperedge holds one), and so
+ *     is the noise of its records-only cycles once a window of the same
+ *     registered cycles has passed the horizon test below;
  *   - all windows of a step are compiled in one batched launch
  *     (gp_compile_batch), and a hyperedge is delivered with request t when
  *     its smallest detector lies in cycle t - H (the final request of a

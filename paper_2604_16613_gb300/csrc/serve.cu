@@ -6,11 +6,13 @@
 //   - the new cycles are copied into their patches' resident rings;
 //   - assemble: one launch copies every window's cycles from the rings into
 //     the batch arena, shifting record and location indices to the window,
-//     emptying the detectors of records-only cycles (and zeroing their noise
-//     in a final window) and appending the rows that close a window with the
-//     declared logicals; the noise rows of a window's last H cycles are
-//     left out unless the window ends its patch (no hyperedge it delivers
-//     can hold one of their mechanisms);
+//     emptying the detectors of records-only cycles and appending the rows
+//     that close a window with the declared logicals; noise rows are left
+//     out (made NOP rows) where no delivered hyperedge can hold their
+//     mechanisms: in a window's last H cycles unless the window ends its
+//     patch, and in its records-only cycles when only the horizon test
+//     would read them and that test is moot (a final window, or a window of
+//     registered cycles whose pattern passed it before);
 //   - the windows are compiled as one batch (gp_compile_batch);
 //   - seal (one captured graph of four kernels): a horizon test per window
 //     (no mechanism of a records-only cycle c flips a detector after cycle
@@ -27,6 +29,7 @@
 #include <cstring>
 #include <deque>
 #include <new>
+#include <set>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -68,11 +71,12 @@ struct SegDesc {
     uint32_t n_ops, n_recs, n_loc;
     uint32_t dst_ops, dst_recs, dst_loc;
     uint32_t rec_shift, loc_shift;
-    uint32_t flags;             // kSegRecordsOnly | kSegZeroNoise | kSegNoNoise
+    uint32_t flags;             // kSegRecordsOnly | kSegNoNoise
     uint32_t pad;
 };
 // kSegNoNoise: the cycle's noise rows become NOP rows (no mechanisms)
-constexpr uint32_t kSegRecordsOnly = 1u, kSegZeroNoise = 2u, kSegNoNoise = 4u;
+constexpr uint32_t kSegRecordsOnly = 1u, kSegNoNoise = 4u;
+constexpr size_t kMaxVerified = 1024;   // tested window patterns kept per patch
 
 // what a window seals
 struct SealDesc {
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const SegDesc *seg, uint3
     }
     for (uint32_t i = t0; i < d.n_recs; i += stride) recs[d.dst_recs + i] = d.recs[i];
     for (uint32_t i = t0; i < d.n_loc; i += stride)
-        noise[d.dst_loc + i] = (d.flags & kSegZeroNoise) ? 0.0f : d.noise[i];
+        noise[d.dst_loc + i] = d.noise[i];
 }
 
 // What the select phase of a step needs beyond the compile: the windows,
@@ -417,6 +421,7 @@ struct CycleInfo {
     const uint4 *src_ops;
     const uint32_t *src_recs;
     const float *src_noise;
+    int32_t reg = -1;           // the registered cycle it repeats, or -1
 };
 
 // what a cycle's rows fix, whatever the patch saw before it: its counts and
@@ -478,6 +483,10 @@ struct Patch {
     std::vector<Registered> registered;
     uint32_t next_step = 0;              // first cycle not yet stepped
     bool final_submitted = false;
+    // windows of registered cycles whose horizon test passed, by their
+    // cycles' registered ids: the same rows give the same test, so such a
+    // window leaves its records-only cycles' noise out and is not tested
+    std::set<std::vector<int32_t>> verified;
     std::deque<uint64_t> pending;        // submitted, not yet stepped (cycle order)
 };
 
@@ -1039,6 +1048,8 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         bool final;
         std::vector<uint64_t> reqs;
         std::vector<uint64_t> det_off;   // window-local detector offset per cycle c0..t_b+1
+        std::vector<int32_t> key;        // registered ids of cycles c0..t_b
+        bool keyed = false, known = false;
     };
     std::vector<Win> wins;
     SegDesc *hseg = reinterpret_cast<SegDesc *>(s->h_desc);
@@ -1072,6 +1083,7 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         for (uint64_t id : w.reqs) {
             const Request &r = s->requests.at(id);
             CycleInfo &ci = P.cycles[r.cycle];
+            ci.reg = r.reg;
             if (r.reg >= 0) {
                 // a registered cycle is read from its device copy
                 const Registered &g = P.registered[r.reg];
@@ -1095,6 +1107,14 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
                                         s->h_stage_noise + (uint64_t)r.stage * c.max_cycle_locations, ci.n_loc * sizeof(float),
                                         cudaMemcpyHostToDevice, st));
         }
+        // a window of registered cycles that passed the horizon test before
+        // passes it again: its records-only cycles' noise is left out
+        w.keyed = !w.final && w.n_rec > 0;
+        for (uint32_t k = w.c0; k <= w.t_b; k++) {
+            w.key.push_back(P.cycles[k].reg);
+            if (P.cycles[k].reg < 0) w.keyed = false;
+        }
+        w.known = w.keyed && P.verified.count(w.key) != 0;
         // segments of the window
         gp_circuit g{};
         const uint64_t ops0 = a_ops, recs0 = a_recs, loc0 = a_loc;
@@ -1120,10 +1140,13 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
             // every cycle the window seals: its hyperedge is not delivered,
             // and no delivered hyperedge has its mask, so it is left out
             const bool unsealed = !w.final && k + P.H > w.t_b;
-            d.flags = (rec_only ? kSegRecordsOnly : 0u) | (rec_only && w.final ? kSegZeroNoise : 0u) |
-                      (unsealed ? kSegNoNoise : 0u);
+            // a records-only cycle's mechanisms only serve the horizon test
+            // (none is in a delivered hyperedge when H holds): a final window
+            // and a known window leave them out
+            const bool untested = rec_only && (w.final || w.known);
+            d.flags = (rec_only ? kSegRecordsOnly : 0u) | (unsealed || untested ? kSegNoNoise : 0u);
             d.pad = 0;
-            if (rec_only) mech_rec += ci.mech[(int)level];
+            if (rec_only && !untested) mech_rec += ci.mech[(int)level];
             a_ops += ci.n_ops;
             a_recs += ci.n_recs;
             a_loc += ci.n_loc;
@@ -1178,8 +1201,8 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         }
         sd.take_no_det = w.final ? 1u : 0u;
         sd.det_base = (uint32_t)P.cycles[w.c0].det_base;
-        // the final window's records-only noise is zero: nothing to check
-        sd.n_mech_rec = w.final ? 0u : mech_rec;
+        // a final or known window has no records-only mechanisms to test
+        sd.n_mech_rec = mech_rec;
         sd.n_rec = w.n_rec;
         sd.n_cyc = w.t_b - w.c0 + 1u;
         sd.r_off = (int32_t)(w.c0 + P.H) - (int32_t)w.t_a;
@@ -1236,8 +1259,13 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
             const uint2 tot = s->h_starts[(size_t)(n_pass - 1u) * rs + n_win];
             if (tot.x + (uint64_t)n_pass * n_win > ob->edges_cap || tot.y > ob->det_cap)
                 cst = sfail(GP_ERR_CAPACITY, "sealed output larger than the step's whole output");
-            for (uint32_t w = 0; w < n_win; w++)
+            for (uint32_t w = 0; w < n_win; w++) {
                 if (s->h_horizon[w]) win_status[w] = GP_ERR_HORIZON;
+                // a tested window's pattern passes from now on
+                Patch &P = s->patches[wins[w].patch];
+                if (wins[w].keyed && !wins[w].known && win_status[w] == GP_OK && P.verified.size() < kMaxVerified)
+                    P.verified.insert(wins[w].key);
+            }
         }
     }
     const uint64_t t_selected = now_ns();

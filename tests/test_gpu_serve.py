@@ -90,6 +90,54 @@ def test_wide_windows_span_select_chunks():
     compare_edges(got, orc.edges(), "d=11 stream")
 
 
+def stream_registered(srv, circ, H, mid_repeats_registered=True):
+    """Stream a memory experiment whose first and repeated middle cycles are
+    registered once and submitted by id (the final cycle as rows); returns
+    the union of the delivered hyperedges."""
+    blocks = circ.cycle_blocks()
+    pid = srv.open_circuit_patch(circ, H)
+    first = srv.register_cycle(pid, blocks[0])
+    mid = srv.register_cycle(pid, blocks[1])
+    rids = [srv.submit_registered(pid, first)]
+    rids += [srv.submit_registered(pid, mid) for _ in blocks[1:-1]]
+    rids.append(srv.submit(pid, blocks[-1]))
+    out, done = {}, 0
+    for _ in range(4 * len(rids)):          # a server that stops making progress fails, never hangs
+        if done == len(rids):
+            break
+        srv.step()
+        for r in srv.completed():
+            Server._merge(out, Server.edges(srv.result(r)), 0)
+            srv.release(r)
+            done += 1
+    assert done == len(rids)
+    srv.close_patch(pid)
+    return out
+
+
+@pytest.mark.parametrize("name,rounds,K", [("surface", 9, 1), ("surface", 9, 2), ("bb", 7, 1)])
+def test_registered_cycles_equal_full_compile(name, rounds, K):
+    """Registered cycles repeated by id: the first window of each pattern
+    runs the horizon test, later windows of the same registered cycles leave
+    the records-only noise out.  The stream equals the full compile bit for
+    bit and the oracle within tolerance, on a server reused for a second
+    stream."""
+    circ = (C.rotated_surface_code_memory(5, rounds, C.NoiseModel.uniform(1e-3)) if name == "surface"
+            else C.bb_memory(rounds, C.NoiseModel.uniform(1e-3), seed=3))
+    blocks = circ.cycle_blocks()
+    for b in blocks[2:-1]:
+        for k in ("ops", "recs", "noise"):
+            assert np.array_equal(np.asarray(blocks[1][k]), np.asarray(b[k]))
+    srv = Server.for_circuits([circ], max_cycles_per_step=K, max_horizon=1, max_pending=4 * rounds)
+    ref = gpu_full(circ)
+    for _ in range(2):
+        got = stream_registered(srv, circ, 1)
+        assert got == ref
+    orc = oracle_edges(circ, f32(circ.default_noise))
+    assert len(ref) == orc.n_classes
+    compare_edges(got, orc.edges(), f"{name} registered K={K}")
+
+
 def test_levels(wl):
     circ, H = wl["surface5"]
     srv = Server.for_circuits([circ], max_cycles_per_step=2, max_horizon=H)
