@@ -503,11 +503,13 @@ struct gp_server {
     uint4 *arena_ops = nullptr;
     uint32_t *arena_recs = nullptr;
     float *arena_noise = nullptr;
-    SegDesc *d_seg = nullptr;
+    // the seal block: per window its SealDesc, record table and cycle table,
+    // laid out alike in device memory and at the start of h_desc, so that
+    // one copy brings it over (the segment descriptors and closing rows are
+    // read by the assembly straight from pinned host memory)
+    uint64_t sealblk_bytes = 0;
     SealDesc *d_seal = nullptr;
     uint2 *d_rec_tab = nullptr;
-    uint4 *d_extra_ops = nullptr;
-    uint32_t *d_extra_recs = nullptr;
     uint32_t *d_cyc_tab = nullptr;       // per window: detector offset of each cycle
     SelScratch sel{};                    // select-phase scratch
     SelParams *d_sel = nullptr;          // the select phase's per-step parameters
@@ -518,7 +520,7 @@ struct gp_server {
                                                  // then the compile's device stages (us)
     uint64_t out_edges_cap = 0, out_det_cap = 0;
     // pinned host memory
-    unsigned char *h_desc = nullptr;     // segs | seals | extra ops | extra recs
+    unsigned char *h_desc = nullptr;     // seal block | segs | extra ops | extra recs
     size_t h_desc_bytes = 0;
     uint4 *h_stage_ops = nullptr;
     uint32_t *h_stage_recs = nullptr;
@@ -673,6 +675,7 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
     s->out_edges_cap = b.max_mechanisms;
     s->out_det_cap = std::min<uint64_t>(max_det_entries, 0xFFFFFFFFull);
     const uint64_t nseg = Bt * (W + 1);
+    s->sealblk_bytes = Bt * sizeof(SealDesc) + Bt * c.max_horizon * sizeof(uint2) + Bt * (W + 1) * sizeof(uint32_t);
     auto layout = [&](unsigned char *base) {
         uint64_t off = 0;
         for (uint32_t p = 0; p < c.max_patches; p++) {
@@ -688,12 +691,12 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
         s->arena_ops = carve_dev<uint4>(base, off, ops);
         s->arena_recs = carve_dev<uint32_t>(base, off, std::max<uint64_t>(recs, 1));
         s->arena_noise = carve_dev<float>(base, off, std::max<uint64_t>(locs, 1));
-        s->d_seg = carve_dev<SegDesc>(base, off, nseg);
-        s->d_seal = carve_dev<SealDesc>(base, off, Bt);
-        s->d_rec_tab = carve_dev<uint2>(base, off, Bt * c.max_horizon);
-        s->d_extra_ops = carve_dev<uint4>(base, off, Bt * s->extra_ops);
-        s->d_extra_recs = carve_dev<uint32_t>(base, off, std::max<uint64_t>(Bt * s->extra_recs, 1));
-        s->d_cyc_tab = carve_dev<uint32_t>(base, off, Bt * (W + 1));
+        unsigned char *blk = carve_dev<unsigned char>(base, off, s->sealblk_bytes);
+        if (base) {
+            s->d_seal = reinterpret_cast<SealDesc *>(blk);
+            s->d_rec_tab = reinterpret_cast<uint2 *>(blk + Bt * sizeof(SealDesc));
+            s->d_cyc_tab = reinterpret_cast<uint32_t *>(blk + Bt * sizeof(SealDesc) + Bt * c.max_horizon * sizeof(uint2));
+        }
         const uint64_t K = c.max_cycles_per_step, max_chunks = s->out_edges_cap / kSelChunk + Bt + 1;
         SelScratch sc{};
         sc.win_e0 = carve_dev<uint32_t>(base, off, Bt + 1);
@@ -728,9 +731,8 @@ gp_status gp_server_create(const gp_server_config *config, gp_server **out) {
         if (ts != GP_OK) return cleanup(ts);
     }
     // pinned staging
-    s->h_desc_bytes = nseg * sizeof(SegDesc) + Bt * sizeof(SealDesc) + Bt * s->extra_ops * sizeof(uint4) +
-                      Bt * s->extra_recs * sizeof(uint32_t) + Bt * c.max_horizon * sizeof(uint2) +
-                      Bt * (W + 1) * sizeof(uint32_t);
+    s->h_desc_bytes = ((s->sealblk_bytes + 15u) & ~(uint64_t)15u) + nseg * sizeof(SegDesc) + Bt * s->extra_ops * sizeof(uint4) +
+                      Bt * s->extra_recs * sizeof(uint32_t);
     if (cudaMallocHost(&s->h_desc, s->h_desc_bytes) != cudaSuccess ||
         cudaMallocHost(&s->h_stage_ops, sizeof(uint4) * (uint64_t)c.max_pending * c.max_cycle_ops) != cudaSuccess ||
         cudaMallocHost(&s->h_stage_recs, sizeof(uint32_t) * std::max<uint64_t>((uint64_t)c.max_pending * c.max_cycle_recs, 1)) != cudaSuccess ||
@@ -1052,13 +1054,15 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         bool keyed = false, known = false;
     };
     std::vector<Win> wins;
-    SegDesc *hseg = reinterpret_cast<SegDesc *>(s->h_desc);
-    const uint64_t nseg_cap = (uint64_t)c.max_batch * (s->W + 1);
-    SealDesc *hseal = reinterpret_cast<SealDesc *>(hseg + nseg_cap);
-    uint4 *hxops = reinterpret_cast<uint4 *>(hseal + c.max_batch);
-    uint32_t *hxrecs = reinterpret_cast<uint32_t *>(hxops + (uint64_t)c.max_batch * s->extra_ops);
-    uint2 *hrtab = reinterpret_cast<uint2 *>(hxrecs + (uint64_t)c.max_batch * s->extra_recs);
+    // h_desc: the seal block (as in device memory), then the segment
+    // descriptors and closing rows that the assembly reads from here
+    SealDesc *hseal = reinterpret_cast<SealDesc *>(s->h_desc);
+    uint2 *hrtab = reinterpret_cast<uint2 *>(hseal + c.max_batch);
     uint32_t *hctab = reinterpret_cast<uint32_t *>(hrtab + (uint64_t)c.max_batch * c.max_horizon);
+    SegDesc *hseg = reinterpret_cast<SegDesc *>(s->h_desc + ((s->sealblk_bytes + 15u) & ~(uint64_t)15u));
+    const uint64_t nseg_cap = (uint64_t)c.max_batch * (s->W + 1);
+    uint4 *hxops = reinterpret_cast<uint4 *>(hseg + nseg_cap);
+    uint32_t *hxrecs = reinterpret_cast<uint32_t *>(hxops + (uint64_t)c.max_batch * s->extra_ops);
     std::vector<gp_circuit> circ;
     uint32_t nseg = 0;
     uint64_t a_ops = 0, a_recs = 0, a_loc = 0, x_ops = 0, x_recs = 0;
@@ -1164,8 +1168,8 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
                 hxops[x_ops++] = make_uint4(K_OBS, rbase + P.virt_off[k], P.virt_off[k + 1] - P.virt_off[k], k);
             for (uint32_t v : P.virt_recs) hxrecs[x_recs++] = v;
             SegDesc &d = hseg[nseg++];
-            d.ops = s->d_extra_ops + xo0;
-            d.recs = s->d_extra_recs + xr0;
+            d.ops = hxops + xo0;
+            d.recs = hxrecs + xr0;
             d.noise = nullptr;
             d.n_ops = (uint32_t)(x_ops - xo0);
             d.n_recs = (uint32_t)(x_recs - xr0);
@@ -1220,13 +1224,10 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     }
     const uint32_t n_win = (uint32_t)wins.size();
     // descriptors and closing rows: one copy each
-    SV_CUDA(cudaMemcpyAsync(s->d_seg, hseg, nseg * sizeof(SegDesc), cudaMemcpyHostToDevice, st));
-    SV_CUDA(cudaMemcpyAsync(s->d_seal, hseal, n_win * sizeof(SealDesc), cudaMemcpyHostToDevice, st));
-    SV_CUDA(cudaMemcpyAsync(s->d_rec_tab, hrtab, (size_t)n_win * c.max_horizon * sizeof(uint2), cudaMemcpyHostToDevice, st));
-    SV_CUDA(cudaMemcpyAsync(s->d_cyc_tab, hctab, (size_t)n_win * (s->W + 1u) * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    if (x_ops) SV_CUDA(cudaMemcpyAsync(s->d_extra_ops, hxops, x_ops * sizeof(uint4), cudaMemcpyHostToDevice, st));
-    if (x_recs) SV_CUDA(cudaMemcpyAsync(s->d_extra_recs, hxrecs, x_recs * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    assemble_kernel<<<dim3(nseg, kSegBlocksY), 256, 0, st>>>(s->d_seg, nseg, s->arena_ops, s->arena_recs, s->arena_noise);
+    // descriptors: one copy of the seal block; the assembly reads the
+    // segment descriptors and closing rows from pinned host memory
+    SV_CUDA(cudaMemcpyAsync(s->d_seal, s->h_desc, s->sealblk_bytes, cudaMemcpyHostToDevice, st));
+    assemble_kernel<<<dim3(nseg, kSegBlocksY), 256, 0, st>>>(hseg, nseg, s->arena_ops, s->arena_recs, s->arena_noise);
     SV_CUDA(cudaGetLastError());
     const uint64_t t_built = now_ns();
     gp_dem_view view{};
