@@ -504,7 +504,8 @@ def calibration_section(args) -> dict:
 
 def serve_section(args) -> dict:
     """Continuous serving: ``--serve-patches`` patches, each issuing one
-    per-cycle request as a Poisson process, for ``--serve-seconds`` at each
+    per-cycle request as a Poisson process, for ``--serve-seconds`` (after
+    ``--serve-warmup-seconds`` untimed at the same load) at each
     per-patch rate of ``--serve-rates``; patch mix rotated surface code d in
     {5, 7, ..., 25} (uniform) and [[144,12,12]] bivariate bicycle memory at
     3:1, p = 1e-3, level L2.  Every patch registers its first and its
@@ -546,7 +547,7 @@ def serve_section(args) -> dict:
         pass
     srv.drain()
 
-    def run(rate: float, seed: int) -> dict:
+    def run(rate: float, seed: int, T: float = T) -> dict:
         rng = np.random.default_rng(seed)
         ev_t, ev_p = [], []
         for i in range(P):
@@ -612,13 +613,20 @@ def serve_section(args) -> dict:
     gc.collect()
     gc.disable()
     try:
-        loads = [run(r, 5 + n) for n, r in enumerate(rates)]
+        loads = []
+        for n, r in enumerate(rates):
+            # an untimed stretch at the same load first: the server pins larger
+            # step buffers once, when a load first needs them
+            if args.serve_warmup_seconds > 0:
+                run(r, 1005 + n, args.serve_warmup_seconds)
+            loads.append(run(r, 5 + n))
     finally:
         gc.enable()
     srv.close()
     return {
         "workload": f"{P} patches (surface d=5..25 odd : BB [[144,12,12]] = 3:1), Poisson per-cycle requests, "
-                    f"{T:g} s per load, p=1e-3, L2, H=1, up to {K} cycles per patch per step",
+                    f"{T:g} s per load (after {args.serve_warmup_seconds:g} s untimed at the load), p=1e-3, L2, H=1, "
+                    f"up to {K} cycles per patch per step",
         "loads": loads,
     }
 
@@ -840,6 +848,8 @@ def main():
     ap.add_argument("--serve-rates", default="50,100,250,500,750,1000",
                     help="per-patch request rates (Hz) of the serving loads, comma-separated")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-warmup-seconds", type=float, default=0.3,
+                    help="untimed seconds at each load before its timed run")
     ap.add_argument("--serve-k", type=int, default=4, help="cycles of one patch merged into a step")
     args = ap.parse_args()
     if args.impl == "reference":
