@@ -221,6 +221,29 @@ gp_status gp_result_view(const gp_driver *drv, gp_dem_view *out);
 gp_status gp_result_to_host(gp_driver *drv, uint32_t *det_offsets, uint32_t *det_idx,
                             uint64_t *obs_mask, float *prob, float *logodds, void *stream);
 
+/* Host output (not in the paper): caller-owned arrays in host memory that
+ * every later compile on the driver also fills, from its compaction kernel,
+ * with the hyperedges of gp_result_to_host -- so no separate copy follows
+ * the compile.  det_offsets holds edges_cap + 1 entries, obs_mask, prob and
+ * logodds edges_cap, det_idx det_cap.  The memory must be addressable by the
+ * device: page-locked (cudaHostAlloc / cudaHostRegister), or any host memory
+ * on a device that reads pageable memory coherently.  The arrays are 4-byte
+ * aligned (obs_mask 8), owned by the caller and must outlive their use; they
+ * are complete when the compile returns.  A compile whose hyperedges exceed
+ * a capacity fails with GP_ERR_CAPACITY (the arrays then hold what fitted). */
+typedef struct {
+    uint32_t *det_offsets;
+    uint32_t *det_idx;
+    uint64_t *obs_mask;
+    float *prob;
+    float *logodds;
+    uint64_t edges_cap;
+    uint64_t det_cap;
+} gp_host_output;
+/* out == NULL turns the host output off.  Errors: GP_ERR_INVALID (a NULL
+ * array, misaligned or non-addressable memory, zero edges_cap). */
+gp_status gp_set_host_output(gp_driver *drv, const gp_host_output *out);
+
 /* Tunable launch and work-split parameters (picked by the package's
  * autotuner; not in the paper).  None changes a compile's result.
  *   obs_words     the observables of a circuit are split evenly over

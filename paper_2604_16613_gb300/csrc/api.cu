@@ -196,6 +196,7 @@ struct gp_driver {
     // tuning / instrumentation / test knobs
     gp_tuning tuning{512, 0, 512, 8, 4, kMaxSegments, 0};
     gp_debug debug{0, 0, 0, 0};
+    gp_host_output host_out{};          // edges_cap == 0: none
     bool timing = false;
     cudaEvent_t ev[5] = {};
     float times[4] = {0, 0, 0, 0};
@@ -470,6 +471,31 @@ gp_status gp_get_tuning(const gp_driver *d, gp_tuning *t) {
     return GP_OK;
 }
 
+gp_status gp_set_host_output(gp_driver *d, const gp_host_output *o) {
+    if (!d) return fail(GP_ERR_INVALID, "null argument");
+    if (!o) {
+        d->host_out = gp_host_output{};
+        return GP_OK;
+    }
+    if (!o->det_offsets || !o->det_idx || !o->obs_mask || !o->prob || !o->logodds || o->edges_cap == 0)
+        return fail(GP_ERR_INVALID, "host output: every array and a positive edges_cap are needed");
+    const void *arrays[5] = {o->det_offsets, o->det_idx, o->obs_mask, o->prob, o->logodds};
+    for (int i = 0; i < 5; i++) {
+        if (reinterpret_cast<uintptr_t>(arrays[i]) % (i == 2 ? 8u : 4u))
+            return fail(GP_ERR_INVALID, "host output: misaligned array");
+        if (!d->coherent_host) {
+            // without coherent access only page-locked memory is addressable
+            cudaPointerAttributes a{};
+            if (cudaPointerGetAttributes(&a, arrays[i]) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+                cudaGetLastError();
+                return fail(GP_ERR_INVALID, "host output: memory the device cannot address (page-lock it)");
+            }
+        }
+    }
+    d->host_out = *o;
+    return GP_OK;
+}
+
 gp_status gp_set_debug(gp_driver *d, const gp_debug *dbg) {
     if (!d || !dbg) return fail(GP_ERR_INVALID, "null argument");
     if (dbg->weak_hash > 2u || dbg->stall_windows > 1u || dbg->reserved != 0u)
@@ -708,6 +734,14 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     P->stall_windows = d->debug.stall_windows;
     P->ov_cap = L.ov_cap;
     P->obs_segments = n_seg;
+    const gp_host_output &ho = d->host_out;
+    P->h_det_off = reinterpret_cast<unsigned long long>(ho.edges_cap ? ho.det_offsets : nullptr);
+    P->h_det_idx = reinterpret_cast<unsigned long long>(ho.det_idx);
+    P->h_obs = reinterpret_cast<unsigned long long>(ho.obs_mask);
+    P->h_prob = reinterpret_cast<unsigned long long>(ho.prob);
+    P->h_logodds = reinterpret_cast<unsigned long long>(ho.logodds);
+    P->h_edges_cap = ho.edges_cap;
+    P->h_det_cap = ho.det_cap;
     // ---- pipeline: one graph launch ----------------------------------------------
     {
         const gp_status gs = ensure_graph(d);
@@ -729,6 +763,9 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
         full_reset(d, s);
         return fail((gp_status)st.code, msg);
     }
+    if (d->host_out.edges_cap &&
+        (st.n_edges + 1ull > d->host_out.edges_cap + 1ull || st.n_det_entries > d->host_out.det_cap))
+        return fail(GP_ERR_CAPACITY, "host output: the compile's hyperedges exceed its capacities");
     // ---- result view -----------------------------------------------------------
     d->n_loc_total = (uint32_t)loc_total;
     d->edge_offsets.assign(n_circuits + 1, 0);

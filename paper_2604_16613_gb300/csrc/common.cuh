@@ -81,6 +81,9 @@ struct Params {
     uint32_t stall_windows;     // 1: stage 1 stages no window
     uint32_t ov_cap;            // capacity of the overflow word list
     uint32_t obs_segments;      // most work items of one observable walk
+    // host output (0: none): the hyperedges also written into host memory
+    unsigned long long h_det_off, h_det_idx, h_obs, h_prob, h_logodds;
+    uint64_t h_edges_cap, h_det_cap;
 };
 
 // device status block (read back by the host after every compile)

@@ -421,12 +421,23 @@ __global__ void compact_write_kernel(Buffers B) {
     if (B.status->code != 0u) return;
     const uint32_t E = B.status->n_edges;
     const uint32_t lane = threadIdx.x & 31u;
+    // host output (when set): the same arrays, written into host memory too
+    const Params &P = *B.params;
+    uint32_t *const h_off = reinterpret_cast<uint32_t *>(P.h_det_off);
+    uint32_t *const h_idx = reinterpret_cast<uint32_t *>(P.h_det_idx);
+    unsigned long long *const h_obs = reinterpret_cast<unsigned long long *>(P.h_obs);
+    float *const h_prob = reinterpret_cast<float *>(P.h_prob);
+    float *const h_lo = reinterpret_cast<float *>(P.h_logodds);
+    const uint64_t h_ecap = P.h_edges_cap, h_dcap = P.h_det_cap;
+    if (h_off && E == 0u && blockIdx.x == 0 && threadIdx.x == 0) h_off[0] = 0u;
     for (uint32_t base = blockIdx.x * blockDim.x; base < E; base += gridDim.x * blockDim.x) {
         const uint32_t e = base + threadIdx.x;
         uint32_t b = 0xFFFFFFFFu;
+        uint32_t d0 = 0u, d1 = 0u;          // this edge's detector ids [d0, d1)
         if (e < E) {
             const uint32_t m = B.edge_mech[e];
             uint32_t d = B.det_off[e];
+            d0 = d;
             const uint32_t slot = B.slot_of[m];
             const unsigned long long info = B.mech_info[m];
             b = (uint32_t)(info >> 48);
@@ -455,15 +466,33 @@ __global__ void compact_write_kernel(Buffers B) {
                     x &= x - 1ull;
                 }
             }
+            d1 = d;
             const TabSlot &ts = B.table[slot];
             const float T = fixed_to_float(ts.acc_lo, ts.acc_hi, kProbShift);
             const float Pc = -0.5f * expm1f(-T);
+            const float lo = log1pf(-Pc) - logf(Pc);
             B.obs_mask[e] = obs;
             B.prob[e] = Pc;
-            B.logodds[e] = log1pf(-Pc) - logf(Pc);
+            B.logodds[e] = lo;
             B.class_slot[e] = slot;
             B.edge_circ[e] = b;
             B.table[slot].cls = e;
+            if (h_off && e < h_ecap) {
+                h_off[e] = d0;
+                h_obs[e] = obs;
+                h_prob[e] = Pc;
+                h_lo[e] = lo;
+                if (e + 1u == E && E <= h_ecap) h_off[E] = d1;
+            }
+        }
+        if (h_off) {
+            // the warp's edges are consecutive, so their detector ids are one
+            // range: copied to the host lane by lane (coalesced stores)
+            __syncwarp();
+            const uint32_t lo_w = __shfl_sync(0xFFFFFFFFu, d0, 0);
+            const unsigned has = __ballot_sync(0xFFFFFFFFu, e < E);
+            const uint32_t hi_w = has ? __shfl_sync(0xFFFFFFFFu, d1, 31 - __clz(has)) : lo_w;
+            for (uint32_t i = lo_w + lane; i < hi_w && i < h_dcap; i += 32u) h_idx[i] = B.det_idx[i];
         }
         // edges per circuit: one atomic per circuit present in the warp
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);

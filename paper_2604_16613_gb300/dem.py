@@ -300,6 +300,30 @@ class Driver:
         native.check(self.lib.gp_get_tuning(self.handle, ctypes.byref(t)))
         return {f: getattr(t, f) for f, _ in t._fields_}
 
+    def set_host_output(self, arrays: dict | None):
+        """Host arrays every later compile also fills with its hyperedges
+        (gp_set_host_output): ``det_offsets`` (int32, edges_cap + 1),
+        ``det_idx`` (int32), ``obs_mask`` (int64), ``prob`` and ``logodds``
+        (float32, edges_cap each) -- page-locked torch tensors or, on a device
+        that reads host memory coherently, numpy arrays.  None turns it off.
+        The arrays are kept referenced while they are in use."""
+        if arrays is None:
+            native.check(self.lib.gp_set_host_output(self.handle, None))
+            self._host_out = None
+            return
+
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+        def n(a):
+            return a.numel() if hasattr(a, "numel") else a.size
+        o = native.GpHostOutput(ptr(arrays["det_offsets"]), ptr(arrays["det_idx"]), ptr(arrays["obs_mask"]),
+                                ptr(arrays["prob"]), ptr(arrays["logodds"]),
+                                min(n(arrays["det_offsets"]) - 1, n(arrays["obs_mask"]), n(arrays["prob"]),
+                                    n(arrays["logodds"])), n(arrays["det_idx"]))
+        native.check(self.lib.gp_set_host_output(self.handle, ctypes.byref(o)))
+        self._host_out = arrays
+
     def set_debug(self, weak_hash: int = 0, wait_limit: int = 0, stall_windows: int = 0):
         """Test knobs of gp_set_debug: the weak grouping hashes (1: one tag for
         every mask, 2: one hash for every mask), the polls before a device

@@ -26,7 +26,7 @@ EXPORTED = [
     "gp_server_create", "gp_server_destroy", "gp_server_open_patch", "gp_server_close_patch",
     "gp_server_submit", "gp_server_step", "gp_server_completed", "gp_server_result", "gp_server_release",
     "gp_server_register_cycle", "gp_server_submit_registered", "gp_server_submit_registered_many",
-    "gp_server_drain", "gp_server_last_timing", "gp_server_set_tuning",
+    "gp_server_drain", "gp_server_last_timing", "gp_server_set_tuning", "gp_set_host_output",
 ]
 
 
@@ -61,6 +61,12 @@ class GpTuning(ctypes.Structure):
                 ("stage2_threads", ctypes.c_uint32), ("stage2_blocks_per_sm", ctypes.c_uint32),
                 ("obs_words", ctypes.c_uint32), ("obs_segments", ctypes.c_uint32),
                 ("stage1_wide_emit", ctypes.c_uint32)]
+
+
+class GpHostOutput(ctypes.Structure):
+    _fields_ = [("det_offsets", ctypes.c_void_p), ("det_idx", ctypes.c_void_p), ("obs_mask", ctypes.c_void_p),
+                ("prob", ctypes.c_void_p), ("logodds", ctypes.c_void_p), ("edges_cap", ctypes.c_uint64),
+                ("det_cap", ctypes.c_uint64)]
 
 
 class GpDebug(ctypes.Structure):
@@ -122,6 +128,7 @@ def load(path: str = LIB_PATH):
         lib.gp_result_view.argtypes = [vp, ctypes.POINTER(GpDemView)]
         lib.gp_result_to_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.gp_set_tuning.argtypes = [vp, ctypes.POINTER(GpTuning)]
+        lib.gp_set_host_output.argtypes = [vp, ctypes.POINTER(GpHostOutput)]
         lib.gp_get_tuning.argtypes = [vp, ctypes.POINTER(GpTuning)]
         lib.gp_enable_timing.argtypes = [vp, i32]
         lib.gp_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
@@ -157,7 +164,7 @@ def load(path: str = LIB_PATH):
         lib.gp_last_error.restype = ctypes.c_char_p
         for name in ("gp_workspace_size", "gp_driver_create", "gp_compile_batch", "gp_compile",
                      "gp_backward", "gp_result_view", "gp_result_to_host", "gp_set_tuning",
-                     "gp_get_tuning", "gp_enable_timing", "gp_last_timing", "gp_set_debug"):
+                     "gp_get_tuning", "gp_enable_timing", "gp_last_timing", "gp_set_debug", "gp_set_host_output"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib

@@ -254,6 +254,61 @@ def test_nop_rows_equal_zero_probability_locations():
     compare_edges(dem.edges(), oracle_edges(circ, zero).edges(), "nop")
 
 
+def test_host_output_equals_device_result():
+    """Host output (gp_set_host_output): the compaction kernel also writes the
+    hyperedges into caller-owned host arrays; they equal the device result
+    bit for bit (page-locked tensors, and numpy arrays where the device reads
+    host memory coherently); a capacity too small fails the compile; turning
+    it off restores the plain compile."""
+    circs = [C.rotated_surface_code_memory(5, 5, C.NoiseModel.uniform(1e-3)),
+             C.bb_memory(3, C.NoiseModel.uniform(1e-3), seed=3)] + [C.random_circuit(s) for s in range(4)]
+    noise = np.concatenate([f32(c.default_noise) for c in circs])
+    drv = Driver.for_circuits(circs)
+    ref = drv.compile(circs, noise).to_host()
+    ne, nd = ref["det_offsets"].size - 1, ref["det_idx"].size
+    cap_e, cap_d = ne + 7, nd + 13
+
+    def arrays(make):
+        return {"det_offsets": make(cap_e + 1, np.int32), "det_idx": make(cap_d, np.int32),
+                "obs_mask": make(cap_e, np.int64), "prob": make(cap_e, np.float32),
+                "logodds": make(cap_e, np.float32)}
+
+    def check(out):
+        assert np.array_equal(np.asarray(out["det_offsets"])[:ne + 1], ref["det_offsets"])
+        assert np.array_equal(np.asarray(out["det_idx"])[:nd], ref["det_idx"])
+        assert np.array_equal(np.asarray(out["obs_mask"])[:ne].view(np.uint64), ref["obs_mask"])
+        assert np.array_equal(np.asarray(out["prob"])[:ne], ref["prob"])
+        assert np.array_equal(np.asarray(out["logodds"])[:ne], ref["logodds"])
+
+    pinned = arrays(lambda n, t: torch.full((n,), -1, dtype=getattr(torch, np.dtype(t).name), pin_memory=True))
+    drv.set_host_output(pinned)
+    for inputs_on_device in (False, True):
+        for a in pinned.values():
+            a.fill_(-1)
+        if inputs_on_device:
+            drv.compile([DeviceCircuit(c) for c in circs], torch.tensor(noise, device="cuda"))
+        else:
+            drv.compile(circs, noise)
+        check({k: v.numpy() for k, v in pinned.items()})
+    try:
+        plain = arrays(lambda n, t: np.full(n, -1, dtype=t))
+        drv.set_host_output(plain)
+    except native.GpError as e:
+        assert e.code == native.GP_ERR_INVALID        # pageable memory on a device that cannot read it
+    else:
+        drv.compile(circs, noise)
+        check(plain)
+    small = {k: v[: (ne // 2 + 1 if k == "det_offsets" else ne // 2)] for k, v in pinned.items()}
+    drv.set_host_output(small)
+    with pytest.raises(native.GpError) as e:
+        drv.compile(circs, noise)
+    assert e.value.code == native.GP_ERR_CAPACITY
+    drv.set_host_output(None)
+    again = drv.compile(circs, noise).to_host()
+    for k in ref:
+        assert np.array_equal(ref[k], again[k]), k
+
+
 def test_saturated_x_error():
     c = C.Circuit(1)
     c.gate1(C.R, [0]); c.tick()
