@@ -502,7 +502,24 @@ def calibration_section(args) -> dict:
             "loss_first_best": [history[0], min(history)]}
 
 
-def serve_section(args) -> dict:
+def record_horizon(blocks) -> int:
+    """The most cycles back that a detector or observable row of a cycle
+    reads a measurement record from (blocks: ``Circuit.cycle_blocks()``)."""
+    from paper_2604_16613_gb300.circuits import DETECTOR, OBSERVABLE_INCLUDE, MEASURE_KINDS
+    starts = np.concatenate([[0], np.cumsum([int(b["n_measurements"]) for b in blocks])])
+    reach = 0
+    for c, b in enumerate(blocks):
+        ops = np.asarray(b["ops"], np.int64).reshape(-1, 4)
+        recs = np.asarray(b["recs"], np.int64)
+        before = starts[c] + np.concatenate([[0], np.cumsum(np.isin(ops[:, 0], list(MEASURE_KINDS)))])[:-1]
+        for r in np.flatnonzero(np.isin(ops[:, 0], [DETECTOR, OBSERVABLE_INCLUDE])):
+            for lb in recs[ops[r, 1]:ops[r, 1] + ops[r, 2]]:
+                m = before[r] - lb
+                reach = max(reach, c - int(np.searchsorted(starts, m, side="right") - 1))
+    return reach
+
+
+def serve_section(args, n_adaptive: int = 0, rates: str | None = None) -> dict:
     """Continuous serving: ``--serve-patches`` patches, each issuing one
     per-cycle request as a Poisson process, for ``--serve-seconds`` (after
     ``--serve-warmup-seconds`` untimed at the same load) at each
@@ -518,17 +535,29 @@ def serve_section(args) -> dict:
     completed rate below the offered one and a latency that grows with the
     run's length."""
     from paper_2604_16613_gb300 import circuits as C
+    from paper_2604_16613_gb300 import native
     from paper_2604_16613_gb300.serve import Server
     P, T, K = args.serve_patches, args.serve_seconds, args.serve_k
-    rates = [float(r) for r in args.serve_rates.split(",") if r]
+    rates = [float(r) for r in (rates or args.serve_rates).split(",") if r]
     ds = list(range(5, 27, 2))
-    kinds = [("bb", 0) if i % 4 == 3 else ("surface", ds[(i - i // 4) % len(ds)]) for i in range(P)]
+    kinds = [("bb", 0) if i % 4 == 3 else ("surface", ds[(i - i // 4) % len(ds)]) for i in range(P - n_adaptive)]
     tmpl = {}
     for k in sorted(set(kinds)):
         tmpl[k] = (C.bb_memory(3, C.NoiseModel.uniform(1e-3), seed=3) if k[0] == "bb"
                    else C.rotated_surface_code_memory(k[1], 3, C.NoiseModel.uniform(1e-3)))
-    srv = Server.for_circuits(list(tmpl.values()), max_patches=P, max_batch=P, max_cycles_per_step=K,
-                              max_horizon=1, max_pending=P * 512)
+    # adaptive patches: realised branches of the adaptive [[4,2,2]]-concatenated
+    # code (outer distance 10, a block firing with probability 5 % per cycle),
+    # each long enough for every load, streamed cycle by cycle as rows (every
+    # cycle drawn anew, so nothing is registered)
+    warm_s = args.serve_warmup_seconds
+    # (the most events a load can draw per patch, timed and untimed, and the warm-up)
+    n_cyc = sum(int(r * T * 1.3) + 32 + (int(r * warm_s * 1.3) + 32 if warm_s > 0 else 0) for r in rates) + 16
+    streams = [C.concatenated_adaptive_branch(10, n_cyc, seed=4000 + a, noise=C.NoiseModel.uniform(1e-3))
+               for a in range(n_adaptive)]
+    blocks_a = [c.cycle_blocks()[:-1] for c in streams]        # the final data readout is never reached
+    H_a = max([record_horizon(b) for b in blocks_a] + [1])
+    srv = Server.for_circuits(list(tmpl.values()) + streams, max_patches=P, max_batch=P, max_cycles_per_step=K,
+                              max_horizon=H_a if n_adaptive else 1, max_pending=P * 512)
     pids, mid = [], []
     first = []
     for k in kinds:
@@ -538,11 +567,22 @@ def serve_section(args) -> dict:
         first.append(srv.register_cycle(pid, b[0]))
         mid.append(srv.register_cycle(pid, b[1]))
         pids.append(pid)
-    pids, mid = np.array(pids, np.uint32), np.array(mid, np.uint32)
+    apids = [srv.open_circuit_patch(c, H_a) for c in streams]
+    nxt = [0] * n_adaptive                  # next cycle of each adaptive stream
+    pids, mid = np.array(pids + apids, np.uint32), np.array(mid + [0] * n_adaptive, np.uint32)
+    n_reg = P - n_adaptive
+
+    def submit_adaptive(a: int, t_ns: int = 0):
+        srv.submit(int(apids[a]), blocks_a[a][nxt[a]], final=False, t_arrival_ns=t_ns)
+        nxt[a] += 1
+
     # warm-up (graph capture, first cycles): five cycles per patch
-    srv.submit_registered_many(pids, np.array(first, np.uint32))
+    srv.submit_registered_many(pids[:n_reg], np.array(first, np.uint32))
     for _ in range(4):
-        srv.submit_registered_many(pids, mid)
+        srv.submit_registered_many(pids[:n_reg], mid[:n_reg])
+    for a in range(n_adaptive):
+        for _ in range(5):
+            submit_adaptive(a)
     while srv.step():
         pass
     srv.drain()
@@ -563,6 +603,7 @@ def serve_section(args) -> dict:
         deadline = start + int((10 * T + 30) * 1e9)     # a stuck server fails the load, never hangs the bench
         abs_ns = (start + ev_t * 1e9).astype(np.uint64)
         ev_patch, ev_cycle = pids[ev_p], mid[ev_p]
+        ad_pos = np.flatnonzero(ev_p >= n_reg)   # events of adaptive patches (submitted as rows)
         lat, edges, bad = [], 0, 0
         i = outstanding = steps = 0
         step_ns, step_req, step_parts = [], [], []
@@ -571,10 +612,26 @@ def serve_section(args) -> dict:
             now = time.monotonic_ns()
             j = int(np.searchsorted(abs_ns, now, side="right"))
             if j > i:
-                got = srv.submit_registered_many(ev_patch[i:j], ev_cycle[i:j], None, abs_ns[i:j],
-                                                 stop_when_full=True)
-                outstanding += got.size
-                i += got.size
+                while i < j:
+                    if ev_p[i] >= n_reg:
+                        try:
+                            submit_adaptive(int(ev_p[i]) - n_reg, int(abs_ns[i]))
+                        except native.GpError as e:
+                            if e.code != native.GP_ERR_CAPACITY:
+                                raise
+                            break                   # the queue is full: the rest waits for a step
+                        i += 1
+                        outstanding += 1
+                        continue
+                    # registered cycles up to the next adaptive event, in one call
+                    q = int(np.searchsorted(ad_pos, i))
+                    k2 = min(j, int(ad_pos[q]) if q < ad_pos.size else j)
+                    got = srv.submit_registered_many(ev_patch[i:k2], ev_cycle[i:k2], None, abs_ns[i:k2],
+                                                     stop_when_full=True)
+                    outstanding += got.size
+                    i += got.size
+                    if got.size < k2 - (i - got.size):
+                        break
                 client_max = max(client_max, time.monotonic_ns() - now)
             if outstanding:
                 t0 = time.monotonic_ns()
@@ -623,10 +680,13 @@ def serve_section(args) -> dict:
     finally:
         gc.enable()
     srv.close()
+    mix = "surface d=5..25 odd : BB [[144,12,12]] = 3:1" + (
+        f", plus {n_adaptive} adaptive [[4,2,2]]-concatenated d=10 patches (cycles drawn per cycle, H={H_a})"
+        if n_adaptive else "")
     return {
-        "workload": f"{P} patches (surface d=5..25 odd : BB [[144,12,12]] = 3:1), Poisson per-cycle requests, "
-                    f"{T:g} s per load (after {args.serve_warmup_seconds:g} s untimed at the load), p=1e-3, L2, H=1, "
-                    f"up to {K} cycles per patch per step",
+        "workload": f"{P} patches ({mix}), Poisson per-cycle requests, "
+                    f"{T:g} s per load (after {args.serve_warmup_seconds:g} s untimed at the load), p=1e-3, L2, "
+                    f"H=1 for surface and BB, up to {K} cycles per patch per step",
         "loads": loads,
     }
 
@@ -823,6 +883,8 @@ def run_ours(args):
         if args.serve_patches > 0:
             torch.cuda.empty_cache()
             result["serve"] = serve_section(args)
+            if args.serve_adaptive > 0:
+                result["serve_adaptive"] = serve_section(args, args.serve_adaptive, args.serve_adaptive_rates)
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -853,6 +915,9 @@ def main():
     ap.add_argument("--serve-rates", default="50,100,250,500,750,1000",
                     help="per-patch request rates (Hz) of the serving loads, comma-separated")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-adaptive", type=int, default=4,
+                    help="adaptive patches among --serve-patches in a second serving section (0: none)")
+    ap.add_argument("--serve-adaptive-rates", default="50,100")
     ap.add_argument("--serve-warmup-seconds", type=float, default=0.3,
                     help="untimed seconds at each load before its timed run")
     ap.add_argument("--serve-k", type=int, default=4, help="cycles of one patch merged into a step")
