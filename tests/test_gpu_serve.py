@@ -138,6 +138,18 @@ def test_registered_cycles_equal_full_compile(name, rounds, K):
     compare_edges(got, orc.edges(), f"{name} registered K={K}")
 
 
+def test_adaptive_d10_stream_equals_full_compile():
+    """A realised branch of the adaptive [[4,2,2]]-concatenated code at outer
+    distance 10 (the serving bench's adaptive patch), streamed cycle by cycle
+    as rows with H = 5 (its outer checks run every d/2 cycles), two cycles per
+    step: the delivered hyperedges equal the full compile bit for bit."""
+    circ = C.concatenated_adaptive_branch(10, 14, seed=4000, noise=C.NoiseModel.uniform(1e-3))
+    got = Server.for_circuits([circ], max_cycles_per_step=2, max_horizon=5).stream([circ], [5])[0]
+    ref = gpu_full(circ)
+    assert len(got) == len(ref)
+    assert got == ref
+
+
 def test_levels(wl):
     circ, H = wl["surface5"]
     srv = Server.for_circuits([circ], max_cycles_per_step=2, max_horizon=H)
