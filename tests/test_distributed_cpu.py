@@ -34,6 +34,19 @@ def test_single_process_helpers():
     assert bench.job_rate(100.0, 4, 2.0) == 200.0
 
 
+def test_record_horizon_of_cycle_blocks():
+    """The bench's horizon for streamed patches: how many cycles back a
+    detector reads a record.  The surface and [[144,12,12]] memories compare
+    consecutive rounds; the adaptive code's outer checks run every d/2 cycles
+    (two at outer distance 4)."""
+    from paper_2604_16613_gb300 import circuits as C
+    nm = C.NoiseModel.uniform(1e-3)
+    assert bench.record_horizon(C.rotated_surface_code_memory(5, 5, nm).cycle_blocks()) == 1
+    assert bench.record_horizon(C.bb_memory(3, nm, seed=3).cycle_blocks()) == 1
+    ad = C.concatenated_adaptive_branch(4, 9, seed=5, noise=nm, layout=C.ConcatenatedLayout(4))
+    assert bench.record_horizon(ad.cycle_blocks()) == 2
+
+
 def test_max_over_ranks_gloo_world2():
     ctx = mp.get_context("spawn")
     queue = ctx.Queue()
