@@ -53,6 +53,7 @@ namespace {
 
 constexpr int kSegCache = 256;      // layer segments cached for the producer
 constexpr uint32_t kSplitMinLayers = 64;   // observable walks this long are split in two (twice: three)
+constexpr uint32_t kRankSortMax = 256;     // column entries sorted in one rank pass (else bitonic)
 constexpr int kMaxBufs = 4;         // window ring slots at most
 
 struct Smem {
@@ -184,13 +185,16 @@ __device__ uint32_t column_entries(const Buffers &B, const CircuitDev &C, uint32
     } else {
         // observable word k holds observables k * obs_per .. (bit = observable)
         const uint32_t o0 = (local - (C.n_cols - C.n_ocols)) * C.obs_per, o1 = o0 + C.obs_per;
+        // one warp per row, its records over the lanes (a logical reads
+        // many records)
         const uint32_t n_rows = B.obs_count[cidx];
-        for (uint32_t i0 = threadIdx.x; i0 < n_rows; i0 += NT) {
+        const uint32_t lane = threadIdx.x & 31u;
+        for (uint32_t i0 = threadIdx.x >> 5; i0 < n_rows; i0 += NT / 32u) {
             const uint32_t row = B.obs_rows[C.op_base + i0];
             const uint4 op = C.ops[row];
             if (op.w < o0 || op.w >= o1) continue;
             const uint32_t mb = B.aux[C.op_base + row];
-            for (uint32_t i = 0; i < op.z; i++) {
+            for (uint32_t i = lane; i < op.z; i += 32u) {
                 const uint32_t e = atomicAdd(&nent_sh, 1u);
                 if (e < (uint32_t)kMaxEntries) {
                     ent_m[e] = mb - C.recs[op.y + i];
@@ -206,6 +210,31 @@ __device__ uint32_t column_entries(const Buffers &B, const CircuitDev &C, uint32
         return 0u;
     }
     if (n_ent == 0u) return 0u;
+    if (n_ent <= kRankSortMax) {
+        // few entries: each one's place is the number of entries before it
+        // in (measurement, position) order -- one pass instead of the
+        // bitonic network's barriers.  The sorted copies go to the layer and
+        // qubit arrays (free until the merge below), then back.
+        unsigned long long *sw = reinterpret_cast<unsigned long long *>(ent_l);     // n_ent words
+        uint32_t *sm = ent_q + kMaxEntries / 2u;                                   // n_ent measurements
+        static_assert(2 * kRankSortMax <= kMaxEntries / 2, "rank-sort scratch inside ent_l / ent_q");
+        for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
+            const uint32_t m = ent_m[i];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < n_ent; j++) {
+                const uint32_t mj = ent_m[j];
+                r += (mj < m || (mj == m && j < i)) ? 1u : 0u;
+            }
+            sm[r] = m;
+            sw[r] = ent_w[i];
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n_ent; i += NT) {
+            ent_m[i] = sm[i];
+            ent_w[i] = sw[i];
+        }
+        __syncthreads();
+    } else {
     // bitonic sort of the entries by measurement index
     uint32_t npow = 1;
     while (npow < n_ent) npow <<= 1;
@@ -227,6 +256,7 @@ __device__ uint32_t column_entries(const Buffers &B, const CircuitDev &C, uint32
             }
             __syncthreads();
         }
+    }
     }
     // merge the entries of one measurement: the first of a run holds the
     // XOR of the run, the rest hold zero (the layer array holds the merged
