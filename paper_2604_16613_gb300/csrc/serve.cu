@@ -1234,8 +1234,8 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
     gp_status cst = gp_compile_batch(s->drv, circ.data(), n_win, s->arena_noise, 1, level, stream, &view);
     const uint64_t t_compiled = now_ns();
     std::vector<uint32_t> win_status(n_win, GP_OK);
-    uint32_t n_pass = 0;
-    for (const Win &w : wins) n_pass = std::max<uint32_t>(n_pass, (uint32_t)w.reqs.size());
+    uint32_t n_slots = 0;
+    for (const Win &w : wins) n_slots = std::max<uint32_t>(n_slots, (uint32_t)w.reqs.size());
     const uint32_t rs = n_win + 1u;             // entries of one slot's row of starts
     OutBuf *ob = nullptr;
     if (cst == GP_OK && view.n_edges) {
@@ -1245,11 +1245,11 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         if (view.n_det_entries > 0xFFFFFFFFull)
             cst = sfail(GP_ERR_CAPACITY, "a step's detector ids exceed 32 bits");
         if (cst == GP_OK) {
-            ob = take_outbuf(s, view.n_edges, (uint64_t)n_pass * n_win, view.n_det_entries);
+            ob = take_outbuf(s, view.n_edges, (uint64_t)n_slots * n_win, view.n_det_entries);
             if (!ob) cst = sfail(GP_ERR_CUDA, "cudaMallocHost of a result buffer failed");
         }
         if (cst == GP_OK) {
-            *s->h_sel = SelParams{n_win, n_pass, ob->edges_cap, ob->det_cap,
+            *s->h_sel = SelParams{n_win, n_slots, ob->edges_cap, ob->det_cap,
                                   SealOut{ob->doff, ob->det, ob->prob, ob->logodds, ob->obs}};
             const gp_status gs = ensure_select_graph(s);
             if (gs != GP_OK) cst = gs;
@@ -1257,8 +1257,8 @@ gp_status gp_server_step(gp_server *s, gp_level level, void *stream, uint32_t *n
         if (cst == GP_OK) {
             SV_CUDA(cudaGraphLaunch(s->sel_exec, st));
             SV_CUDA(cudaStreamSynchronize(st));
-            const uint2 tot = s->h_starts[(size_t)(n_pass - 1u) * rs + n_win];
-            if (tot.x + (uint64_t)n_pass * n_win > ob->edges_cap || tot.y > ob->det_cap)
+            const uint2 tot = s->h_starts[(size_t)(n_slots - 1u) * rs + n_win];
+            if (tot.x + (uint64_t)n_slots * n_win > ob->edges_cap || tot.y > ob->det_cap)
                 cst = sfail(GP_ERR_CAPACITY, "sealed output larger than the step's whole output");
             for (uint32_t w = 0; w < n_win; w++) {
                 if (s->h_horizon[w]) win_status[w] = GP_ERR_HORIZON;
