@@ -165,6 +165,7 @@ struct gp_driver {
     gp_bounds bounds{};
     Layout L{};
     int device = 0, n_sms = 0;
+    uint64_t l2_bytes = 0;          // the device's L2 cache
     size_t smem_limit = 0;          // dynamic shared memory a stage-1 block may take
     unsigned char *ws = nullptr;
     bool own_ws = false;
@@ -408,6 +409,9 @@ gp_status gp_driver_create(const gp_bounds *bounds, void *d_workspace, uint64_t 
         // tested against each other)
         const char *env = getenv("GPDEM_STAGE_HOST_INPUTS");
         if (env && env[0] == '1') d->coherent_host = false;
+        int l2 = 0;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, d->device) == cudaSuccess && l2 > 0)
+            d->l2_bytes = (uint64_t)l2;
     }
     for (int i = 0; i < 5; i++)
         if (cudaEventCreate(&d->ev[i]) != cudaSuccess) return cleanup(fail(GP_ERR_CUDA, "cudaEventCreate failed"));
@@ -734,6 +738,7 @@ gp_status gp_compile_batch(gp_driver *d, const gp_circuit *circuits, uint32_t n_
     P->stall_windows = d->debug.stall_windows;
     P->ov_cap = L.ov_cap;
     P->obs_segments = n_seg;
+    P->l2_prefetch_max = d->l2_bytes / 4u * 3u;
     const gp_host_output &ho = d->host_out;
     P->h_det_off = reinterpret_cast<unsigned long long>(ho.edges_cap ? ho.det_offsets : nullptr);
     P->h_det_idx = reinterpret_cast<unsigned long long>(ho.det_idx);

@@ -81,6 +81,8 @@ struct Params {
     uint32_t stall_windows;     // 1: stage 1 stages no window
     uint32_t ov_cap;            // capacity of the overflow word list
     uint32_t obs_segments;      // most work items of one observable walk
+    uint64_t l2_prefetch_max;   // bytes of per-mechanism grouping arrays stage 1
+                                // prefetches into L2 (0: none; about 3/4 of L2)
     // host output (0: none): the hyperedges also written into host memory
     unsigned long long h_det_off, h_det_idx, h_obs, h_prob, h_logodds;
     uint64_t h_edges_cap, h_det_cap;
@@ -98,7 +100,8 @@ struct Status {
     uint32_t rec_count;         // records handed out from the pool
     uint32_t ov_count;          // overflow words taken (mechanisms with more
                                 // than kInlineWords words)
-    uint32_t pad[5];
+    uint32_t pf_ticket;         // stage-1 blocks that ran out of work (L2 prefetch)
+    uint32_t pad[4];
 };
 
 // one slot of the grouping hash table (one 32-byte sector)

@@ -755,6 +755,16 @@ struct SplitSmem {
     unsigned char *win;             // window buffers
 };
 
+// Share r of R of [base, base + bytes) prefetched into L2 (a hint: bulk
+// prefetches of up to 64 KB, which nothing waits for).  base is 16-byte aligned.
+__device__ __forceinline__ void l2_prefetch_share(const void *base, size_t bytes, uint32_t r, uint32_t R) {
+    const char *p = static_cast<const char *>(base);
+    for (size_t off = (size_t)r * 65536u; off < bytes; off += (size_t)R * 65536u) {
+        const uint32_t len = (uint32_t)(min(bytes - off, (size_t)65536u) & ~(size_t)15u);
+        if (len) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + off), "r"(len) : "memory");
+    }
+}
+
 // Warps of a block: the first warps walk (two from 512 threads, four from
 // 1024), the last warp stages windows, the rest emit.
 __host__ __device__ constexpr uint32_t split_walkers(uint32_t nt) { return nt >= 1024u ? 4u : (nt >= 512u ? 2u : 1u); }
@@ -826,6 +836,7 @@ struct SplitShared {
     int posted_lo;          // lowest window the producer posted
     WalkStep wstep;         // warp 0 -> helper walker warps: the large step
     uint32_t wcnt[2];       // large step: {active, added}
+    uint32_t worked;        // the block took at least one work item
 };
 
 template <int NT, bool WIDE>
@@ -863,6 +874,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         }
         fence_mbar_init();
         sh.tmo = 0;
+        sh.worked = 0;
     }
     for (uint32_t q = threadIdx.x; q < round8(maxq); q += NT) s.tag0[q] = s.tag1[q] = kNone;
     __syncthreads();
@@ -936,6 +948,7 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
     for (;;) {
         if (threadIdx.x == 0) {
             sh.item = atomicAdd(&B.status->queue_head, 1u);
+            if (sh.item < P.n_items) sh.worked = 1u;
             sh.bail = (*(volatile uint32_t *)&B.status->code) != 0u;
             sh.nent = 0;
             sh.lmax = 0;
@@ -1570,6 +1583,27 @@ __global__ void __launch_bounds__(NT, 1) stage1_split_kernel(Buffers B, uint32_t
         }
     }
     flush_chunks();
+    // The grouping's first kernel adds into every mechanism's key and stores
+    // its words into the mechanism's inline slots: after an L2 flush (or
+    // another compile) those lines are in DRAM, and each atomic or partial
+    // store waits for its sector.  The first quarter of the blocks that
+    // walked, in the order they run out of work, prefetch the two arrays into
+    // L2 while the last walks finish; the last blocks, which end the kernel,
+    // issue nothing.  Only when the arrays fit well within L2.
+    if (threadIdx.x == 0 && sh.worked) {
+        const size_t nm = min(B.status->n_mech, P.max_mech);
+        const size_t bytes = nm * (sizeof(unsigned long long) +
+                                   kInlineWords * (sizeof(uint32_t) + sizeof(unsigned long long)));
+        if (nm && bytes <= P.l2_prefetch_max) {
+            const uint32_t R = max(1u, min(gridDim.x, P.n_items) / 4u);
+            const uint32_t t = atomicAdd(&B.status->pf_ticket, 1u);
+            if (t < R) {
+                l2_prefetch_share(B.mech_key, (nm * sizeof(unsigned long long)) & ~(size_t)15u, t, R);
+                l2_prefetch_share(B.inl_col, nm * kInlineWords * sizeof(uint32_t), t, R);
+                l2_prefetch_share(B.inl_word, nm * kInlineWords * sizeof(unsigned long long), t, R);
+            }
+        }
+    }
     // copies still in flight (after a timeout) land before the block exits
     if (producer && lane == 0u) {
         for (uint32_t i = 0; i < nring; i++)
