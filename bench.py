@@ -608,8 +608,10 @@ def serve_section(args, n_adaptive: int = 0, rates: str | None = None) -> dict:
         i = outstanding = steps = 0
         step_ns, step_req, step_parts = [], [], []
         client_max = 0                      # longest submit or drain call of the client
+        other_max = 0                       # longest stretch of one loop pass outside those calls and the step
         while i < n_ev or outstanding:
             now = time.monotonic_ns()
+            inside = 0
             j = int(np.searchsorted(abs_ns, now, side="right"))
             if j > i:
                 while i < j:
@@ -632,7 +634,8 @@ def serve_section(args, n_adaptive: int = 0, rates: str | None = None) -> dict:
                     i += got.size
                     if got.size < k2 - (i - got.size):
                         break
-                client_max = max(client_max, time.monotonic_ns() - now)
+                inside = time.monotonic_ns() - now
+                client_max = max(client_max, inside)
             if outstanding:
                 t0 = time.monotonic_ns()
                 if t0 > deadline:
@@ -644,11 +647,14 @@ def serve_section(args, n_adaptive: int = 0, rates: str | None = None) -> dict:
                 step_parts.append(srv.last_timing())
                 steps += 1
                 d = srv.drain()
-                client_max = max(client_max, time.monotonic_ns() - t1)
+                t2 = time.monotonic_ns()
+                client_max = max(client_max, t2 - t1)
+                inside += t2 - t0
                 outstanding -= d["ids"].size
                 lat.append((d["t_done_ns"].astype(np.int64) - d["t_arrival_ns"].astype(np.int64)))
                 edges += int(d["n_edges"].sum())
                 bad += int((d["status"] != 0).sum())
+            other_max = max(other_max, time.monotonic_ns() - now - inside)
         elapsed = (time.monotonic_ns() - start) / 1e9
         lat_us = np.concatenate(lat) / 1e3
         return {
@@ -658,6 +664,7 @@ def serve_section(args, n_adaptive: int = 0, rates: str | None = None) -> dict:
             "latency_us_max": float(lat_us.max()),
             "step_ms_mean": float(np.mean(step_ns) / 1e6), "step_ms_p99": float(np.percentile(step_ns, 99) / 1e6),
             "step_ms_max": float(np.max(step_ns) / 1e6), "client_call_ms_max": client_max / 1e6,
+            "loop_other_ms_max": other_max / 1e6,
             "requests_per_step_mean": float(np.mean(step_req)),
             "step_us_mean": dict(zip(["build", "compile", "select", "hand_out", "lowering", "stage1", "group",
                                       "compact"],
